@@ -1,0 +1,554 @@
+"""Pins of the FP64 oracle against closed forms, invariants and brute force.
+
+None of these re-types the oracle's own formulas: each compares it with something the
+paper or the mathematics fixes independently (closed-form energies of simple shapes,
+Euler-Bernoulli statics, conservation laws, brute-force minimisation, discrete
+Gauss-Bonnet for the loop holonomy, central finite differences of whole rollouts).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import OracleSim, elastic_energy, closest_params, sdf_box, sdf_capsule
+from oracle.dlo import build_frames, edges_of, hinge_sides, signed_angle, transport, unit, F64
+from paper_2606_04206_gb300 import inputs
+
+
+def straight(n, L, z=1.0):
+    x = np.zeros((n, 3))
+    x[:, 0] = np.linspace(0.0, L, n)
+    x[:, 2] = z
+    return x
+
+
+def energy_forces(sim, gi=0):
+    G, S = sim.groups[gi], sim.state[gi]
+    x = S["x"].clone().requires_grad_(True)
+    th = S["theta"].clone().requires_grad_(True)
+    U = elastic_energy(x, th, S["tb"], S["d1b"], S["mprev"], S["kbar"], G["R"], G["closed"])
+    gx, gth = torch.autograd.grad(U.sum(), [x, th])
+    return U.detach(), -gx, -gth
+
+
+def make(rods, x0=None, theta0=None, **kw):
+    p = inputs.custom(rods, **kw)
+    if x0 is not None:
+        p.x0 = np.concatenate(x0)
+    if theta0 is not None:
+        p.theta0 = np.asarray(theta0, np.float64)
+    sim = OracleSim(p)
+    sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    return p, sim
+
+
+R_, RHO = float(np.float32(0.002)), 1000.0     # inputs are float32-representable
+A_ = math.pi * R_ ** 2
+
+
+# ---------------------------------------------------------------------- P1 closed-form energies
+
+def test_straight_rod_has_zero_energy_and_force():
+    p, sim = make([straight(12, 0.5)], K=1e6, E=1e6, G=4e5)
+    U, F, tau = energy_forces(sim)
+    assert abs(float(U)) < 1e-20
+    assert float(F.abs().max()) < 1e-12 and float(tau.abs().max()) < 1e-14
+
+
+def test_uniform_stretch_energy():
+    eps, L, K = 0.01, 0.5, 1e6
+    p, sim = make([straight(12, L)], x0=[straight(12, L * (1 + eps))], K=K, E=1e6, G=4e5)
+    U, _, _ = energy_forces(sim)
+    A = math.pi * p.radius[0] ** 2
+    eb = np.linalg.norm(np.diff(p.x_rest, axis=0), axis=1)
+    e = np.linalg.norm(np.diff(p.x0, axis=0), axis=1)
+    assert float(U) == pytest.approx((0.5 * K * A * (e / eb - 1) ** 2 * eb).sum(), rel=1e-10)
+    assert float(U) == pytest.approx(0.5 * K * A_ * eps ** 2 * L, rel=1e-6)
+
+
+def arc(n, l, Rc):
+    phi = 2 * math.asin(l / (2 * Rc))
+    a = np.arange(n) * phi
+    return np.stack([Rc * np.sin(a), Rc * (1 - np.cos(a)), np.ones(n)], 1), phi
+
+
+def test_planar_arc_bending_energy():
+    n, l, Rc, E = 20, 0.01, 0.1, 1e6
+    x, phi = arc(n, l, Rc)
+    p, sim = make([straight(n, l * (n - 1))], x0=[x], K=1e6, E=E, G=4e5)
+    U, _, _ = energy_forces(sim)
+    kb = 2 * math.tan(phi / 2)
+    eb = np.linalg.norm(np.diff(p.x_rest, axis=0), axis=1)
+    lbar = 0.5 * (eb[1:] + eb[:-1])
+    expect = 0.5 * (E * A_ * R_ ** 2 / 4) * (kb ** 2 / lbar).sum()
+    assert float(U) == pytest.approx(expect, rel=1e-9)
+    # continuum limit of a closed circle: U_b -> E I pi / R (checked at fine resolution)
+    N = 400
+    ang = np.arange(N) * 2 * math.pi / N
+    circ = np.stack([Rc * np.cos(ang), Rc * np.sin(ang), np.ones(N)], 1)
+    p2, sim2 = make([circ], closed=[True], K=1e6, E=E, G=0.0)
+    G2 = sim2.groups[0]
+    G2["R"]["kbar0"].zero_()
+    sim2.state[0]["kbar"].zero_()
+    U2, _, _ = energy_forces(sim2)
+    EI = E * math.pi * R_ ** 4 / 4
+    assert float(U2) == pytest.approx(EI * math.pi / Rc, rel=1e-3)
+
+
+def test_uniform_twist_energy_and_end_torques():
+    n, L, Gm = 10, 0.45, 4e5
+    E = n - 1
+    Phi = 0.7
+    th = Phi * np.arange(E) / (E - 1)
+    p, sim = make([straight(n, L)], theta0=th, K=1e6, E=1e6, G=Gm)
+    U, F, tau = energy_forces(sim)
+    eb = np.linalg.norm(np.diff(p.x_rest, axis=0), axis=1)
+    lbar = 0.5 * (eb[1:] + eb[:-1])
+    l = L / (n - 1)
+    beta = Gm * A_ * R_ ** 2 / 2
+    m = Phi / (E - 1)
+    assert float(U) == pytest.approx(0.5 * beta * m ** 2 * (1 / lbar).sum(), rel=1e-10)
+    t = tau[0].numpy()
+    assert t[0] == pytest.approx(beta * m / lbar[0], rel=1e-10)
+    assert t[-1] == pytest.approx(-beta * m / lbar[-1], rel=1e-10)
+    np.testing.assert_allclose(t[1:-1], beta * m * (1 / lbar[1:] - 1 / lbar[:-1]), atol=1e-12 * beta * m / l)
+    assert float(F.abs().max()) < 1e-10
+
+
+# ---------------------------------------------------------------------- P2 derivatives
+
+def test_force_matches_central_differences_of_energy():
+    rng = np.random.default_rng(0)
+    x = straight(7, 0.3) + rng.normal(scale=0.01, size=(7, 3))
+    p, sim = make([straight(7, 0.3)], x0=[x], theta0=rng.normal(scale=0.3, size=6),
+                  K=1e5, E=1e6, G=4e5)
+    G, S = sim.groups[0], sim.state[0]
+    U0, F, tau = energy_forces(sim)
+    h = 1e-6
+
+    def U_at(xx, tt):
+        return float(elastic_energy(xx, tt, S["tb"], S["d1b"], S["mprev"], S["kbar"], G["R"], False))
+
+    for (i, k) in [(0, 0), (2, 1), (3, 2), (6, 0)]:
+        xp, xm = S["x"].clone(), S["x"].clone()
+        xp[0, i, k] += h
+        xm[0, i, k] -= h
+        fd = -(U_at(xp, S["theta"]) - U_at(xm, S["theta"])) / (2 * h)
+        assert fd == pytest.approx(float(F[0, i, k]), rel=1e-6, abs=1e-9)
+    for j in [0, 3, 5]:
+        tp, tm = S["theta"].clone(), S["theta"].clone()
+        tp[0, j] += h
+        tm[0, j] -= h
+        fd = -(U_at(S["x"], tp) - U_at(S["x"], tm)) / (2 * h)
+        assert fd == pytest.approx(float(tau[0, j]), rel=1e-6, abs=1e-12)
+
+
+# ---------------------------------------------------------------------- P3 invariance
+
+def rand_rot(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, a, b, c = q
+    return np.array([[1 - 2 * (b * b + c * c), 2 * (a * b - c * w), 2 * (a * c + b * w)],
+                     [2 * (a * b + c * w), 1 - 2 * (a * a + c * c), 2 * (b * c - a * w)],
+                     [2 * (a * c - b * w), 2 * (b * c + a * w), 1 - 2 * (a * a + b * b)]])
+
+
+@pytest.mark.parametrize("closed", [False, True])
+def test_rigid_motion_invariance_and_balance(closed):
+    rng = np.random.default_rng(1)
+    n = 14
+    if closed:
+        ang = np.arange(n) * 2 * math.pi / n
+        x = np.stack([0.1 * np.cos(ang), 0.1 * np.sin(ang), 0.02 * np.sin(3 * ang)], 1)
+    else:
+        x = straight(n, 0.4) + rng.normal(scale=0.02, size=(n, 3))
+    E = n if closed else n - 1
+    p, sim = make([x], closed=[closed], theta0=rng.normal(scale=0.2, size=E),
+                  K=1e5, E=1e6, G=4e5, plastic=True, yield_curv=1.0)
+    sim.state[0]["kbar"] = sim.state[0]["kbar"] + torch.as_tensor(rng.normal(scale=0.05, size=sim.state[0]["kbar"].shape))
+    U0, F, tau = energy_forces(sim)
+    # net force and net moment vanish (moment includes twist torques about each tangent)
+    assert float(F.sum(1).abs().max()) < 1e-10 * float(F.abs().max())
+    S = sim.state[0]
+    xs = S["x"][0]
+    t = unit(edges_of(S["x"], closed))[0]
+    M = torch.linalg.cross(xs, F[0], dim=-1).sum(0) + (tau[0][:, None] * t).sum(0)
+    assert float(M.abs().max()) < 1e-10 * float((xs.norm(dim=1).max() * F.abs().max()))
+    # rotate + translate the whole state: energy unchanged
+    Q = torch.as_tensor(rand_rot(rng))
+    c = torch.as_tensor(rng.normal(size=3))
+    st = sim.get_state(as_numpy=False)
+    rot = {k: v for k, v in st.items()}
+    rot["x"] = st["x"] @ Q.T + c
+    rot["tb"] = st["tb"] @ Q.T
+    rot["d1b"] = st["d1b"] @ Q.T
+    sim.set_full_state({k: v.numpy() for k, v in rot.items()})
+    U1, _, _ = energy_forces(sim)
+    assert float(U1) == pytest.approx(float(U0), rel=1e-12)
+
+
+# ---------------------------------------------------------------------- P4 Euler-Bernoulli statics
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_cantilever_static_balance(N):
+    """Euler-Bernoulli deflection w(s) = q s^2 (6L^2 - 4Ls + s^2) / (24 EI) of a clamped beam
+    under its own weight: the oracle's internal forces at interior vertices must balance
+    gravity, because the discrete bending force reproduces EI w'''' = q."""
+    L, E = 0.2, 1e9
+    EI = E * math.pi * R_ ** 4 / 4
+    q = RHO * A_ * 9.81
+    s = np.linspace(0, L, N)
+    w = q * s ** 2 * (6 * L ** 2 - 4 * L * s + s ** 2) / (24 * EI)
+    x = np.stack([s, np.zeros(N), 1.0 - w], 1)
+    pinned = np.zeros(N, bool)
+    pinned[:2] = True
+    p, sim = make([straight(N, L)], x0=[x], E=E, G=0.4 * E, inextensible=True, pinned=pinned)
+    _, F, _ = energy_forces(sim)
+    m = sim.groups[0]["R"]["mass"][0]
+    resid = (F[0, :, 2] - m * 9.81).numpy()
+    inner = slice(3, N - 3)
+    rel = np.abs(resid[inner]).max() / float(m[inner].max() * 9.81)
+    assert rel < 0.02, rel
+    # the tip deflection itself is the classical q L^4 / (8 EI)
+    assert w[-1] == pytest.approx(q * L ** 4 / (8 * EI), rel=1e-12)
+
+
+# ---------------------------------------------------------------------- P5 energy behaviour
+
+@pytest.mark.slow
+def test_energy_conservation_symplectic_euler():
+    n, L = 10, 0.3
+    x = straight(n, L)
+    pinned = np.zeros(n, bool)
+    pinned[0] = True
+    drift = []
+    for nmin in (10, 20):
+        p = inputs.custom([x], frames=60, K=1e6, E=1e5, G=4e4, damping=0.0, pinned=pinned,
+                          substeps_min=nmin)
+        p.theta0 = np.linspace(0, 0.5, n - 1)
+        sim = OracleSim(p)
+        sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+        e0 = sim.energies().sum()
+        hist = []
+        for f in range(60):
+            sim.step(p.actions[f:f + 1], 1)
+            hist.append(sim.energies().sum())
+        hist = np.array(hist)
+        scale = abs(sim.energies()[0, 2] - e0) + 1e-30
+        drift.append(np.abs(hist - e0).max())
+        # no secular drift: the last third stays within the band of the first two thirds
+        assert np.abs(hist[40:] - e0).max() < 2.0 * np.abs(hist[:40] - e0).max() + 1e-12
+    ratio = drift[0] / drift[1]
+    assert 1.4 < ratio < 2.8, ratio     # first-order: halving h halves the energy error
+
+
+# ---------------------------------------------------------------------- P6 inextensibility
+
+def test_inextensibility_single_edge_exact_and_momentum():
+    x = straight(2, 0.1)
+    p, sim = make([x], x0=[x * np.array([1.5, 1, 1])], inextensible=True, E=1e4)
+    G, S = sim.groups[0], sim.state[0]
+    xs = sim.inext_sweep(G, S["x"], G["colors"][0])
+    rest = float(np.linalg.norm(p.x_rest[1] - p.x_rest[0]))
+    assert float((xs[0, 1] - xs[0, 0]).norm()) == pytest.approx(rest, rel=1e-14)
+    m = G["R"]["mass"][0]
+    assert float(((xs[0] - S["x"][0]) * m[:, None]).sum(0).abs().max()) < 1e-18
+
+
+def test_inextensibility_residual_decreases_with_iterations():
+    rng = np.random.default_rng(3)
+    n = 20
+    x = straight(n, 0.5)
+    p, sim = make([x], x0=[x + rng.normal(scale=0.004, size=x.shape)], inextensible=True, E=1e4)
+    G, S = sim.groups[0], sim.state[0]
+    xs = S["x"]
+    eb = G["R"]["ebar"][0]
+    res = []
+    for it in range(8):
+        res.append(float(((edges_of(xs, False)[0].norm(dim=-1) - eb).abs() / eb).max()))
+        for col in G["colors"]:
+            xs = sim.inext_sweep(G, xs, col)
+    assert all(b < a for a, b in zip(res, res[1:])), res
+    m = G["R"]["mass"][0]
+    assert float(((xs[0] - S["x"][0]) * m[:, None]).sum(0).abs().max()) < 1e-16
+
+
+# ---------------------------------------------------------------------- P7 momentum in contact
+
+@pytest.mark.parametrize("inclined", [False, True])
+def test_momentum_conserved_through_self_contact(inclined):
+    """The paper reports a total momentum error of 1e-13 .. 1e-14 in 'parallel' and
+    'inclined' contact (App. C); an inverse-mass-weighted projection conserves it exactly."""
+    n = 30
+    l = 0.01
+    # hairpin: two arms joined by a half-turn; arms 3.5 mm apart (r = 2 mm, so they overlap)
+    arm = np.arange(12) * l
+    gap = 0.0035
+    a1 = np.stack([arm, np.zeros(12), np.zeros(12)], 1)
+    turn_ang = np.linspace(-math.pi / 2, math.pi / 2, 8)[1:-1]
+    rt = gap / 2
+    turn = np.stack([arm[-1] + 0.003 + rt * np.cos(turn_ang) * 0 + 0.004 * np.cos(turn_ang),
+                     rt + rt * np.sin(turn_ang), np.zeros(6)], 1)
+    a2 = a1[::-1] + np.array([0, gap, 0])
+    if inclined:
+        a2 = a2 + np.stack([np.zeros(12), np.zeros(12), np.linspace(0.004, -0.004, 12)], 1)
+    x = np.concatenate([a1, turn, a2])[:n]
+    rng = np.random.default_rng(5)
+    p = inputs.custom([x], frames=15, K=1e5, E=1e4, G=1e3, damping=0.0, gravity=0.0,
+                      self_contact=True)
+    p.v0 = rng.normal(scale=0.05, size=x.shape)
+    sim = OracleSim(p)
+    sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    P0 = sim.momentum()[0]
+    pairs = sim.candidates(sim.groups[0], sim.state[0]["x"])
+    assert pairs[0].shape[0] > 0
+    errs = []
+    for f in range(15):
+        sim.step(p.actions[f:f + 1], 1)
+        errs.append(np.abs(sim.momentum()[0] - P0).max())
+    assert max(errs) < 1e-13, errs
+
+
+# ---------------------------------------------------------------------- P8 plasticity
+
+def test_plastic_return_reaches_yield_surface():
+    n = 8
+    p, sim = make([straight(n, 0.3)], E=1e4, plastic=True, yield_curv=2.0, creep_rate=1.0)
+    G = sim.groups[0]
+    rng = np.random.default_rng(2)
+    kappa = torch.as_tensor(rng.normal(scale=0.07, size=(1, n - 2, 2)))
+    kbar = torch.zeros_like(kappa)
+    new = sim.plastic_update(G, kappa, kbar)
+    thr = (G["R"]["sy"][:, None] * G["R"]["lbar"]).numpy()[0]
+    el = (kappa - new).norm(dim=-1).numpy()[0]
+    yielded = kappa.norm(dim=-1).numpy()[0] > thr
+    assert yielded.any() and (~yielded).any()
+    np.testing.assert_allclose(el[yielded], thr[yielded], rtol=1e-12)
+    assert torch.equal(new[0, ~torch.as_tensor(yielded)], kbar[0, ~torch.as_tensor(yielded)])
+
+
+@pytest.mark.slow
+def test_bend_and_release_keeps_plastic_shape():
+    """A clamped wire sagging under its own weight past yield keeps a bent rest shape after
+    the load is removed (App. A.1: 'retain a new intrinsic shape'); an elastic one springs
+    back straight."""
+    n, L, F = 10, 0.3, 250
+    pinned = np.zeros(n, bool)
+    pinned[:2] = True
+    res = {}
+    for plastic in (False, True):
+        p = inputs.custom([straight(n, L)], frames=F, K=1e7, E=1e8, G=0.0, plastic=plastic,
+                          yield_curv=1.0, damping=20.0, pinned=pinned)
+        sim = OracleSim(p)
+        sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+        sim.step(p.actions, F)              # sag under gravity
+        loaded = 1.0 - sim.get_state()["x"][-1, 2]
+        sim.p.gravity = 0.0
+        sim.step(p.actions, F)              # remove the load, damp to rest
+        st = sim.get_state()
+        res[plastic] = (loaded, 1.0 - st["x"][-1, 2], np.abs(st["kbar"]).max())
+        sim.p.gravity = 9.81
+    assert res[False][2] == 0.0
+    assert res[False][1] < 0.05 * res[False][0]     # elastic rod springs back
+    assert res[True][1] > 0.3 * res[True][0]        # plastic rod keeps most of its sag
+    assert res[True][2] > 0.0
+
+
+# ---------------------------------------------------------------------- P9 loop holonomy
+
+def tantrix_area(t):
+    """Signed area of the spherical polygon t_0..t_{E-1} (fan triangulation, Van Oosterom &
+    Strackee solid angle of each triangle)."""
+    a = t[0]
+    tot = 0.0
+    for j in range(1, len(t) - 1):
+        b, c = t[j], t[j + 1]
+        num = a @ np.cross(b, c)
+        den = 1 + a @ b + b @ c + c @ a
+        tot += 2 * math.atan2(num, den)
+    return tot
+
+
+def test_planar_loop_has_no_holonomy():
+    N = 24
+    ang = np.arange(N) * 2 * math.pi / N
+    x = np.stack([0.1 * np.cos(ang) + 0.03 * np.cos(3 * ang), 0.1 * np.sin(ang), np.zeros(N)], 1)
+    _, _, psi = build_frames(torch.as_tensor(x)[None], True)
+    assert abs(float(psi)) < 1e-12
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_loop_holonomy_matches_tantrix_area_and_closes(seed):
+    rng = np.random.default_rng(seed)
+    N = 40
+    s = np.arange(N) * 2 * math.pi / N
+    c = rng.uniform(0.3, 1.0, 3)
+    x = np.stack([np.cos(s) + c[0] * np.cos(2 * s), np.sin(s) + c[1] * np.sin(3 * s), c[2] * np.sin(2 * s + 1)], 1) * 0.1
+    X = torch.as_tensor(x)[None]
+    t, d1, psi = build_frames(X, True)
+    area = tantrix_area(t[0].numpy())
+    # discrete Gauss-Bonnet: transport around the tangent indicatrix rotates a vector
+    # counter-clockwise by the (right-hand signed) area it encloses, modulo 2 pi
+    diff = (float(psi) - area + math.pi) % (2 * math.pi) - math.pi
+    assert abs(diff) < 1e-9, (float(psi), area)
+    # after the correction every hinge carries the same reference twist -psi/N_e
+    ta, tb = hinge_sides(t, True)
+    ra, rb = hinge_sides(d1, True)
+    ang = signed_angle(transport(ta, tb, ra), rb, tb)[0].numpy()
+    np.testing.assert_allclose(ang, -float(psi) / N, atol=1e-12)
+
+
+# ---------------------------------------------------------------------- P10 closest points
+
+def test_closest_points_brute_force():
+    rng = np.random.default_rng(4)
+    g = np.linspace(0, 1, 2001)
+    for trial in range(6):
+        P = rng.normal(size=(4, 3))
+        if trial == 5:                        # parallel segments
+            P[3] = P[2] + (P[1] - P[0]) * 0.7
+        p1, q1, p2, q2 = (torch.as_tensor(v) for v in P)
+        s, u = closest_params(p1, q1, p2, q2)
+        d = float(((p1 + s * (q1 - p1)) - (p2 + u * (q2 - p2))).norm())
+        A = P[0][None] + g[:, None] * (P[1] - P[0])[None]
+        Bp = P[2][None] + g[:, None] * (P[3] - P[2])[None]
+        # coarse grid minimum, then exact minimisation of the quadratic along each clamp face
+        D = np.linalg.norm(A[:, None] - Bp[None], axis=2)
+        i, j = np.unravel_index(D.argmin(), D.shape)
+        best = D[i, j]
+        assert d <= best + 1e-12
+        assert d == pytest.approx(best, abs=2e-6 * np.linalg.norm(P[1] - P[0]) + 2e-6 * np.linalg.norm(P[3] - P[2]))
+
+
+# ---------------------------------------------------------------------- P12 SDF primitives
+
+def test_box_and_capsule_sdf_against_sampling():
+    rng = np.random.default_rng(6)
+    c = np.array([0.1, -0.2, 0.05])
+    hl = np.array([0.15, 0.1, 0.05])
+    pts = c + rng.uniform(-2, 2, size=(200, 3)) * hl
+    sdf, n = sdf_box(torch.as_tensor(pts), torch.as_tensor(c), torch.as_tensor(hl))
+    # exact distance to the surface: nearest point on each of the six face rectangles
+    best = np.full(len(pts), np.inf)
+    for ax in range(3):
+        for sgn in (-1, 1):
+            q = np.clip(pts - c, -hl, hl)
+            q[:, ax] = sgn * hl[ax]
+            best = np.minimum(best, np.linalg.norm(pts - c - q, axis=1))
+    inside = np.all(np.abs(pts - c) < hl, axis=1)
+    np.testing.assert_allclose(np.abs(sdf.numpy()), best, atol=1e-14)
+    assert np.array_equal(sdf.numpy() < 0, inside)
+    # gradient = finite-difference gradient of the SDF
+    h = 1e-7
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fd = (sdf_box(torch.as_tensor(pts + e), torch.as_tensor(c), torch.as_tensor(hl))[0]
+              - sdf_box(torch.as_tensor(pts - e), torch.as_tensor(c), torch.as_tensor(hl))[0]) / (2 * h)
+        np.testing.assert_allclose(fd.numpy(), n[:, k].numpy(), atol=1e-6)
+    # capsule against sampling of its axis
+    a, b, rc = np.array([0.0, 0, 0]), np.array([0.0, 0, 0.04]), 0.01
+    axis = a + np.linspace(0, 1, 4001)[:, None] * (b - a)
+    q = rng.uniform(-0.05, 0.08, size=(100, 3))
+    sd, nn = sdf_capsule(torch.as_tensor(q), torch.as_tensor(a), torch.as_tensor(b), rc)
+    ref = np.linalg.norm(q[:, None] - axis[None], axis=2).min(1) - rc
+    np.testing.assert_allclose(sd.numpy(), ref, atol=1e-7)
+
+
+# ---------------------------------------------------------------------- rigid contact response
+
+def test_rigid_contact_removes_approach_and_applies_coulomb_friction():
+    """Vertex at the ground surface (d = 0, so f = 1) moving down and sideways: the normal
+    approach velocity is removed (restitution 0) and the tangential speed drops by mu times
+    the normal velocity change (Coulomb)."""
+    x = straight(3, 0.02, z=R_)
+    p = inputs.custom([x], K=1e5, E=1e4, planes=np.array([[0, 0, 1.0, 0.0]]))
+    sim = OracleSim(p)
+    sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    G, S = sim.groups[0], sim.state[0]
+    v = torch.zeros(1, 3, 3, dtype=F64)
+    v[0, :, 2] = -0.1
+    v[0, :, 0] = 0.2
+    out = sim.rigid_contact(G, S["x"], v, None, None, None, None)
+    np.testing.assert_allclose(out[0, :, 2].numpy(), 0.0, atol=1e-15)
+    np.testing.assert_allclose(out[0, :, 0].numpy(), 0.2 - 0.5 * 0.1, rtol=1e-12)
+    # far above the plane (f below 0.1) nothing changes
+    S2 = S["x"].clone()
+    S2[..., 2] = 0.05
+    out2 = sim.rigid_contact(G, S2, v, None, None, None, None)
+    assert torch.equal(out2, v)
+
+
+# ---------------------------------------------------------------------- substep count
+
+@pytest.mark.parametrize("mat", [dict(K=1e8, E=1e8, G=4e7), dict(K=1e5, E=1e4, G=1e3),
+                                 dict(K=1e4, E=1e8, G=4e3), dict(K=0.0, E=1e6, G=4e5, inextensible=True)])
+def test_substep_count_keeps_symplectic_euler_stable(mat):
+    """The per-rod substep count must put h * omega_max below the symplectic-Euler limit 2,
+    where omega_max is the largest natural frequency of the linearised rod (generalised
+    eigenvalues of the oracle energy's Hessian against the lumped masses and inertias)."""
+    assert OracleSim(inputs.plain(2)).nsub == [5]
+    n = 16
+    p, sim = make([straight(n, 0.05)], substeps_min=1, **mat)
+    G, S = sim.groups[0], sim.state[0]
+    R = G["R"]
+
+    def U(z):
+        x = z[: 3 * n].reshape(1, n, 3)
+        th = z[3 * n:].reshape(1, n - 1)
+        return elastic_energy(x, th, S["tb"], S["d1b"], S["mprev"], S["kbar"], R, False).sum()
+
+    z0 = torch.cat([S["x"].reshape(-1), S["theta"].reshape(-1)])
+    H = torch.autograd.functional.hessian(U, z0).numpy()
+    minv = np.concatenate([np.repeat(1.0 / R["mass"][0].numpy(), 3), 1.0 / R["inertia"][0].numpy()])
+    lam = np.linalg.eigvals(np.sqrt(minv)[:, None] * H * np.sqrt(minv)[None]).real.max()
+    h = 1e-3 / sim.nsub[0]
+    w = math.sqrt(max(lam, 0.0))
+    assert h * w < 2.0, (sim.nsub, h * w)
+    assert h * w > 0.3, (sim.nsub, h * w)
+
+
+# ---------------------------------------------------------------------- P14 rollout gradient
+
+@pytest.mark.slow
+def test_rollout_gradient_matches_central_differences():
+    """Autograd through the whole oracle rollout (forces, plasticity, gripper kinematics,
+    ground contact, inextensibility) against FP64 central differences, h = 1e-6."""
+    rng = np.random.default_rng(9)
+    n = 7
+    rods = [straight(n, 0.18, z=0.03) + rng.normal(scale=0.004, size=(n, 3)) for _ in range(2)]
+    acts = rng.normal(scale=0.002, size=(4, 2, 2, 6))
+    gp = np.stack([np.stack([r[2], r[4]]) for r in rods])
+    p = inputs.custom(rods, frames=4, actions=acts, n_grippers=[2, 2], grip_pos=gp,
+                      K=[1e5, 0.0], E=[2e3, 1e3], G=[1e2, 0.0], inextensible=[False, True],
+                      plastic=[True, False], yield_curv=[0.2, 0.0], damping=1.0,
+                      planes=np.array([[0, 0, 1.0, 0.0]]), grip_radius=0.004, grip_half_len=0.006)
+    target = rng.normal(size=(2 * n, 3))
+
+    def loss(x0, v0, th0, act, E, sy):
+        sim = OracleSim(p, params={"E": E, "yield_curv": sy})
+        sim.set_state(x0, v0, th0, torch.zeros_like(th0))
+        sim.step(act, 4, diff=True)
+        st = sim.get_state(as_numpy=False)
+        return (st["x"] * torch.as_tensor(target)).sum() + 0.1 * (st["theta"] ** 2).sum()
+
+    args = [torch.as_tensor(p.x0), torch.as_tensor(p.v0) + 0.01, torch.as_tensor(p.theta0) + 0.05,
+            torch.as_tensor(p.actions), torch.as_tensor(p.E), torch.as_tensor(p.yield_curv)]
+    leaves = [a.clone().requires_grad_(True) for a in args]
+    L = loss(*leaves)
+    grads = torch.autograd.grad(L, leaves)
+    h = 1e-6
+    picks = [(0, (3, 2)), (0, (9, 0)), (1, (4, 1)), (2, (2,)), (3, (1, 0, 1, 0)), (3, (2, 1, 0, 4)),
+             (4, (0,)), (5, (0,))]
+    scale = {4: 1e3, 5: 0.2}
+    for ai, idx in picks:
+        hh = h * scale.get(ai, 1.0)
+        ap = [a.clone() for a in args]
+        am = [a.clone() for a in args]
+        ap[ai][idx] += hh
+        am[ai][idx] -= hh
+        fd = (float(loss(*ap).detach()) - float(loss(*am).detach())) / (2 * hh)
+        g = float(grads[ai][idx])
+        assert g == pytest.approx(fd, rel=2e-4, abs=1e-8 * max(1.0, abs(fd))), (ai, idx, g, fd)
