@@ -1,0 +1,181 @@
+/*
+ * dlo.h -- C ABI of the GB300 batched differentiable discrete-elastic-rod stepper.
+ *
+ * The library steps many independent rods ("DLOs") forward in time and differentiates
+ * whole rollouts back through time.  The model is the one of DLO-Lab (arXiv 2606.04206):
+ * discrete elastic rods with stretching, bending and twisting energies and symplectic-Euler
+ * time stepping (Sec. 3.1, App. A.1), position-based inextensibility and self-collision
+ * projections with friction (App. A.1), bending plasticity with a yield threshold and a
+ * creep rate (App. A.1), soft SDF coupling to rigid planes, boxes and kinematic capsule
+ * grippers (Sec. 3.2), closed-loop holonomy frame initialisation (App. A.1) and gradient
+ * checkpointing over long horizons (Sec. 3.3).  Frame time and substeps follow App. B.1.
+ *
+ * Conventions
+ *   B          number of rods ("batch"); rod b has Nv[b] vertices and Ne[b] edges,
+ *              Ne = Nv-1 for open rods, Ne = Nv for closed loops.
+ *   V = sum Nv, Etot = sum Ne; rods are packed back to back (rod 0 first).
+ *   x   [V][4] float   positions (x, y, z, unused on input / inverse mass on output)
+ *   v   [V][4] float   velocities (vx, vy, vz, twist rate of the edge that starts at this
+ *                      vertex; unused for the last vertex of an open rod)
+ *   theta [Etot] float twist angle of each edge's material frame about its reference frame
+ *   actions [F][B][2][6] float  per frame, per rod, per gripper: translation increment
+ *                      (m) then rotation-vector increment (rad), both in world coordinates.
+ *   All device pointers must be 16-byte aligned where they hold float4 data.
+ *
+ * Ownership and ordering
+ *   The caller owns every pointer it passes.  Host arrays are read during the call only.
+ *   Device arrays must stay valid until the work enqueued on the context's stream has run.
+ *   The library's own workspace (state mirror, checkpoints, segment buffers, scratch) is
+ *   allocated through the caller's allocator (or cudaMalloc when none is given) and freed
+ *   by dlo_destroy.  All work is enqueued on the stream given at dlo_create and is
+ *   asynchronous; argument errors are returned at once, device-side errors (non-finite
+ *   state, pair-list overflow) are reported by the next call that synchronises
+ *   (dlo_get_state, dlo_backward, dlo_query).  No call throws or exits; a context is not
+ *   thread-safe.
+ */
+#ifndef DLO_H
+#define DLO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dlo_ctx dlo_ctx;
+
+typedef enum {
+    DLO_OK = 0,
+    DLO_ERR_INVALID_ARG = 1,   /* bad size, pointer, option or alignment */
+    DLO_ERR_CUDA = 2,          /* a CUDA call failed; dlo_last_error has the CUDA message */
+    DLO_ERR_OOM = 3,           /* the allocator returned NULL */
+    DLO_ERR_NONFINITE = 4,     /* a rod's state became NaN/Inf; dlo_last_error names the rod */
+    DLO_ERR_CAPACITY = 5,      /* self-contact pair list or checkpoint ring too small */
+    DLO_ERR_TIMEOUT = 6,       /* reserved: no device-side wait exists in this library */
+    DLO_ERR_STATE = 7          /* call out of order, e.g. dlo_backward without a rollout */
+} dlo_status;
+
+/* Per-rod material (App. A.1 energies; App. B Table "sim_params" gives the task values). */
+typedef struct {
+    float density;        /* kg/m^3 */
+    float radius;         /* m (uniform along the rod) */
+    float K_stretch;      /* stretching modulus K, Pa (k_s = K A); ignored if inextensible */
+    float E_bend;         /* bending modulus E, Pa (B = E A r^2 / 4) */
+    float G_twist;        /* twisting modulus G, Pa (beta = G A r^2 / 2); 0 = no twist energy */
+    int   inextensible;   /* 1: stretching energy off, edges projected to rest length */
+    float strain_limit;   /* >0: elastic stretching plus projection back into [1-s, 1+s] */
+    int   plastic;        /* 1: bending plasticity on */
+    float yield_curv;     /* sigma_y, 1/m (compared with |kappa_el| / lbar) */
+    float creep_rate;     /* r_c; 1 = return to the yield surface in one substep */
+    float damping;        /* c_d, 1/s: force -c_d m v and torque -c_d I omega */
+    int   closed;         /* 1: closed loop (edge Nv-1 joins vertex Nv-1 to vertex 0) */
+} dlo_material;
+
+/* Rigid scene shared by every rod (each rod is its own environment), plus per-rod grippers. */
+typedef struct {
+    int          n_planes;      /* <= 4 */
+    const float* planes;        /* host [n_planes][4]: unit normal n, offset o (n.x = o) */
+    int          n_boxes;       /* <= 4 */
+    const float* boxes;         /* host [n_boxes][6]: centre, half extents (axis aligned) */
+    const int*   n_grippers;    /* host [B] in 0..2, or NULL for none */
+    const float* grip_pose;     /* host [B][2][12]: position (3) then rotation matrix (3x3,
+                                   row major; column 2 is the capsule axis) at grasp time */
+    float        grip_radius;   /* capsule radius, m */
+    float        grip_half_len; /* capsule half length, m */
+    const unsigned char* pinned;/* host [V] 1 = vertex fixed in space, or NULL */
+} dlo_scene;
+
+typedef struct {
+    float  dt;              /* frame time, s (App. B.1: 1e-3) */
+    int    n_iter_pbd;      /* N_C projection iterations per substep (default 10) */
+    int    substeps_min;    /* minimum substeps per frame (App. B.1: 5) */
+    float  gravity;         /* m/s^2 along -z */
+    float  mu_self;         /* self-contact Coulomb coefficient */
+    float  mu_rigid;        /* rigid-contact Coulomb coefficient */
+    float  restitution;     /* rigid-contact restitution */
+    float  eps_soft;        /* softness eps_s as a multiple of the rod radius */
+    float  contact_margin;  /* self-contact candidate margin as a multiple of the radius */
+    int    self_contact;    /* 1: self-collision projections and friction on */
+    int    checkpoint_every;/* frames between rollout checkpoints; 0 = chosen by the library */
+    size_t hbm_budget;      /* bytes for checkpoints + backward buffers; 0 = 80 GiB */
+    int    warps_per_cta;   /* rods per CTA of the persistent kernels; 0 = autotune */
+} dlo_options;
+
+typedef struct {
+    void* (*alloc)(size_t bytes, void* user);  /* device memory, 256-byte aligned */
+    void  (*free)(void* ptr, void* user);
+    void* user;
+} dlo_allocator;
+
+/* Create a context.  n_verts[B] >= 2 and <= 256, mat[B], x_rest [V][3] host: the rest shape
+ * (rest lengths, masses and grasped vertices are taken from it; open rods rest straight,
+ * loops rest as a planar circle of the same length).  The state is set to the rest shape
+ * at rest.  cuda_stream may be NULL (legacy default stream).  alloc may be NULL. */
+dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, const dlo_material* mat,
+                      const float* x_rest, const dlo_scene* scene, const dlo_options* opt,
+                      const dlo_allocator* alloc, void* cuda_stream);
+
+/* Set a fresh state (device x [V][4], v [V][4], theta [Etot]).  Reference frames are rebuilt
+ * from x by space-parallel transport (loops: holonomy spread over the edges, App. A.1), rest
+ * curvatures and gripper poses are reset to their create-time values. */
+dlo_status dlo_set_state(dlo_ctx* ctx, const float* x, const float* v, const float* theta);
+
+/* Copy the state into caller-owned device buffers (any may be NULL).  Synchronises the
+ * stream and reports device-side errors. */
+dlo_status dlo_get_state(dlo_ctx* ctx, float* x, float* v, float* theta);
+
+/* Copy the full internal state into caller-owned device buffers (any may be NULL):
+ * ref [Etot][4] = (reference d1 xyz, theta), tan [Etot][4] = (tangent the reference frame
+ * is adapted to, unused), hinge [V][4] = (rest curvature 2, rest twist, reference twist)
+ * indexed by the hinge's vertex, grip [B][2][12] = current gripper poses. Synchronises. */
+dlo_status dlo_get_internal(dlo_ctx* ctx, float* ref, float* tan, float* hinge, float* grip);
+
+/* Arm recording of the next n_frames frames: checkpoints every K frames into the HBM ring
+ * and a copy of the actions, so that dlo_backward can differentiate the rollout. */
+dlo_status dlo_begin_rollout(dlo_ctx* ctx, int n_frames);
+
+/* Advance every rod by `frames` frames of dt with actions (device, [frames][B][2][6]; may be
+ * NULL = no gripper motion).  substeps > 0 forces that many substeps per frame for every rod;
+ * 0 uses each rod's own count (max(substeps_min, ceil(dt * omega_max))).  x_frames (device,
+ * [frames][V][4]) optionally receives the positions after every frame (may be NULL). */
+dlo_status dlo_step(dlo_ctx* ctx, const float* actions, int frames, int substeps, float* x_frames);
+
+/* The same rollout computed by the plain per-phase kernels (one launch per phase per
+ * substep, state in HBM, one thread per element): the speed comparator. Same arguments. */
+dlo_status dlo_step_plain(dlo_ctx* ctx, const float* actions, int frames, int substeps);
+
+/* Differentiate the recorded rollout.  Inputs (device, may be NULL = zero): dL/dx_T [V][4]
+ * (w ignored), dL/dv_T [V][4] (w = dL/d twist rate), dL/dtheta_T [Etot].  Outputs (device,
+ * may be NULL = not wanted): dL/dactions [F][B][2][6], dL/dmaterial [B][5] for
+ * (K_stretch, E_bend, G_twist, yield_curv, damping), dL/dx0 [V][4], dL/dv0 [V][4],
+ * dL/dtheta0 [Etot].  Gradients are with respect to the state set by dlo_set_state when the
+ * rollout started from it (reference frames rebuilt from x0), else with respect to the state
+ * at dlo_begin_rollout holding its reference frames fixed.  Synchronises. */
+dlo_status dlo_backward(dlo_ctx* ctx, const float* dL_dx_T, const float* dL_dv_T,
+                        const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
+                        float* dL_dx0, float* dL_dv0, float* dL_dtheta0);
+
+enum {
+    DLO_Q_SUBSTEPS = 1,      /* int [B]: substeps per frame of each rod */
+    DLO_Q_STATUS = 2,        /* unsigned [B]: status bits (1 non-finite, 2 pair overflow) */
+    DLO_Q_BYTES = 3,         /* size_t: device bytes held by the context */
+    DLO_Q_CONFIG = 4,        /* int [4]: warps per CTA, checkpoint interval, CTAs, smem/CTA */
+    DLO_Q_RESIDUAL = 5,      /* double [B]: sum |C_j| of the inextensibility constraints
+                                after the last frame, accumulated in FP64 */
+    DLO_Q_PAIRS = 6,         /* int [B]: self-contact candidate pairs in the last frame */
+    DLO_Q_LAUNCHES = 7,      /* long long: kernels launched by this context so far */
+    DLO_Q_MASS = 8           /* float [V][4]: (mass, inverse mass, kind, 0); kind 0 free,
+                                1 pinned, 2/3 grasped by gripper 0/1 (host out) */
+};
+
+/* Query (host `out`).  Synchronises. */
+dlo_status dlo_query(dlo_ctx* ctx, int what, void* out);
+
+const char* dlo_status_string(dlo_status s);
+const char* dlo_last_error(const dlo_ctx* ctx);
+void dlo_destroy(dlo_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DLO_H */

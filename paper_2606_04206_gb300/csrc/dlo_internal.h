@@ -1,0 +1,71 @@
+// dlo_internal.h -- device data layout shared by the C-ABI runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dlo {
+
+enum RodFlags : int {
+    ROD_INEXT = 1,       // stretching energy off, edges projected to rest length
+    ROD_PLASTIC = 2,     // bending plasticity
+    ROD_SLIMIT = 4,      // elastic stretching plus strain-limit projection
+    ROD_SELF = 8,        // self-contact on
+    ROD_CLOSED = 16
+};
+
+// One rod: offsets into the packed arrays and its per-rod constants (64 bytes).
+struct RodInfo {
+    int v0, nv, e0, ne;        // first vertex / edge, counts
+    int nsub, flags, ngrip, excl;
+    float h, kA, Bm, beta;     // substep, K A, E A r^2 / 4, G A r^2 / 2
+    float sy, rc, cd, radius;  // yield curvature, creep rate, damping, radius
+    float slim, contact_d, cell, eps;   // strain limit, candidate distance, hash cell, eps_s
+    int pair_cap, pair_off, pad0, pad1;
+};
+
+constexpr int kMaxPlanes = 4;
+constexpr int kMaxBoxes = 4;
+
+struct SceneDev {
+    int n_planes, n_boxes, n_iter, self_contact;
+    float4 planes[kMaxPlanes];     // (n, offset)
+    float4 box_c[kMaxBoxes];       // centre
+    float4 box_h[kMaxBoxes];       // half extents
+    float grip_r, grip_hl, gravity, dt;
+    float mu_self, mu_rigid, restitution, pad;
+};
+
+// State arrays of one snapshot (live state, or one checkpoint of the ring).
+struct StateRef {
+    float4* X;    // [V]    position, inverse mass
+    float4* Vl;   // [V]    velocity, twist rate of edge starting here
+    float4* ED;   // [Etot] reference d1 (base), theta
+    float4* ET;   // [Etot] tangent the base frame is adapted to, unused
+    float4* HG;   // [V]    rest curvature (2), rest twist, reference twist (hinge at vertex)
+    float* GP;    // [B][2][12] gripper position + rotation (row major)
+};
+
+struct FwdParams {
+    const RodInfo* rods;
+    const int* order;         // rods in decreasing cost
+    int n_order;
+    int* counter;             // work queue head (zeroed before the launch)
+    StateRef S;
+    const float4* KIN;        // [V] grasp offset (xyz), kind (0 free, 1 pinned, 2/3 gripper)
+    const float2* ES;         // [Etot] rest length, 1 / axial inertia
+    const float* actions;     // [frames][B][2][6] or null
+    float* xframes;           // [frames][V][4] or null
+    int frames, B, force_nsub, frame0;
+    long long nvert_total;
+    // checkpoint ring: snapshot c holds the state at the start of rollout frame c * ck_every
+    StateRef ck;
+    long long ck_strideV, ck_strideE, ck_strideB;
+    int ck_every, ck_count;
+    unsigned* status;         // [B] bit 1 non-finite, bit 2 pair overflow
+    double* residual;         // [B]
+    int* npairs;              // [B]
+    uint32_t* pairs_g;        // global spill of pair lists (unused when they fit in smem)
+    SceneDev scene;
+};
+
+}  // namespace dlo

@@ -1,0 +1,36 @@
+// dlo_kernels.h -- launch entry points of the device kernels (host side of each .cu file).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include "dlo_internal.h"
+
+namespace dlo {
+
+// Shared memory of one warp (one rod of at most NV vertices) in the persistent kernels:
+// ten float4 arrays of NV (positions, start positions, velocities, base frames + twist,
+// base tangents + rest lengths, hinge state, three per-hinge gradient slots, new reference
+// frames) and, with self-contact, 2 NV pair slots (two float4 of projection data each,
+// one packed index pair) plus an int4 fixed-point accumulator per vertex.
+__host__ __device__ constexpr size_t warp_smem_bytes(int NV, bool contact) {
+    return (size_t)(10 * NV) * 16 + (contact ? ((size_t)(4 * NV) * 16 + (size_t)NV * 16 + (size_t)(2 * NV) * 4) : 0);
+}
+
+cudaError_t launch_forward(const FwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
+int forward_blocks_per_sm(int nv_max, bool contact, int warps);
+
+struct InitParams {
+    const RodInfo* rods;
+    int B;
+    const float4* xin;       // [V][4] positions (w ignored)
+    const float4* vin;       // [V][4] or null
+    const float* thin;       // [Etot] or null
+    const float2* mass;      // [V] (mass, inverse mass)
+    const float2* ES;        // [Etot] (rest length, 1/inertia)
+    float4* rest;            // [V] rest hinge data (kbar0 x, kbar0 y, mbar, unused)
+    StateRef S;
+    const float* GP0;        // [B][2][12] initial gripper poses
+    int rest_mode;           // 1: compute the rest twist from xin into rest[].z only
+};
+cudaError_t launch_init(const InitParams& P, cudaStream_t st);
+
+}  // namespace dlo

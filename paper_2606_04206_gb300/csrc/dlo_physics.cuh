@@ -1,0 +1,295 @@
+// dlo_physics.cuh -- element functions of the discrete-elastic-rod step (device side).
+//
+// Model: DLO-Lab (arXiv 2606.04206) Sec. 3.1 / App. A.1.  Each function is a template on the
+// scalar type (float for the step, dualf for Jacobian-vector products in the adjoint).
+//
+// Energy of one hinge i (edges a = i-1, b = i), App. A.1:
+//   (kappa b)_i = 2 t^a x t^b / (1 + t^a . t^b)
+//   kappa_i     = 1/2 ( (kappa b).(d2^a + d2^b), (kappa b).(d1^a + d1^b) )
+//   m_i         = theta^b - theta^a + (reference twist)
+//   U_i = 1/2 (B/lbar) |kappa - kbar|^2 + 1/2 (beta/lbar) (m - mbar)^2
+// Stretching of one edge: U_j = 1/2 K A (|e|/|ebar| - 1)^2 |ebar|.
+// The reference frame of an edge is its stored base frame (t_base, d1_base) transported in
+// time to the current tangent and re-orthonormalised; the material frame is that frame
+// rotated by theta.  Forces are the exact gradient of U with respect to the vertex positions
+// (including the dependence of the transported reference frame on them); it is computed by
+// a hand-written reverse pass over the same expressions.
+#pragma once
+#include "dlo_vec.cuh"
+
+namespace dlo {
+
+constexpr float kTwoPi = 6.28318530717958647692f;
+
+DLO_HD double dsqrt(double a) { return sqrt(a); }
+
+// Parallel transport of d from unit tangent a to unit tangent b (rotation about a x b).
+template <class T>
+DLO_HD V3<T> transport(V3<T> a, V3<T> b, V3<T> d) {
+    T c = dot(a, b);
+    V3<T> k = cross(a, b);
+    return c * d + cross(k, d) + (dot(k, d) / (1.f + c)) * k;
+}
+DLO_HD V3<double> transport_d(V3<double> a, V3<double> b, V3<double> d) {
+    double c = dot(a, b);
+    V3<double> k = cross(a, b);
+    return c * d + cross(k, d) + (dot(k, d) / (1.0 + c)) * k;
+}
+
+// ------------------------------------------------------------------ edge frames
+template <class T>
+struct EdgeF {
+    V3<T> t, w0, d1r, d2r, d1, d2;
+    T ell, n1, c, s;
+};
+
+template <class T>
+DLO_HD void edge_forward(EdgeF<T>& E, V3<T> xa, V3<T> xb, V3<T> tb, V3<T> d1b, T th) {
+    V3<T> e = xb - xa;
+    E.ell = norm(e);
+    E.t = e / E.ell;
+    E.w0 = transport(tb, E.t, d1b);
+    V3<T> w1 = E.w0 - dot(E.w0, E.t) * E.t;
+    E.n1 = norm(w1);
+    E.d1r = w1 / E.n1;
+    E.d2r = cross(E.t, E.d1r);
+    E.c = dcos(th);
+    E.s = dsin(th);
+    E.d1 = E.c * E.d1r + E.s * E.d2r;
+    E.d2 = E.c * E.d2r - E.s * E.d1r;
+}
+
+// Reverse of edge_forward: given adjoints of t and d1r (and of |e|), the adjoint of the edge
+// vector e = xb - xa; with BASE also the adjoints of the base frame (tb, d1b).
+template <class T, bool BASE>
+DLO_HD V3<T> edge_reverse(const EdgeF<T>& E, V3<T> tb, V3<T> d1b, V3<T> gt, V3<T> gd1r, T gell,
+                          V3<T>* gtb, V3<T>* gd1b) {
+    V3<T> gw1 = (gd1r - dot(gd1r, E.d1r) * E.d1r) / E.n1;
+    T w0t = dot(E.w0, E.t);
+    T gw1t = dot(gw1, E.t);
+    V3<T> gw0 = gw1 - gw1t * E.t;
+    gt -= gw1t * E.w0 + w0t * gw1;
+    T cp = dot(tb, E.t);
+    V3<T> k = cross(tb, E.t);
+    T kd = dot(k, d1b);
+    T opc = 1.f + cp;
+    T gkk = dot(gw0, k);
+    T gcp = dot(gw0, d1b) - kd * gkk / (opc * opc);
+    V3<T> gk = cross(d1b, gw0) + (kd / opc) * gw0 + (gkk / opc) * d1b;
+    gt += gcp * tb + cross(gk, tb);
+    if (BASE) {
+        *gd1b = cp * gw0 + cross(gw0, k) + (gkk / opc) * k;
+        *gtb = gcp * E.t + cross(E.t, gk);
+    }
+    return (gt - dot(gt, E.t) * E.t) / E.ell + gell * E.t;
+}
+
+// ------------------------------------------------------------------ hinge
+template <class T>
+struct HingeF {
+    EdgeF<T> a, b;
+    V3<T> X, kb, u;
+    T cc, y, xq, mref, m, k0, k1;
+};
+
+template <class T>
+DLO_HD void hinge_forward(HingeF<T>& H, V3<T> xm, V3<T> xi, V3<T> xp, V3<T> tba, V3<T> d1ba,
+                          V3<T> tbb, V3<T> d1bb, T tha, T thb, T mprev) {
+    edge_forward(H.a, xm, xi, tba, d1ba, tha);
+    edge_forward(H.b, xi, xp, tbb, d1bb, thb);
+    H.cc = 1.f + dot(H.a.t, H.b.t);
+    H.X = cross(H.a.t, H.b.t);
+    H.kb = (2.f / H.cc) * H.X;
+    H.k0 = 0.5f * dot(H.kb, H.a.d2 + H.b.d2);
+    H.k1 = 0.5f * dot(H.kb, H.a.d1 + H.b.d1);
+    // reference twist: angle about t^b from the space-transported d1r^a to d1r^b
+    H.u = (H.cc - 1.f) * H.a.d1r + cross(H.X, H.a.d1r) + (dot(H.X, H.a.d1r) / H.cc) * H.X;
+    H.y = dot(cross(H.u, H.b.d1r), H.b.t);
+    H.xq = dot(H.u, H.b.d1r);
+    T ang = datan2(H.y, H.xq);
+    float wr = rintf((vof(ang) - vof(mprev)) / kTwoPi);
+    H.mref = mprev + ((ang - mprev) - kTwoPi * wr);
+    H.m = thb - tha + H.mref;
+}
+
+// Reverse of hinge_forward from seeds on kappa (gk0, gk1), on the total twist m (gmt, flows
+// to theta and the reference twist) and on the reference twist alone (gmr).  Returns the
+// adjoints of the three vertices and the two twist angles; with BASE also of both base frames.
+template <class T, bool BASE>
+DLO_HD void hinge_reverse(const HingeF<T>& H, V3<T> tba, V3<T> d1ba, V3<T> tbb, V3<T> d1bb,
+                          T gk0, T gk1, T gmt, T gmr, V3<T>& gxm, V3<T>& gxi, V3<T>& gxp,
+                          T& gtha, T& gthb, V3<T>* gtba, V3<T>* gd1ba, V3<T>* gtbb,
+                          V3<T>* gd1bb) {
+    const EdgeF<T>& A = H.a;
+    const EdgeF<T>& B = H.b;
+    T hk0 = 0.5f * gk0, hk1 = 0.5f * gk1;
+    V3<T> gkb = hk0 * (A.d2 + B.d2) + hk1 * (A.d1 + B.d1);
+    V3<T> gd2 = hk0 * H.kb;      // same for both edges
+    V3<T> gd1 = hk1 * H.kb;
+    V3<T> gX = (2.f / H.cc) * gkb;
+    T gcc = -dot(gkb, H.kb) / H.cc;
+    // twist
+    T gang = gmt + gmr;
+    gtha = -gmt;
+    gthb = gmt;
+    T r2 = H.y * H.y + H.xq * H.xq;
+    T gy = gang * H.xq / r2;
+    T gxq = -(gang * H.y) / r2;
+    V3<T> gu = gy * cross(B.d1r, B.t) + gxq * B.d1r;
+    V3<T> gd1rb = gy * cross(B.t, H.u) + gxq * H.u;
+    V3<T> gtb_ = gy * cross(H.u, B.d1r);
+    T Xd = dot(H.X, A.d1r);
+    T gux = dot(gu, H.X);
+    gcc += dot(gu, A.d1r) - Xd * gux / (H.cc * H.cc);
+    V3<T> gd1ra = (H.cc - 1.f) * gu + cross(gu, H.X) + (gux / H.cc) * H.X;
+    gX += cross(A.d1r, gu) + (Xd / H.cc) * gu + (gux / H.cc) * A.d1r;
+    V3<T> gta = gcc * B.t + cross(B.t, gX);
+    gtb_ += gcc * A.t + cross(gX, A.t);
+    // material frames -> reference frames and twist angles
+    {
+        gd1ra += A.c * gd1 - A.s * gd2;
+        V3<T> gd2r = A.s * gd1 + A.c * gd2;
+        gtha += dot(gd1, A.d2) - dot(gd2, A.d1);
+        gta += cross(A.d1r, gd2r);
+        gd1ra += cross(gd2r, A.t);
+    }
+    {
+        gd1rb += B.c * gd1 - B.s * gd2;
+        V3<T> gd2r = B.s * gd1 + B.c * gd2;
+        gthb += dot(gd1, B.d2) - dot(gd2, B.d1);
+        gtb_ += cross(B.d1r, gd2r);
+        gd1rb += cross(gd2r, B.t);
+    }
+    T zero = cst<T>(0.f);
+    V3<T> gea = edge_reverse<T, BASE>(A, tba, d1ba, gta, gd1ra, zero, gtba, gd1ba);
+    V3<T> geb = edge_reverse<T, BASE>(B, tbb, d1bb, gtb_, gd1rb, zero, gtbb, gd1bb);
+    gxm = -gea;
+    gxi = gea - geb;
+    gxp = geb;
+}
+
+// ------------------------------------------------------------------ plasticity (App. A.1)
+// kappa_el = kappa - kbar; if |kappa_el| > sigma_y lbar: kbar += r_c (|k_el| - y)/|k_el| k_el.
+DLO_HD bool plastic_update(float k0, float k1, float& kb0, float& kb1, float thr, float rc) {
+    float e0 = k0 - kb0, e1 = k1 - kb1;
+    float n2 = e0 * e0 + e1 * e1;
+    if (!(n2 > 0.f)) return false;
+    float n = sqrtf(n2);
+    if (!(n > thr)) return false;
+    float g = rc * (n - thr) / n;
+    kb0 = kb0 + g * e0;
+    kb1 = kb1 + g * e1;
+    return true;
+}
+
+// ------------------------------------------------------------------ rigid SDF primitives
+template <class T>
+DLO_HD T sdf_box(V3<T> x, V3<float> c, V3<float> hl, V3<T>& n) {
+    V3<T> p = x - mk3(cst<T>(c.x), cst<T>(c.y), cst<T>(c.z));
+    float sx = vof(p.x) >= 0.f ? 1.f : -1.f, sy = vof(p.y) >= 0.f ? 1.f : -1.f,
+          sz = vof(p.z) >= 0.f ? 1.f : -1.f;
+    T qx = sx * p.x - hl.x, qy = sy * p.y - hl.y, qz = sz * p.z - hl.z;
+    T ox = vof(qx) > 0.f ? qx : cst<T>(0.f), oy = vof(qy) > 0.f ? qy : cst<T>(0.f),
+      oz = vof(qz) > 0.f ? qz : cst<T>(0.f);
+    T ol2 = ox * ox + oy * oy + oz * oz;
+    if (vof(ol2) > 0.f) {
+        T ol = dsqrt(ol2);
+        n = mk3(sx * ox / ol, sy * oy / ol, sz * oz / ol);
+        return ol;
+    }
+    // inside: the largest (least negative) q, first index on ties
+    int k = 0;
+    T qm = qx;
+    if (vof(qy) > vof(qm)) { k = 1; qm = qy; }
+    if (vof(qz) > vof(qm)) { k = 2; qm = qz; }
+    n = mk3(cst<T>(k == 0 ? sx : 0.f), cst<T>(k == 1 ? sy : 0.f), cst<T>(k == 2 ? sz : 0.f));
+    return qm;
+}
+
+template <class T>
+DLO_HD T sdf_capsule(V3<T> x, V3<T> a, V3<T> b, float rc, V3<T>& n) {
+    V3<T> ab = b - a;
+    T s = dclamp(dot(x - a, ab) / dot(ab, ab), 0.f, 1.f);
+    V3<T> dv = x - (a + s * ab);
+    T d2 = dot(dv, dv);
+    if (!(vof(d2) > 0.f)) {
+        n = zero3<T>();
+        return cst<T>(-rc);
+    }
+    T d = dsqrt(d2);
+    n = dv / d;
+    return d - rc;
+}
+
+// Soft coupling (Sec. 3.2): d = r - SDF, f = min(exp(d / eps_s), 1); if f > 0.1 the relative
+// velocity's normal part gets restitution and its tangential part Coulomb friction, and the
+// result is blended in with weight f.
+template <class T>
+DLO_HD V3<T> contact_respond(V3<T> v, T sdf, V3<T> n, V3<T> vrig, float r, float eps_s,
+                             float mu, float rest, bool& act) {
+    T f = dexp((r - sdf) / eps_s);
+    if (vof(f) > 1.f) f = cst<T>(1.f);
+    act = vof(f) > 0.1f;
+    if (!act) return v;
+    V3<T> vr = v - vrig;
+    T vn = dot(vr, n);
+    V3<T> vt = vr - vn * n;
+    T vn2 = dmax(vn, (-rest) * vn);
+    T dvn = vn2 - vn;
+    T vt2 = dot(vt, vt);
+    T sc = cst<T>(1.f);
+    if (vof(vt2) > 1e-24f) sc = dmax(1.f - mu * dvn / dsqrt(vt2), cst<T>(0.f));
+    V3<T> vr2 = vn2 * n + sc * vt;
+    return v + f * (vr2 - vr);
+}
+
+// ------------------------------------------------------------------ segment closest points
+// Clamped closed-form closest points of segments p1q1 and p2q2 (Ericson, Real-Time Collision
+// Detection, Sec. 5.1.9); near-parallel segments take s = 0 and u clamped.
+template <class T>
+DLO_HD void closest_params(V3<T> p1, V3<T> q1, V3<T> p2, V3<T> q2, T& s, T& u) {
+    V3<T> d1 = q1 - p1, d2 = q2 - p2, r = p1 - p2;
+    T a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r), c = dot(d1, r), b = dot(d1, d2);
+    T den = a * e - b * b;
+    if (vof(den) <= 1e-6f * vof(a) * vof(e))
+        s = cst<T>(0.f);
+    else
+        s = dclamp((b * f - c * e) / den, 0.f, 1.f);
+    T uu = (b * s + f) / e;
+    if (vof(uu) < 0.f) {
+        s = dclamp((-c) / a, 0.f, 1.f);
+        u = cst<T>(0.f);
+    } else if (vof(uu) > 1.f) {
+        s = dclamp((b - c) / a, 0.f, 1.f);
+        u = cst<T>(1.f);
+    } else {
+        u = uu;
+    }
+}
+
+// One self-collision projection for an edge pair (App. A.1): the four position corrections.
+template <class T>
+DLO_HD bool pair_correction(V3<T> xa0, V3<T> xa1, V3<T> xb0, V3<T> xb1, float wa0, float wa1,
+                            float wb0, float wb1, float rsum, V3<T>* dx, T& s, T& u, V3<T>& n,
+                            T& d, T& W) {
+    closest_params(xa0, xa1, xb0, xb1, s, u);
+    V3<T> ca = xa0 + s * (xa1 - xa0);
+    V3<T> cb = xb0 + u * (xb1 - xb0);
+    V3<T> dv = ca - cb;
+    T d2 = dot(dv, dv);
+    T os = 1.f - s, ou = 1.f - u;
+    W = wa0 * os * os + wa1 * s * s + wb0 * ou * ou + wb1 * u * u;
+    if (!(vof(d2) > 1e-24f) || !(vof(W) > 0.f)) return false;
+    T dist = dsqrt(d2);
+    d = rsum - dist;
+    if (!(vof(d) > 0.f)) return false;
+    n = dv / dist;
+    T k = d / W;
+    dx[0] = (k * (wa0 * os)) * n;
+    dx[1] = (k * (wa1 * s)) * n;
+    dx[2] = (-(k * (wb0 * ou))) * n;
+    dx[3] = (-(k * (wb1 * u))) * n;
+    return true;
+}
+
+}  // namespace dlo

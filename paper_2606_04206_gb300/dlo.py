@@ -1,0 +1,323 @@
+"""ctypes binding of libdlo.so (include/dlo.h) plus a torch ``autograd.Function``.
+
+Argument marshalling only: every step of the simulation runs in the library's CUDA
+kernels.  PyTorch provides device memory (its caching allocator, passed to the library as
+``dlo_allocator``) and the CUDA stream.  There is no CPU fallback: if the library is
+missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libdlo.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "dlo.h")
+
+STATUS = {0: "DLO_OK", 1: "DLO_ERR_INVALID_ARG", 2: "DLO_ERR_CUDA", 3: "DLO_ERR_OOM", 4: "DLO_ERR_NONFINITE",
+          5: "DLO_ERR_CAPACITY", 6: "DLO_ERR_TIMEOUT", 7: "DLO_ERR_STATE"}
+Q_SUBSTEPS, Q_STATUS, Q_BYTES, Q_CONFIG, Q_RESIDUAL, Q_PAIRS, Q_LAUNCHES, Q_MASS = range(1, 9)
+N_MAT_GRAD = 5      # K_stretch, E_bend, G_twist, yield_curv, damping
+
+
+class DloError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Material(C.Structure):
+    _fields_ = [("density", C.c_float), ("radius", C.c_float), ("K_stretch", C.c_float), ("E_bend", C.c_float),
+                ("G_twist", C.c_float), ("inextensible", C.c_int), ("strain_limit", C.c_float),
+                ("plastic", C.c_int), ("yield_curv", C.c_float), ("creep_rate", C.c_float),
+                ("damping", C.c_float), ("closed", C.c_int)]
+
+
+class Scene(C.Structure):
+    _fields_ = [("n_planes", C.c_int), ("planes", C.POINTER(C.c_float)), ("n_boxes", C.c_int),
+                ("boxes", C.POINTER(C.c_float)), ("n_grippers", C.POINTER(C.c_int)),
+                ("grip_pose", C.POINTER(C.c_float)), ("grip_radius", C.c_float), ("grip_half_len", C.c_float),
+                ("pinned", C.POINTER(C.c_ubyte))]
+
+
+class Options(C.Structure):
+    _fields_ = [("dt", C.c_float), ("n_iter_pbd", C.c_int), ("substeps_min", C.c_int), ("gravity", C.c_float),
+                ("mu_self", C.c_float), ("mu_rigid", C.c_float), ("restitution", C.c_float),
+                ("eps_soft", C.c_float), ("contact_margin", C.c_float), ("self_contact", C.c_int),
+                ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t), ("warps_per_cta", C.c_int)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libdlo.so (built by ``paper_2606_04206_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libdlo.so not found at {p}: run paper_2606_04206_gb300.build.build() first")
+    lib = C.CDLL(p)
+    vp, fp, ip, st = C.c_void_p, C.POINTER(C.c_float), C.c_int, C.c_int
+    lib.dlo_create.argtypes = [C.POINTER(vp), ip, C.POINTER(C.c_int), C.POINTER(Material), fp, C.POINTER(Scene),
+                               C.POINTER(Options), C.POINTER(Allocator), vp]
+    lib.dlo_create.restype = st
+    lib.dlo_set_state.argtypes = [vp, vp, vp, vp]
+    lib.dlo_set_state.restype = st
+    lib.dlo_get_state.argtypes = [vp, vp, vp, vp]
+    lib.dlo_get_state.restype = st
+    lib.dlo_get_internal.argtypes = [vp, vp, vp, vp, vp]
+    lib.dlo_get_internal.restype = st
+    lib.dlo_begin_rollout.argtypes = [vp, ip]
+    lib.dlo_begin_rollout.restype = st
+    lib.dlo_step.argtypes = [vp, vp, ip, ip, vp]
+    lib.dlo_step.restype = st
+    lib.dlo_step_plain.argtypes = [vp, vp, ip, ip]
+    lib.dlo_step_plain.restype = st
+    lib.dlo_backward.argtypes = [vp] * 9
+    lib.dlo_backward.restype = st
+    lib.dlo_query.argtypes = [vp, ip, vp]
+    lib.dlo_query.restype = st
+    lib.dlo_status_string.argtypes = [st]
+    lib.dlo_status_string.restype = C.c_char_p
+    lib.dlo_last_error.argtypes = [vp]
+    lib.dlo_last_error.restype = C.c_char_p
+    lib.dlo_destroy.argtypes = [vp]
+    lib.dlo_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions the public header declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dlo_[a-z_]+)\s*\(", txt)))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def options_from(prob, **over) -> Options:
+    o = Options(dt=prob.dt, n_iter_pbd=prob.n_iter, substeps_min=prob.substeps_min, gravity=prob.gravity,
+                mu_self=prob.mu_self, mu_rigid=prob.mu_rigid, restitution=prob.restitution,
+                eps_soft=prob.eps_soft, contact_margin=prob.contact_margin, self_contact=int(prob.self_contact),
+                checkpoint_every=0, hbm_budget=0, warps_per_cta=0)
+    for k, v in over.items():
+        setattr(o, k, v)
+    return o
+
+
+class DloSim:
+    """One library context over the rods of a workload (``inputs.Problem``)."""
+
+    def __init__(self, prob, torch_alloc: bool = True, **opt):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.p = prob
+        self.B = prob.batch
+        self.V = int(prob.vert_off[-1])
+        self.E = int(prob.edge_off[-1])
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = torch.cuda.current_stream()
+        B = self.B
+        self._keep = []
+        mats = (Material * B)()
+        for b in range(B):
+            mats[b] = Material(prob.density[b], prob.radius[b], prob.K[b], prob.E[b], prob.G[b],
+                               int(prob.inextensible[b]), prob.strain_limit[b], int(prob.plastic[b]),
+                               prob.yield_curv[b], prob.creep_rate[b], prob.damping[b], int(prob.closed[b]))
+        nv = np.ascontiguousarray(prob.n_verts, np.int32)
+        xr = np.ascontiguousarray(prob.x_rest, np.float32)
+        planes = np.ascontiguousarray(prob.planes, np.float32).reshape(-1)
+        boxes = np.ascontiguousarray(prob.boxes, np.float32).reshape(-1)
+        ng = np.ascontiguousarray(prob.n_grippers, np.int32)
+        pose = np.zeros((B, 2, 12), np.float32)
+        pose[..., :3] = prob.grip_pos
+        pose[..., 3:] = np.asarray(prob.grip_rot).reshape(B, 2, 9)
+        pinned = np.ascontiguousarray(prob.pinned, np.uint8)
+        self._keep += [mats, nv, xr, planes, boxes, ng, pose, pinned]
+        scene = Scene(len(prob.planes), _fptr(planes) if len(planes) else None, len(prob.boxes),
+                      _fptr(boxes) if len(boxes) else None, ng.ctypes.data_as(C.POINTER(C.c_int)),
+                      _fptr(pose), prob.grip_radius, prob.grip_half_len,
+                      pinned.ctypes.data_as(C.POINTER(C.c_ubyte)))
+        self.options = options_from(prob, **opt)
+        alloc = None
+        if torch_alloc:
+            dev = self.device.index
+            stream = self.stream
+
+            def _alloc(n, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(n), dev, stream)
+                except Exception:
+                    return None
+
+            def _free(p, user):
+                torch.cuda.caching_allocator_delete(p)
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            alloc = Allocator(self._cb[0], self._cb[1], None)
+        ctx = C.c_void_p()
+        st = self.lib.dlo_create(C.byref(ctx), B, nv.ctypes.data_as(C.POINTER(C.c_int)), mats, _fptr(xr),
+                                 C.byref(scene), C.byref(self.options), C.byref(alloc) if alloc else None,
+                                 C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise DloError(st, "dlo_create failed")
+        self.ctx = ctx
+
+    # ------------------------------------------------------------------ helpers
+    def _check(self, st, what):
+        if st != 0:
+            raise DloError(st, f"{what}: {self.lib.dlo_last_error(self.ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.dlo_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tensors_from_problem(self, x=None, v=None, theta=None, omega=None):
+        """Device state tensors (x [V,4], v [V,4], theta [E]) from workload arrays."""
+        torch, p = self.torch, self.p
+        x = p.x0 if x is None else x
+        v = p.v0 if v is None else v
+        theta = p.theta0 if theta is None else theta
+        omega = p.omega0 if omega is None else omega
+        X = np.zeros((self.V, 4), np.float32)
+        X[:, :3] = x
+        Vv = np.zeros((self.V, 4), np.float32)
+        Vv[:, :3] = v
+        vo, eo = p.vert_off, p.edge_off
+        for b in range(self.B):
+            ne = eo[b + 1] - eo[b]
+            Vv[vo[b]:vo[b] + ne, 3] = omega[eo[b]:eo[b + 1]]
+        dev = self.device
+        return (torch.as_tensor(X, device=dev), torch.as_tensor(Vv, device=dev),
+                torch.as_tensor(np.asarray(theta, np.float32), device=dev))
+
+    # ------------------------------------------------------------------ API
+    def set_state(self, x, v, theta):
+        self._check(self.lib.dlo_set_state(self.ctx, _ptr(x), _ptr(v), _ptr(theta)), "dlo_set_state")
+
+    def reset(self):
+        self.set_state(*self.tensors_from_problem())
+
+    def get_state(self):
+        torch = self.torch
+        x = torch.empty(self.V, 4, device=self.device)
+        v = torch.empty(self.V, 4, device=self.device)
+        th = torch.empty(self.E, device=self.device)
+        self._check(self.lib.dlo_get_state(self.ctx, _ptr(x), _ptr(v), _ptr(th)), "dlo_get_state")
+        return x, v, th
+
+    def get_internal(self):
+        torch = self.torch
+        ref = torch.empty(self.E, 4, device=self.device)
+        tan = torch.empty(self.E, 4, device=self.device)
+        hinge = torch.empty(self.V, 4, device=self.device)
+        grip = torch.empty(self.B, 2, 12, device=self.device)
+        self._check(self.lib.dlo_get_internal(self.ctx, _ptr(ref), _ptr(tan), _ptr(hinge), _ptr(grip)),
+                    "dlo_get_internal")
+        return ref, tan, hinge, grip
+
+    def full_state_numpy(self):
+        """Every state array as float64 numpy in the oracle's layout."""
+        x, v, th = self.get_state()
+        ref, tan, hinge, grip = self.get_internal()
+        x, v, th, ref, tan, hinge, grip = (a.double().cpu().numpy() for a in (x, v, th, ref, tan, hinge, grip))
+        p = self.p
+        om = np.zeros(self.E)
+        vo, eo = p.vert_off, p.edge_off
+        for b in range(self.B):
+            ne = eo[b + 1] - eo[b]
+            om[eo[b]:eo[b + 1]] = v[vo[b]:vo[b] + ne, 3]
+        return dict(x=x[:, :3], v=v[:, :3], theta=th, omega=om, d1b=ref[:, :3], tb=tan[:, :3],
+                    kbar=hinge[:, :2], mprev=hinge[:, 3], mbar=hinge[:, 2], gp=grip[..., :3],
+                    gR=grip[..., 3:].reshape(self.B, 2, 3, 3))
+
+    def begin_rollout(self, n_frames):
+        self._check(self.lib.dlo_begin_rollout(self.ctx, int(n_frames)), "dlo_begin_rollout")
+        self._rollout_frames = int(n_frames)
+
+    def step(self, actions=None, frames=None, substeps=0, x_frames=None):
+        if frames is None:
+            frames = actions.shape[0]
+        if actions is not None:
+            assert actions.is_cuda and actions.dtype == self.torch.float32 and actions.is_contiguous()
+            assert actions.numel() >= frames * self.B * 12
+        self._check(self.lib.dlo_step(self.ctx, _ptr(actions), int(frames), int(substeps), _ptr(x_frames)),
+                    "dlo_step")
+
+    def step_plain(self, actions=None, frames=None, substeps=0):
+        if frames is None:
+            frames = actions.shape[0]
+        self._check(self.lib.dlo_step_plain(self.ctx, _ptr(actions), int(frames), int(substeps)), "dlo_step_plain")
+
+    def backward(self, dL_dx=None, dL_dv=None, dL_dtheta=None, want=("actions", "material", "x0", "v0", "theta0")):
+        torch = self.torch
+        n = getattr(self, "_rollout_frames", 0)
+        out = {}
+        if "actions" in want:
+            out["actions"] = torch.zeros(n, self.B, 2, 6, device=self.device)
+        if "material" in want:
+            out["material"] = torch.zeros(self.B, N_MAT_GRAD, device=self.device)
+        if "x0" in want:
+            out["x0"] = torch.zeros(self.V, 4, device=self.device)
+        if "v0" in want:
+            out["v0"] = torch.zeros(self.V, 4, device=self.device)
+        if "theta0" in want:
+            out["theta0"] = torch.zeros(self.E, device=self.device)
+        st = self.lib.dlo_backward(self.ctx, _ptr(dL_dx), _ptr(dL_dv), _ptr(dL_dtheta), _ptr(out.get("actions")),
+                                   _ptr(out.get("material")), _ptr(out.get("x0")), _ptr(out.get("v0")),
+                                   _ptr(out.get("theta0")))
+        self._check(st, "dlo_backward")
+        return out
+
+    def query(self, what):
+        if what == Q_SUBSTEPS:
+            o = (C.c_int * self.B)()
+        elif what == Q_STATUS:
+            o = (C.c_uint * self.B)()
+        elif what == Q_BYTES:
+            o = C.c_size_t()
+        elif what == Q_CONFIG:
+            o = (C.c_int * 4)()
+        elif what == Q_RESIDUAL:
+            o = (C.c_double * self.B)()
+        elif what == Q_PAIRS:
+            o = (C.c_int * self.B)()
+        elif what == Q_LAUNCHES:
+            o = C.c_longlong()
+        elif what == Q_MASS:
+            o = (C.c_float * (4 * self.V))()
+        else:
+            raise ValueError(what)
+        self._check(self.lib.dlo_query(self.ctx, what, C.byref(o)), "dlo_query")
+        if hasattr(o, "value"):
+            return o.value
+        a = np.ctypeslib.as_array(o).copy()
+        return a.reshape(self.V, 4) if what == Q_MASS else a

@@ -182,7 +182,8 @@ def _spline_rod(rng, n: int, length: float, radius: float, z_min: float = 0.08,
         x = c + (x - c) * (length / _length(x))
         x = _resample(x, n)
         x[:, 2] += max(0.0, z_min - x[:, 2].min())
-        if not _too_close(x, 4 * radius, 2, False):
+        skip = max(2, int(np.ceil(4 * radius * (n - 1) / length)) + 1)
+        if not _too_close(x, 4 * radius, skip, False):
             return x
     raise RuntimeError("could not draw a non-self-intersecting spline")
 

@@ -1,0 +1,103 @@
+// Host-side harness: compiles the device element functions of the stepper as host code so
+// the CPU test suite can check them against the FP64 oracle without a GPU.
+#include "dlo_physics.cuh"
+
+using namespace dlo;
+
+static V3<float> ld3(const float* p) { return V3<float>{p[0], p[1], p[2]}; }
+static void st3(float* p, V3<float> a) { p[0] = a.x; p[1] = a.y; p[2] = a.z; }
+
+// in: xm xi xp tba d1ba tbb d1bb (21) tha thb mprev kbar0 kbar1 mbar lbar Bm beta (9)
+// out: U, gxm(3), gxi(3), gxp(3), gtha, gthb, mref, k0, k1, m, d1ra(3), d1rb(3)
+extern "C" void hinge_grad_host(const float* in, float* out) {
+    HingeF<float> H;
+    V3<float> tba = ld3(in + 9), d1ba = ld3(in + 12), tbb = ld3(in + 15), d1bb = ld3(in + 18);
+    hinge_forward(H, ld3(in), ld3(in + 3), ld3(in + 6), tba, d1ba, tbb, d1bb, in[21], in[22], in[23]);
+    const float il = 1.f / in[27];
+    const float gk0 = in[28] * il * (H.k0 - in[24]), gk1 = in[28] * il * (H.k1 - in[25]);
+    const float gm = in[29] * il * (H.m - in[26]);
+    V3<float> gxm, gxi, gxp;
+    float gta, gtb;
+    hinge_reverse<float, false>(H, tba, d1ba, tbb, d1bb, gk0, gk1, gm, 0.f, gxm, gxi, gxp, gta, gtb, nullptr,
+                                nullptr, nullptr, nullptr);
+    out[0] = 0.5f * in[28] * il * ((H.k0 - in[24]) * (H.k0 - in[24]) + (H.k1 - in[25]) * (H.k1 - in[25])) +
+             0.5f * in[29] * il * (H.m - in[26]) * (H.m - in[26]);
+    st3(out + 1, gxm);
+    st3(out + 4, gxi);
+    st3(out + 7, gxp);
+    out[10] = gta;
+    out[11] = gtb;
+    out[12] = H.mref;
+    out[13] = H.k0;
+    out[14] = H.k1;
+    out[15] = H.m;
+    st3(out + 16, H.a.d1r);
+    st3(out + 19, H.b.d1r);
+}
+
+// Directional derivative of the full hinge gradient (all 30 inputs) along `dir` (30), by
+// running the same reverse pass on dual numbers.  out: 30 tangents of dU/d(input).
+extern "C" void hinge_hvp_host(const float* in, const float* dir, float* out) {
+    auto D3 = [&](int k) { return V3<dualf>{mkd(in[k], dir[k]), mkd(in[k + 1], dir[k + 1]), mkd(in[k + 2], dir[k + 2])}; };
+    auto D1 = [&](int k) { return mkd(in[k], dir[k]); };
+    HingeF<dualf> H;
+    V3<dualf> tba = D3(9), d1ba = D3(12), tbb = D3(15), d1bb = D3(18);
+    hinge_forward(H, D3(0), D3(3), D3(6), tba, d1ba, tbb, d1bb, D1(21), D1(22), D1(23));
+    dualf il = 1.f / D1(27);
+    dualf e0 = H.k0 - D1(24), e1 = H.k1 - D1(25), em = H.m - D1(26);
+    dualf gk0 = D1(28) * il * e0, gk1 = D1(28) * il * e1, gm = D1(29) * il * em;
+    V3<dualf> gxm, gxi, gxp, gtba, gd1ba, gtbb, gd1bb;
+    dualf gta, gtb;
+    hinge_reverse<dualf, true>(H, tba, d1ba, tbb, d1bb, gk0, gk1, gm, mkd(0.f), gxm, gxi, gxp, gta, gtb, &gtba, &gd1ba,
+                               &gtbb, &gd1bb);
+    V3<float> t;
+    t = ders(gxm); out[0] = t.x; out[1] = t.y; out[2] = t.z;
+    t = ders(gxi); out[3] = t.x; out[4] = t.y; out[5] = t.z;
+    t = ders(gxp); out[6] = t.x; out[7] = t.y; out[8] = t.z;
+    t = ders(gtba); out[9] = t.x; out[10] = t.y; out[11] = t.z;
+    t = ders(gd1ba); out[12] = t.x; out[13] = t.y; out[14] = t.z;
+    t = ders(gtbb); out[15] = t.x; out[16] = t.y; out[17] = t.z;
+    t = ders(gd1bb); out[18] = t.x; out[19] = t.y; out[20] = t.z;
+    out[21] = gta.d;
+    out[22] = gtb.d;
+    out[23] = 0.f;                                  // mprev: only through the wrap branch
+    out[24] = -gk0.d;                               // dU/dkbar = -gk
+    out[25] = -gk1.d;
+    out[26] = -gm.d;                                // dU/dmbar = -gm
+    dualf gl = -0.5f * (D1(28) * (e0 * e0 + e1 * e1) + D1(29) * em * em) * il * il;
+    out[27] = gl.d;
+    out[28] = (0.5f * il * (e0 * e0 + e1 * e1)).d;  // dU/dBm
+    out[29] = (0.5f * il * em * em).d;              // dU/dbeta
+}
+
+// in: x(3) v(3) vrig(3) sdf_kind (0 plane, 1 box, 2 capsule) params(9) r eps mu rest  out: v'(3), active
+extern "C" void contact_host(const float* in, float* out) {
+    V3<float> x = ld3(in), v = ld3(in + 3), vr = ld3(in + 6), n;
+    int kind = (int)in[9];
+    float sdf;
+    if (kind == 0) {
+        n = ld3(in + 10);
+        sdf = dot(x, n) - in[13];
+    } else if (kind == 1) {
+        sdf = sdf_box(x, ld3(in + 10), ld3(in + 13), n);
+    } else {
+        sdf = sdf_capsule(x, ld3(in + 10), ld3(in + 13), in[16], n);
+    }
+    bool act;
+    V3<float> o = contact_respond(v, sdf, n, vr, in[19], in[20], in[21], in[22], act);
+    st3(out, o);
+    out[3] = act ? 1.f : 0.f;
+    out[4] = sdf;
+}
+
+extern "C" void closest_host(const float* in, float* out) {
+    float s, u;
+    closest_params(ld3(in), ld3(in + 3), ld3(in + 6), ld3(in + 9), s, u);
+    out[0] = s;
+    out[1] = u;
+}
+
+extern "C" void expmap_host(const float* phi, float* R) {
+    M3 m = expmap(ld3(phi));
+    for (int k = 0; k < 9; ++k) R[k] = m.m[k];
+}

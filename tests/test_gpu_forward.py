@@ -1,0 +1,172 @@
+"""GPU forward path against the FP64 oracle, through the C ABI.
+
+Tolerances: vertex positions within 1e-5 m after 100 and 200 contact-free frames of the
+plain workload; with contact, the per-frame relative error ||x_gpu - x_oracle||_inf /
+||x_oracle||_inf <= 1e-5 from the same float32 state.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import OracleSim
+from paper_2606_04206_gb300 import inputs
+from gpu_util import sim_for, oracle_from_device_state, actions_dev, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+def test_plain_config_against_oracle_100_and_200_frames():
+    p = inputs.plain(200)
+    sim = sim_for(p)
+    sim.reset()
+    o = OracleSim(p)
+    o.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    acts = actions_dev(p)
+    for f0, f1 in ((0, 100), (100, 200)):
+        sim.step(acts[f0:f1].contiguous(), f1 - f0)
+        o.step(p.actions[f0:f1], f1 - f0)
+        x = sim.get_state()[0][:, :3].double().cpu().numpy()
+        err = np.abs(x - o.get_state()["x"]).max()
+        assert err <= 1e-5, (f1, err)
+
+
+@pytest.mark.parametrize("kind", ["batching", "selfcontact", "trajopt", "diff"])
+def test_initial_frames_constants_match_oracle(kind):
+    p = inputs.small_case(kind, n_rods=5, n=40, frames=2)
+    sim = sim_for(p)
+    sim.reset()
+    o = OracleSim(p)
+    o.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    ds, os_ = sim.full_state_numpy(), o.get_state()
+    for k, tol in (("tb", 1e-6), ("d1b", 1e-6), ("mprev", 2e-6), ("kbar", 1e-6), ("x", 0.0)):
+        assert np.abs(ds[k] - os_[k]).max() <= tol, k
+    oc = o.rod_constants()
+    assert np.array_equal(sim.query(1), np.asarray(oc["nsub"]))          # DLO_Q_SUBSTEPS
+    m = sim.query(8)
+    np.testing.assert_allclose(m[:, 0], oc["mass"], rtol=1e-6)
+    np.testing.assert_allclose(m[:, 1], oc["w"], rtol=1e-6)
+    assert np.array_equal(m[:, 2].astype(int), oc["kind"])
+
+
+@pytest.mark.parametrize("kind,warm", [("batching", 5), ("selfcontact", 5), ("trajopt", 20), ("diff", 5)])
+def test_one_frame_from_same_state_with_contact(kind, warm):
+    p = inputs.small_case(kind, n_rods=4, n=40, frames=warm + 1)
+    sim = sim_for(p)
+    sim.reset()
+    acts = actions_dev(p)
+    sim.step(acts[:warm].contiguous(), warm)
+    o = oracle_from_device_state(p, sim)
+    sim.step(acts[warm:warm + 1].contiguous(), 1)
+    o.step(p.actions[warm:warm + 1], 1)
+    fo = o.get_state()
+    fg = sim.full_state_numpy()
+    assert rel_inf(fg["x"], fo["x"]) <= 1e-5
+    # the frame's motion itself (a far stricter check than positions): velocities
+    assert rel_inf(fg["v"], fo["v"]) <= 2e-3
+    assert np.abs(fg["theta"] - fo["theta"]).max() <= 1e-4
+    assert np.abs(fg["kbar"] - fo["kbar"]).max() <= 1e-4
+
+
+def test_ragged_batch_all_size_classes():
+    p = inputs.batching(n_rods=8, frames=3, seed=11, vmin=16, vmax=256)
+    p.E[:] = inputs.f32(np.full(8, 2e4))          # keep substep counts small for the oracle
+    p.K[:] = p.E
+    p.G[:] = inputs.f32(0.4 * p.E)
+    sim = sim_for(p)
+    sim.reset()
+    acts = actions_dev(p)
+    sim.step(acts[:1].contiguous(), 1)
+    o = oracle_from_device_state(p, sim)
+    sim.step(acts[1:2].contiguous(), 1)
+    o.step(p.actions[1:2], 1)
+    assert rel_inf(sim.get_state()[0][:, :3].double().cpu().numpy(), o.get_state()["x"]) <= 1e-5
+
+
+def coils(n_rods=3, frames=3, n=48):
+    """Open rods wound 1.2 turns round a helix whose pitch (3.5 mm) is less than the contact
+    distance 2r = 4 mm, so the overlapping part of the coil is in self-contact."""
+    rods = []
+    for k in range(n_rods):
+        s = np.linspace(0.0, 2.4 * np.pi, n)
+        R = 0.05 + 0.005 * k
+        rods.append(np.stack([R * np.cos(s), R * np.sin(s), 0.05 + 0.0035 * s / (2 * np.pi)], 1))
+    return inputs.custom(rods, frames=frames, K=1e5, E=1e4, G=1e3, self_contact=True,
+                         planes=np.array([[0, 0, 1.0, 0.0]]))
+
+
+def test_self_contact_candidates_and_projection_match_oracle():
+    p = coils()
+    sim = sim_for(p)
+    sim.reset()
+    acts = actions_dev(p)
+    sim.step(acts[:1].contiguous(), 1)
+    o = oracle_from_device_state(p, sim)
+    sim.step(acts[1:2].contiguous(), 1)
+    got = sim.query(6)                            # pairs found by the hash at that frame start
+    for G, S in zip(o.groups, o.state):
+        cand = o.candidates(G, S["x"])
+        for i, b in enumerate(G["ids"]):
+            assert got[b] == cand[i].shape[0], (b, got[b], cand[i].shape[0])
+    assert got.min() > 0
+    o.step(p.actions[1:2], 1)
+    fg, fo = sim.full_state_numpy(), o.get_state()
+    assert rel_inf(fg["x"], fo["x"]) <= 1e-5
+    assert rel_inf(fg["v"], fo["v"]) <= 2e-3
+
+
+def test_self_contact_candidates_match_brute_force_on_knots():
+    p = inputs.small_case("selfcontact", n_rods=6, n=60, frames=3)
+    sim = sim_for(p)
+    sim.reset()
+    acts = actions_dev(p)
+    sim.step(acts[:2].contiguous(), 2)
+    o = oracle_from_device_state(p, sim)
+    sim.step(acts[2:3].contiguous(), 1)
+    got = sim.query(6)
+    for G, S in zip(o.groups, o.state):
+        cand = o.candidates(G, S["x"])
+        for i, b in enumerate(G["ids"]):
+            assert got[b] == cand[i].shape[0], (b, got[b], cand[i].shape[0])
+
+
+def test_bitwise_deterministic():
+    p = inputs.small_case("selfcontact", n_rods=4, n=40, frames=4)
+    outs = []
+    for _ in range(2):
+        sim = sim_for(p)
+        sim.reset()
+        sim.step(actions_dev(p), 4)
+        outs.append(sim.get_state()[0].cpu().numpy())
+        sim.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_edge_cases_two_vertex_rod_and_triangle_loop():
+    x2 = np.array([[0.0, 0, 0.5], [0.05, 0, 0.5]])
+    tri = np.array([[0.0, 0, 0.5], [0.05, 0, 0.5], [0.025, 0.04, 0.5]])
+    p = inputs.custom([x2, tri], closed=[False, True], frames=5, K=1e5, E=1e4, G=1e3,
+                      planes=np.array([[0, 0, 1.0, 0.0]]))
+    sim = sim_for(p)
+    sim.reset()
+    o = OracleSim(p)
+    o.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    sim.step(actions_dev(p), 5)
+    o.step(p.actions, 5)
+    assert np.abs(sim.get_state()[0][:, :3].double().cpu().numpy() - o.get_state()["x"]).max() <= 1e-6
+
+
+def test_zero_frames_and_nonfinite_detection():
+    from paper_2606_04206_gb300.dlo import DloError
+    p = inputs.small_case("trajopt", n_rods=3, n=24, frames=2)
+    sim = sim_for(p)
+    sim.reset()
+    x0 = sim.get_state()[0].clone()
+    sim.step(None, 0)
+    assert torch.equal(sim.get_state()[0], x0)
+    x, v, th = sim.tensors_from_problem()
+    v[5, 0] = float("nan")
+    sim.set_state(x, v, th)
+    sim.step(None, 1)
+    with pytest.raises(DloError) as ei:
+        sim.get_state()
+    assert ei.value.status == 4 and "rod 0" in str(ei.value)

@@ -1,0 +1,173 @@
+"""The CUDA element functions (compiled here as host code) against the FP64 oracle.
+
+The stepper's device math is written once as templates on the scalar type; this test
+compiles those templates for the host and compares each element with the oracle:
+hinge energy gradients (vs autograd of the oracle energy), second derivatives taken with
+dual numbers (vs double autograd), rigid-contact response, segment closest points, the
+exponential map.  It needs nvcc but no GPU."""
+import ctypes as C
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.dlo import edge_frames, hinge_strains, expmap, closest_params, sdf_box, sdf_capsule, OracleSim
+from paper_2606_04206_gb300 import build, inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def H():
+    out = os.path.join(tempfile.mkdtemp(), "libharness.so")
+    cmd = [build.nvcc(), "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr",
+           "-I", build.CSRC, os.path.join(HERE, "host_harness.cu"), "-o", out]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lib = C.CDLL(out)
+    for n in ("hinge_grad_host", "contact_host", "closest_host", "expmap_host"):
+        getattr(lib, n).argtypes = [C.c_void_p, C.c_void_p]
+    lib.hinge_hvp_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    return lib
+
+
+def fl(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def call(fn, *arrs, n_out):
+    out = np.zeros(n_out, np.float32)
+    fn(*[a.ctypes.data for a in arrs], out.ctypes.data)
+    return out
+
+
+def rand_hinge(rng):
+    x = np.cumsum(rng.normal(size=(3, 3)) * 0.02 + np.array([0.02, 0, 0]), axis=0)
+    # bases: previous tangents slightly rotated from the current ones, adapted d1
+    t = np.diff(x, axis=0)
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    tb = t + rng.normal(size=t.shape) * 0.05
+    tb /= np.linalg.norm(tb, axis=1, keepdims=True)
+    d = rng.normal(size=t.shape)
+    d -= (d * tb).sum(1, keepdims=True) * tb
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    th = rng.normal(size=2) * 0.4
+    return x, tb, d, th
+
+
+def oracle_hinge(x, tb, d, th, mprev, kbar, mbar, lbar, Bm, beta):
+    X = torch.tensor(x[None], requires_grad=True)
+    TH = torch.tensor(th[None], requires_grad=True)
+    t, ell, d1r, d1, d2 = edge_frames(X, TH, torch.tensor(tb[None]), torch.tensor(d[None]), False)
+    kap, mref, m = hinge_strains(t, d1r, d1, d2, TH, torch.tensor([[mprev]]), False)
+    U = 0.5 * Bm / lbar * ((kap - torch.tensor(kbar)) ** 2).sum() + 0.5 * beta / lbar * ((m - mbar) ** 2).sum()
+    gx, gth = torch.autograd.grad(U, [X, TH])
+    return float(U.detach()), gx[0].numpy(), gth[0].numpy(), kap.detach()[0, 0].numpy(), float(mref), d1r.detach()[0].numpy()
+
+
+def test_hinge_gradient_matches_oracle_autograd(H):
+    rng = np.random.default_rng(0)
+    for trial in range(20):
+        x, tb, d, th = rand_hinge(rng)
+        mprev = rng.normal() * 0.3
+        kbar = rng.normal(size=2) * 0.05
+        mbar, lbar, Bm, beta = rng.normal() * 0.1, 0.02, 3.0, 2.0
+        inp = fl(np.concatenate([x.ravel(), tb[0], d[0], tb[1], d[1], th, [mprev], kbar, [mbar, lbar, Bm, beta]]))
+        out = call(H.hinge_grad_host, inp, n_out=22)
+        U, gx, gth, kap, mref, d1r = oracle_hinge(x.astype(np.float64), tb, d, th, mprev, kbar, mbar, lbar, Bm, beta)
+        scale = np.abs(gx).max() + 1e-12
+        assert out[0] == pytest.approx(U, rel=2e-4, abs=1e-9)
+        np.testing.assert_allclose(out[1:10].reshape(3, 3), gx, atol=2e-4 * scale)
+        np.testing.assert_allclose(out[10:12], gth, atol=2e-4 * (np.abs(gth).max() + 1e-9))
+        np.testing.assert_allclose(out[13:15], kap, atol=2e-5)
+        assert out[12] == pytest.approx(mref, abs=2e-5)
+        np.testing.assert_allclose(out[16:22].reshape(2, 3), d1r, atol=2e-5)
+
+
+def test_hinge_second_derivatives_match_double_autograd(H):
+    """The adjoint's second-order pieces: directional derivatives of the hinge gradient with
+    respect to every input (positions, bases, twist, rest values, stiffnesses)."""
+    rng = np.random.default_rng(1)
+    for trial in range(10):
+        x, tb, d, th = rand_hinge(rng)
+        mprev = rng.normal() * 0.3
+        kbar = rng.normal(size=2) * 0.05
+        vals = np.concatenate([x.ravel(), tb[0], d[0], tb[1], d[1], th, [mprev], kbar,
+                               [rng.normal() * 0.1, 0.02, 3.0, 2.0]])
+        dirv = rng.normal(size=30)
+        dirv[23] = 0.0
+        out = call(H.hinge_hvp_host, fl(vals), fl(dirv), n_out=30)
+        z = torch.tensor(vals, requires_grad=True)
+
+        def U(z):
+            X = z[:9].reshape(1, 3, 3)
+            tb_ = torch.stack([z[9:12], z[15:18]])[None]
+            d_ = torch.stack([z[12:15], z[18:21]])[None]
+            TH = z[21:23][None]
+            t, ell, d1r, d1, d2 = edge_frames(X, TH, tb_, d_, False)
+            kap, mref, m = hinge_strains(t, d1r, d1, d2, TH, z[23:24][None], False)
+            return (0.5 * z[28] / z[27] * ((kap[0, 0] - z[24:26]) ** 2).sum()
+                    + 0.5 * z[29] / z[27] * (m[0, 0] - z[26]) ** 2)
+
+        g = torch.autograd.grad(U(z), z, create_graph=True)[0]
+        hv = torch.autograd.grad(g, z, torch.tensor(dirv))[0].numpy()
+        scale = np.abs(hv).max()
+        np.testing.assert_allclose(out, hv, atol=5e-4 * scale)
+
+
+def test_contact_response_matches_oracle(H):
+    rng = np.random.default_rng(2)
+    p = inputs.custom([np.array([[0, 0, 0.5], [0.01, 0, 0.5]])], K=1e5, E=1e4)
+    sim = OracleSim(p)
+    r, eps, mu = 0.002, 0.001, 0.5
+    for trial in range(60):
+        kind = trial % 3
+        x = rng.normal(size=3) * 0.004
+        v = rng.normal(size=3) * 0.3
+        vr = rng.normal(size=3) * 0.1 if kind == 2 else np.zeros(3)
+        if kind == 0:
+            n = np.array([0, 0, 1.0])
+            prm = np.concatenate([n, [rng.normal() * 0.002], np.zeros(5)])
+            sdf_o = float(x @ n - prm[3])
+            nrm = n
+        elif kind == 1:
+            c, hl = np.array([0, 0, -0.01]), np.array([0.02, 0.02, 0.01])
+            prm = np.concatenate([c, hl, np.zeros(3)])
+            s, nn = sdf_box(torch.tensor(x)[None], torch.tensor(c), torch.tensor(hl))
+            sdf_o, nrm = float(s[0]), nn[0].numpy()
+        else:
+            a, b = np.array([0, -0.01, -0.006]), np.array([0, 0.01, -0.006])
+            prm = np.concatenate([a, b, [0.004], np.zeros(2)])
+            s, nn = sdf_capsule(torch.tensor(x)[None], torch.tensor(a), torch.tensor(b), 0.004)
+            sdf_o, nrm = float(s[0]), nn[0].numpy()
+        inp = fl(np.concatenate([x, v, vr, [kind], prm, [r, eps, mu, 0.0]]))
+        out = call(H.contact_host, inp, n_out=5)
+        f = min(np.exp((r - sdf_o) / eps), 1.0)
+        vrel = v - vr
+        vn = vrel @ nrm
+        vt = vrel - vn * nrm
+        vn2 = max(vn, 0.0)
+        sc = max(1 - mu * (vn2 - vn) / np.linalg.norm(vt), 0.0)
+        expect = v + f * (vn2 * nrm + sc * vt - vrel) if f > 0.1 else v
+        assert out[4] == pytest.approx(sdf_o, abs=1e-6)
+        if abs(f - 0.1) > 1e-3:
+            assert bool(out[3]) == (f > 0.1)
+            np.testing.assert_allclose(out[:3], expect, atol=2e-5)
+
+
+def test_closest_points_and_expmap(H):
+    rng = np.random.default_rng(3)
+    for trial in range(50):
+        P = rng.normal(size=(4, 3))
+        if trial % 10 == 0:
+            P[3] = P[2] + (P[1] - P[0]) * 0.5
+        out = call(H.closest_host, fl(P.ravel()), n_out=2)
+        s, u = closest_params(*(torch.tensor(q) for q in P))
+        np.testing.assert_allclose(out, [float(s), float(u)], atol=1e-4)
+    for trial in range(20):
+        phi = rng.normal(size=3) * (10.0 ** rng.uniform(-6, 0))
+        out = call(H.expmap_host, fl(phi), n_out=9)
+        np.testing.assert_allclose(out.reshape(3, 3), expmap(torch.tensor(phi)).numpy(), atol=2e-7)
