@@ -276,14 +276,17 @@ class OracleSim:
 
     GRAD_PARAMS = ("K", "E", "G", "yield_curv", "damping")
 
-    def __init__(self, prob, params=None):
+    def __init__(self, prob, params=None, dtype=F64):
+        """``dtype`` is float64 for every reference result; float32 exists only to measure how
+        far a float32 evaluation of the same algorithm drifts from it (conditioning)."""
+        self.dtype = dtype
         self.p = prob
         B = prob.batch
         self.vo = np.concatenate([[0], np.cumsum(prob.n_verts)]).astype(np.int64)
         ne = prob.n_verts - 1 + prob.closed.astype(np.int64)
         self.eo = np.concatenate([[0], np.cumsum(ne)]).astype(np.int64)
         # material tensors; callers may pass leaf tensors to differentiate through them
-        self.mat = {k: torch.as_tensor(np.asarray(getattr(prob, k), np.float64)) for k in self.GRAD_PARAMS}
+        self.mat = {k: torch.as_tensor(np.asarray(getattr(prob, k), np.float64)).to(dtype) for k in self.GRAD_PARAMS}
         if params:
             self.mat.update(params)
         # rest lengths and substep counts per rod
@@ -305,7 +308,7 @@ class OracleSim:
     # ------------------------------------------------------------------ static per-group data
     def _group(self, ids, N, closed, nsub):
         p = self.p
-        t64 = lambda a: torch.as_tensor(np.asarray(a, np.float64))
+        t64 = lambda a: torch.as_tensor(np.asarray(a, np.float64)).to(self.dtype)
         G = dict(ids=ids, N=N, closed=closed, nsub=nsub, E=N - 1 + int(closed), H=N if closed else N - 2)
         r = t64(p.radius[ids])
         rho = t64(p.density[ids])
@@ -353,11 +356,11 @@ class OracleSim:
         # twist of the initial (rest) frames, so the rest state stores no twist energy)
         xr = t64(np.stack([p.x_rest[self.vo[b]:self.vo[b + 1]] for b in ids]))
         t0, d10, _ = build_frames(xr, closed)
-        zero = torch.zeros(len(ids), G["E"], dtype=F64)
+        zero = torch.zeros(len(ids), G["E"], dtype=self.dtype)
         _, _, d1r0, d1m0, d2m0 = edge_frames(xr, zero, t0, d10, closed)
-        _, mref0, m0 = hinge_strains(t0, d1r0, d1m0, d2m0, zero, torch.zeros(len(ids), G["H"], dtype=F64), closed)
+        _, mref0, m0 = hinge_strains(t0, d1r0, d1m0, d2m0, zero, torch.zeros(len(ids), G["H"], dtype=self.dtype), closed)
         R["mbar"] = m0
-        kb = torch.zeros(len(ids), G["H"], 2, dtype=F64)
+        kb = torch.zeros(len(ids), G["H"], 2, dtype=self.dtype)
         if closed:
             kb[..., 1] = 2.0 * math.tan(math.pi / G["E"])
         R["kbar0"] = kb
@@ -388,12 +391,13 @@ class OracleSim:
         """Initial state; reference frames rebuilt from x (space-parallel + holonomy)."""
         self.state = []
         for G in self.groups:
-            xs = self._split(x, G).to(F64)
+            dt = self.dtype
+            xs = self._split(x, G).to(dt)
             t, d1, _ = build_frames(xs, G["closed"])
-            th = self._split(theta, G, "e").to(F64)
-            S = dict(x=xs, v=self._split(v, G).to(F64), theta=th, omega=self._split(omega, G, "e").to(F64),
+            th = self._split(theta, G, "e").to(dt)
+            S = dict(x=xs, v=self._split(v, G).to(dt), theta=th, omega=self._split(omega, G, "e").to(dt),
                      tb=t, d1b=d1, kbar=G["R"]["kbar0"].clone(), gp=G["gpos0"].clone(), gR=G["grot0"].clone())
-            z = torch.zeros(len(G["ids"]), G["H"], dtype=F64)
+            z = torch.zeros(len(G["ids"]), G["H"], dtype=dt)
             _, _, d1r, d1m, d2m = edge_frames(xs, th, t, d1, G["closed"])
             # reading: the first reference twist is the plain signed angle (nothing to unwrap against)
             ra, rb = hinge_sides(d1r, G["closed"])
@@ -412,7 +416,7 @@ class OracleSim:
                      tb=self._split(st["tb"], G, "e"), d1b=self._split(st["d1b"], G, "e"),
                      mprev=hv(self._split(st["mprev"], G)), kbar=hv(self._split(st["kbar"], G)),
                      gp=torch.as_tensor(np.asarray(st["gp"])[ids]), gR=torch.as_tensor(np.asarray(st["gR"])[ids]))
-            self.state.append({k: v.to(F64) for k, v in S.items()})
+            self.state.append({k: v.to(self.dtype) for k, v in S.items()})
 
     def get_state(self, as_numpy=True):
         """Concatenated state in workload order.  Hinge arrays (mprev, kbar) are indexed by
@@ -443,7 +447,7 @@ class OracleSim:
     def step(self, actions, frames=None, diff=False):
         """Advance ``frames`` frames with per-frame gripper actions [F, B, 2, 6]."""
         act = torch.as_tensor(actions) if not torch.is_tensor(actions) else actions
-        act = act.to(F64)
+        act = act.to(self.dtype)
         frames = act.shape[0] if frames is None else frames
         for gi, G in enumerate(self.groups):
             S = self.state[gi]
@@ -484,7 +488,7 @@ class OracleSim:
             U = elastic_energy(x + dx, th + dth, S["tb"], S["d1b"], S["mprev"], kbar, R, closed)
             gx, gth = torch.autograd.grad(U.sum(), [dx, dth], create_graph=diff)
         # A4/A5: gravity, damping, symplectic Euler velocity update
-        grav = torch.tensor([0.0, 0.0, -p.gravity], dtype=F64)
+        grav = torch.tensor([0.0, 0.0, -p.gravity], dtype=self.dtype)
         w = R["w"][..., None]
         free = (G["kind"] == 0)[..., None]
         acc = -w * gx + grav - R["cd"][:, None, None] * v
@@ -564,11 +568,11 @@ class OracleSim:
         zero = torch.zeros_like(v)
         allm = torch.ones_like(free)
         for pl in p.planes:
-            n = torch.as_tensor(pl[:3], dtype=F64)
+            n = torch.as_tensor(pl[:3], dtype=self.dtype)
             sdf, nrm = sdf_plane(x, n, float(pl[3]))
             v = respond(v, sdf, nrm, zero, allm)
         for bx in p.boxes:
-            sdf, nrm = sdf_box(x, torch.as_tensor(bx[:3], dtype=F64), torch.as_tensor(bx[3:], dtype=F64))
+            sdf, nrm = sdf_box(x, torch.as_tensor(bx[:3], dtype=self.dtype), torch.as_tensor(bx[3:], dtype=self.dtype))
             v = respond(v, sdf, nrm, zero, allm)
         for g in range(2):
             on = (G["ngrip"] > g)

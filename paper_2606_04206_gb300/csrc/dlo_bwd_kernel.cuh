@@ -1,0 +1,754 @@
+// dlo_bwd_kernel.cuh -- hand-written adjoint of the rod stepper with gradient checkpointing.
+//
+// DLO-Lab (Sec. 3.3) differentiates whole trajectories by caching one state per segment and,
+// for each segment in reverse, re-running the forward simulation before back-propagating.
+// Here the checkpoints live in HBM (written by the forward kernel every K frames) and one warp
+// runs the whole backward of one rod:
+//   for each segment, last first: reload its checkpoint, recompute its frames storing the
+//   frame-start states (per-warp scratch); for each frame, last first: recompute it storing
+//   the substep-start states; for each substep, last first: recompute it once more recording
+//   its intermediates (velocity before contact, PBD iteration snapshots, displacement before
+//   friction), then apply the vector-Jacobian product of every phase in reverse order.
+// Second-order terms of the elastic forces are exact: the hinge gradient (a hand reverse pass)
+// is re-run on dual numbers, giving d/de [dU/dz](x + e lambda) for every input z, which is
+// the transpose-Jacobian product of the force (U's Hessian is symmetric).  Branches (contact
+// on/off, yield, strain-limit activity, pair sets) follow the recomputed forward.
+#pragma once
+#include "dlo_step.cuh"
+
+namespace dlo {
+
+__host__ __device__ constexpr size_t bwd_smem_bytes(int NV, bool contact) {
+    return warp_smem_bytes(NV, contact) + (size_t)(10 * NV) * 16;
+}
+
+// ------------------------------------------------------------------ small helpers
+__device__ __forceinline__ void atomic_add3(float4* a, V3<float> v) {
+    atomicAdd(&a->x, v.x);
+    atomicAdd(&a->y, v.y);
+    atomicAdd(&a->z, v.z);
+}
+
+// J_l(phi)^T lam for the left Jacobian of the rotation exponential:
+// exp([phi + d]x) ~ exp([J_l(phi) d]x) exp([phi]x),  J_l = I + A [phi]x + B [phi]x^2.
+__device__ __forceinline__ V3<float> jl_t(V3<float> phi, V3<float> lam) {
+    float t2 = dot(phi, phi), A, B;
+    if (t2 < 1e-8f) {
+        A = 0.5f - t2 / 24.f;
+        B = 1.f / 6.f - t2 / 120.f;
+    } else {
+        float t = sqrtf(t2), sh = sinf(0.5f * t);
+        A = 2.f * sh * sh / t2;
+        B = (t - sinf(t)) / (t2 * t);
+    }
+    V3<float> c = cross(phi, lam);
+    return lam - A * c + B * cross(phi, c);
+}
+
+// One rigid primitive acting on a vertex velocity (the k-th of planes, boxes, grippers).
+template <class T>
+__device__ __forceinline__ V3<T> prim_respond(int k, const SceneDev& sc, const RodInfo& R, V3<T> x, V3<T> v,
+                                              V3<T> gp, V3<T> gax, V3<T> vp, V3<T> w, bool& act) {
+    V3<T> n;
+    T sdf;
+    V3<T> vrig = zero3<T>();
+    if (k < sc.n_planes) {
+        n = mk3(cst<T>(sc.planes[k].x), cst<T>(sc.planes[k].y), cst<T>(sc.planes[k].z));
+        sdf = dot(x, n) - sc.planes[k].w;
+    } else if (k < sc.n_planes + sc.n_boxes) {
+        const int b = k - sc.n_planes;
+        sdf = sdf_box(x, f3(sc.box_c[b]), f3(sc.box_h[b]), n);
+    } else {
+        V3<T> a = gp - sc.grip_hl * gax, bb = gp + sc.grip_hl * gax;
+        sdf = sdf_capsule(x, a, bb, sc.grip_r, n);
+        vrig = vp + cross(w, x - gp);
+    }
+    return contact_respond(v, sdf, n, vrig, R.radius, R.eps, sc.mu_rigid, sc.restitution, act);
+}
+
+// Friction of one pair (App. A.1), as a function of the four positions at the first
+// projection and the four rebuilt velocities; returns whether the pair acts.
+template <class T>
+__device__ __forceinline__ bool fric_pair(const V3<T>* P, const V3<T>* Vv, const float* w, float rsum, float mu,
+                                          float h, V3<T>* dv) {
+    T s, u, d, W;
+    V3<T> n, dx[4];
+    if (!pair_correction(P[0], P[1], P[2], P[3], w[0], w[1], w[2], w[3], rsum, dx, s, u, n, d, W)) return false;
+    V3<T> vrel = (1.f - s) * Vv[0] + s * Vv[1] - (1.f - u) * Vv[2] - u * Vv[3];
+    V3<T> vt = vrel - dot(vrel, n) * n;
+    T vt2 = dot(vt, vt);
+    if (!(vof(vt2) > 1e-24f)) return false;
+    T coef = dmin(mu * d / (h * dsqrt(vt2)), cst<T>(1.f));
+    V3<T> dd = (-(coef / W)) * vt;
+    dv[0] = (w[0] * (1.f - s)) * dd;
+    dv[1] = (w[1] * s) * dd;
+    dv[2] = (-(w[2] * (1.f - u))) * dd;
+    dv[3] = (-(w[3] * u)) * dd;
+    return true;
+}
+
+template <int NV, bool CONTACT>
+struct AdjArrays {
+    float4 *LX, *LD, *LV, *LE, *LT, *LK, *LP0, *LG, *V1, *DF;
+    __device__ AdjArrays(float4* a) {
+        LX = a;
+        LD = a + NV;
+        LV = a + 2 * NV;
+        LE = a + 3 * NV;
+        LT = a + 4 * NV;
+        LK = a + 5 * NV;
+        LP0 = a + 6 * NV;
+        LG = a + 7 * NV;
+        V1 = a + 8 * NV;
+        DF = a + 9 * NV;
+    }
+};
+
+// State snapshot layout in the per-warp scratch: X[NV], V[NV], HG[NV], ED[NV], ET[NV].
+template <int NV, bool C>
+__device__ __forceinline__ void save_state(float4* dst, const RodInfo& R, int lane, const Smem<NV, C>& s) {
+    for (int i = lane; i < R.nv; i += 32) {
+        dst[i] = s.X0[i];
+        dst[NV + i] = s.V[i];
+        dst[2 * NV + i] = s.HG[i];
+    }
+    for (int j = lane; j < R.ne; j += 32) {
+        dst[3 * NV + j] = s.ED[j];
+        dst[4 * NV + j] = s.ET[j];
+    }
+}
+template <int NV, bool C>
+__device__ __forceinline__ void load_state(const float4* src, const RodInfo& R, int lane, Smem<NV, C>& s) {
+    for (int i = lane; i < R.nv; i += 32) {
+        float4 x = src[i];
+        s.X0[i] = x;
+        s.X[i] = x;
+        s.V[i] = src[NV + i];
+        s.HG[i] = src[2 * NV + i];
+    }
+    for (int j = lane; j < R.ne; j += 32) {
+        s.ED[j] = src[3 * NV + j];
+        s.ET[j] = src[4 * NV + j];
+    }
+    __syncwarp();
+}
+
+// Per-lane pose cotangents of one substep (two grippers x 3).
+struct PoseAdj {
+    float ps0[6], phs0[6], ps1[6], phs1[6], vp[6], w[6];
+    __device__ void zero() {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ps0[k] = phs0[k] = ps1[k] = phs1[k] = vp[k] = w[k] = 0.f;
+    }
+};
+__device__ __forceinline__ void add3(float* a, int q, V3<float> v) {
+    a[3 * q] += v.x;
+    a[3 * q + 1] += v.y;
+    a[3 * q + 2] += v.z;
+}
+__device__ __forceinline__ V3<float> get3(const float* a, int q) { return f3(a[3 * q], a[3 * q + 1], a[3 * q + 2]); }
+
+// ------------------------------------------------------------------ reverse of one substep
+// On entry the shared state holds S_n (the substep's start), the recorded intermediates and,
+// for a self-contact rod, the frame's pair list and the projection data of the first
+// iteration; the cotangent arrays hold the cotangents of S_{n+1}.  On exit they hold those
+// of S_n.  gm accumulates (kA, Bm, beta, sigma_y, c_d) cotangents, lpf/lphif the frame-start
+// pose cotangents and ga the frame's action cotangents (all per lane).
+template <int NV, bool CONTACT>
+__device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, CONTACT>& s,
+                                AdjArrays<NV, CONTACT>& a, const float4* SN, int lane, float h, const Pose& F0,
+                                const float* act, const M3* gR0, const M3* gR1, float c0, float c1, int np,
+                                double* gm, float* lpf, float* lphif, float* ga) {
+    const SceneDev& sc = P.scene;
+    const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
+    const bool closed = R.flags & ROD_CLOSED;
+    const int nh = closed ? nv : nv - 2;
+    const float ih = 1.f / h;
+    const bool lenc = R.flags & (ROD_INEXT | ROD_SLIMIT);
+    const float rsum = 2.f * R.radius;
+    PoseAdj pa;
+    pa.zero();
+    for (int i = lane; i < nv; i += 32) a.LP0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // ---- B1: positions at the substep end
+    for (int i = lane; i < nv; i += 32) {
+        const float4 kin = P.KIN[v0 + i];
+        const int kind = (int)kin.w;
+        float4 lx = a.LX[i];
+        if (kind >= 2) {
+            const int q = kind - 2;
+            V3<float> y1 = mul(gR1[q], f3(kin));
+            add3(pa.ps1, q, f3(lx));
+            add3(pa.phs1, q, cross(y1, f3(lx)));
+            a.LX[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.LD[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            a.LD[i] = make_float4(lx.x, lx.y, lx.z, 0.f);
+        }
+    }
+    __syncwarp();
+    // ---- B2: self-contact friction
+    if (CONTACT && np > 0) {
+        float4* T0 = s.ND;        // displacements at the first contact sweep
+        float4* LTMP = s.HB0;
+        for (int i = lane; i < nv; i += 32) {
+            T0[i] = SN[i];
+            LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        if (lenc) {
+            inext_color_arr(R, s.X0, T0, s.ET, lane, 0, closed);
+            inext_color_arr(R, s.X0, T0, s.ET, lane, 1, closed);
+            if (closed && (ne & 1)) inext_color_arr(R, s.X0, T0, s.ET, lane, 2, closed);
+        }
+        for (int p = lane; p < np; p += 32) {
+            if (!(s.fr1[p].w > 0.f)) continue;
+            uint32_t pr = s.pairs[p];
+            const int a0 = pr & 0xffff, q0 = pr >> 16;
+            const int idx[4] = {a0, (a0 + 1 == nv) ? 0 : a0 + 1, q0, (q0 + 1 == nv) ? 0 : q0 + 1};
+            const V3<float> o = f3(s.X0[a0]);
+            V3<float> Pf[4], Vf[4], lo[4];
+            float w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                Pf[k] = (k == 0) ? f3(T0[idx[0]]) : (f3(s.X0[idx[k]]) - o) + f3(T0[idx[k]]);
+                Vf[k] = ih * f3(a.DF[idx[k]]);
+                w[k] = s.X0[idx[k]].w;
+                lo[k] = f3(a.LV[idx[k]]);
+            }
+            float lin[24];
+#pragma unroll 1
+            for (int d = 0; d < 24; ++d) {
+                V3<dualf> Pd[4], Vd[4], dv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    V3<float> ep = zf3(), ev = zf3();
+                    if (d / 3 == k) (d % 3 == 0 ? ep.x : d % 3 == 1 ? ep.y : ep.z) = 1.f;
+                    if (d / 3 == 4 + k) (d % 3 == 0 ? ev.x : d % 3 == 1 ? ev.y : ev.z) = 1.f;
+                    Pd[k] = lift(Pf[k], ep);
+                    Vd[k] = lift(Vf[k], ev);
+                }
+                float acc = 0.f;
+                if (fric_pair(Pd, Vd, w, rsum, sc.mu_self, h, dv))
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) acc += dot(ders(dv[k]), lo[k]);
+                lin[d] = acc;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                atomic_add3(&a.LP0[idx[k]], f3(lin[3 * k], lin[3 * k + 1], lin[3 * k + 2]));
+                atomic_add3(&LTMP[idx[k]], f3(lin[12 + 3 * k], lin[13 + 3 * k], lin[14 + 3 * k]));
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < nv; i += 32) {
+            float4 l = a.LV[i], t = LTMP[i];
+            a.LV[i] = make_float4(l.x + t.x, l.y + t.y, l.z + t.z, l.w);
+        }
+        __syncwarp();
+    }
+    // ---- B3: velocity rebuilt from the displacement
+    for (int i = lane; i < nv; i += 32) {
+        const float4 kin = P.KIN[v0 + i];
+        const int kind = (int)kin.w;
+        (void)kin;
+        (void)kind;
+        float4 l = a.LV[i];
+        V3<float> lv = ih * f3(l);
+        float4 d = a.LD[i];
+        a.LD[i] = make_float4(d.x + lv.x, d.y + lv.y, d.z + lv.z, 0.f);
+        a.LV[i] = make_float4(0.f, 0.f, 0.f, l.w);
+    }
+    __syncwarp();
+    // ---- B4: PBD iterations in reverse
+    if (lenc || (CONTACT && np > 0)) {
+        const int ncol = lenc ? ((closed && (ne & 1)) ? 3 : 2) : 0;
+        float4* Cpre[4] = {s.HB0, s.HB1, s.HB2, s.ND};
+        for (int it = sc.n_iter - 1; it >= 0; --it) {
+            for (int i = lane; i < nv; i += 32) Cpre[0][i] = SN[(size_t)it * NV + i];
+            __syncwarp();
+            for (int k = 0; k < ncol; ++k) {
+                for (int i = lane; i < nv; i += 32) Cpre[k + 1][i] = Cpre[k][i];
+                __syncwarp();
+                inext_color_arr(R, s.X0, Cpre[k + 1], s.ET, lane, k, closed);
+            }
+            if (CONTACT && np > 0) {
+                const float4* Dc = Cpre[ncol];
+                float4* LTMP = a.LG;
+                for (int i = lane; i < nv; i += 32) LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                for (int p = lane; p < np; p += 32) {
+                    uint32_t pr = s.pairs[p];
+                    const int a0 = pr & 0xffff, q0 = pr >> 16;
+                    const int idx[4] = {a0, (a0 + 1 == nv) ? 0 : a0 + 1, q0, (q0 + 1 == nv) ? 0 : q0 + 1};
+                    const V3<float> o = f3(s.X0[a0]);
+                    V3<float> Pf[4], lo[4];
+                    float w[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        Pf[k] = (k == 0) ? f3(Dc[idx[0]]) : (f3(s.X0[idx[k]]) - o) + f3(Dc[idx[k]]);
+                        w[k] = s.X0[idx[k]].w;
+                        lo[k] = f3(a.LD[idx[k]]);
+                    }
+                    {
+                        V3<float> dxf[4], nf;
+                        float su, uu, dd, W;
+                        if (!pair_correction(Pf[0], Pf[1], Pf[2], Pf[3], w[0], w[1], w[2], w[3], rsum, dxf, su, uu,
+                                             nf, dd, W))
+                            continue;
+                    }
+                    float lin[12];
+#pragma unroll 1
+                    for (int d = 0; d < 12; ++d) {
+                        V3<dualf> Pd[4], dx[4], n;
+                        dualf su, uu, dd, W;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            V3<float> ep = zf3();
+                            if (d / 3 == k) (d % 3 == 0 ? ep.x : d % 3 == 1 ? ep.y : ep.z) = 1.f;
+                            Pd[k] = lift(Pf[k], ep);
+                        }
+                        float acc = 0.f;
+                        if (pair_correction(Pd[0], Pd[1], Pd[2], Pd[3], w[0], w[1], w[2], w[3], rsum, dx, su, uu, n,
+                                            dd, W))
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) acc += dot(ders(dx[k]), lo[k]);
+                        lin[d] = acc;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) atomic_add3(&LTMP[idx[k]], f3(lin[3 * k], lin[3 * k + 1], lin[3 * k + 2]));
+                }
+                __syncwarp();
+                for (int i = lane; i < nv; i += 32) {
+                    float4 t = LTMP[i];
+                    if (it == 0) {
+                        float4 q = a.LP0[i];
+                        t = make_float4(t.x + q.x, t.y + q.y, t.z + q.z, 0.f);
+                    }
+                    float4 ld = a.LD[i], lx = a.LX[i];
+                    a.LD[i] = make_float4(ld.x + t.x, ld.y + t.y, ld.z + t.z, 0.f);
+                    a.LX[i] = make_float4(lx.x + t.x, lx.y + t.y, lx.z + t.z, 0.f);
+                }
+                __syncwarp();
+            }
+            for (int k = ncol - 1; k >= 0; --k) {
+                const float4* D = Cpre[k];
+                int first, last;
+                color_range(ne, closed, k, first, last);
+                const bool inext = R.flags & ROD_INEXT;
+                for (int j = first + 2 * lane; j < last; j += 64) {
+                    const int j1 = (j + 1 == nv) ? 0 : j + 1;
+                    float4 A = D[j], B = D[j1];
+                    V3<float> e = (f3(s.X0[j1]) - f3(s.X0[j])) + (f3(B) - f3(A));
+                    float ell = sqrtf(dot(e, e));
+                    float eb = s.ET[j].w, target;
+                    bool active;
+                    if (inext) {
+                        target = eb;
+                        active = true;
+                    } else {
+                        float hi = (1.f + R.slim) * eb, lo = (1.f - R.slim) * eb;
+                        active = (ell > hi) || (ell < lo);
+                        target = ell > hi ? hi : lo;
+                    }
+                    float ws = A.w + B.w;
+                    if (!active || !(ws > 0.f)) continue;
+                    V3<float> t = e / ell;
+                    V3<float> la = f3(a.LD[j]), lb = f3(a.LD[j1]);
+                    V3<float> mu = (A.w / ws) * la - (B.w / ws) * lb;
+                    V3<float> le = mu - (target / ell) * (mu - dot(mu, t) * t);
+                    a.LD[j] = f4(la - le, 0.f);
+                    a.LD[j1] = f4(lb + le, 0.f);
+                    a.LX[j] = f4(f3(a.LX[j]) - le, 0.f);
+                    a.LX[j1] = f4(f3(a.LX[j1]) + le, 0.f);
+                }
+                __syncwarp();
+            }
+        }
+    }
+    // ---- B5: vertex phase (rigid contact, symplectic Euler, gravity, damping, twist rate)
+    for (int i = lane; i < nv; i += 32) {
+        const float4 kin = P.KIN[v0 + i];
+        const int kind = (int)kin.w;
+        const float4 x4 = s.X0[i];
+        const float4 vn = s.V[i];
+        V3<float> ld0 = f3(a.LD[i]);
+        float4 lvn = make_float4(0.f, 0.f, 0.f, 0.f), lg = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kind == 0) {
+            V3<float> lam = h * ld0;
+            // forward sequence of the rigid primitives from the recorded pre-contact velocity
+            const int nprim = sc.n_planes + sc.n_boxes + R.ngrip;
+            V3<float> vs[kMaxPlanes + kMaxBoxes + 2];
+            vs[0] = f3(a.V1[i]);
+            const V3<float> x = f3(x4);
+            const float idt = 1.f / sc.dt;
+            for (int k = 0; k < nprim; ++k) {
+                const int q = k - sc.n_planes - sc.n_boxes;
+                V3<float> gp = zf3(), gax = zf3(), vp = zf3(), w = zf3();
+                if (q >= 0) {
+                    gp = f3(F0.p[12 * q] + c0 * act[6 * q], F0.p[12 * q + 1] + c0 * act[6 * q + 1],
+                            F0.p[12 * q + 2] + c0 * act[6 * q + 2]);
+                    gax = col(gR0[q], 2);
+                    vp = idt * f3(act[6 * q], act[6 * q + 1], act[6 * q + 2]);
+                    w = idt * f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
+                }
+                bool on;
+                V3<float> nxt = prim_respond<float>(k, sc, R, x, vs[k], gp, gax, vp, w, on);
+                if (k + 1 < kMaxPlanes + kMaxBoxes + 2) vs[k + 1] = nxt;
+            }
+            V3<float> lx_acc = zf3();
+            for (int k = nprim - 1; k >= 0; --k) {
+                const int q = k - sc.n_planes - sc.n_boxes;
+                V3<float> gp = zf3(), gax = zf3(), vp = zf3(), w = zf3();
+                if (q >= 0) {
+                    gp = f3(F0.p[12 * q] + c0 * act[6 * q], F0.p[12 * q + 1] + c0 * act[6 * q + 1],
+                            F0.p[12 * q + 2] + c0 * act[6 * q + 2]);
+                    gax = col(gR0[q], 2);
+                    vp = idt * f3(act[6 * q], act[6 * q + 1], act[6 * q + 2]);
+                    w = idt * f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
+                }
+                bool on;
+                prim_respond<float>(k, sc, R, x, vs[k], gp, gax, vp, w, on);
+                if (!on) continue;
+                const int nin = q >= 0 ? 18 : 6;
+                float lin[18];
+#pragma unroll 1
+                for (int d = 0; d < nin; ++d) {
+                    V3<float> e = zf3();
+                    (d % 3 == 0 ? e.x : d % 3 == 1 ? e.y : e.z) = 1.f;
+                    const int g = d / 3;
+                    V3<dualf> xd = lift(x, g == 0 ? e : zf3()), vd = lift(vs[k], g == 1 ? e : zf3());
+                    V3<dualf> gpd = lift(gp, g == 2 ? e : zf3()), gaxd = lift(gax, g == 3 ? cross(e, gax) : zf3());
+                    V3<dualf> vpd = lift(vp, g == 4 ? e : zf3()), wd = lift(w, g == 5 ? e : zf3());
+                    bool on2;
+                    V3<dualf> out = prim_respond<dualf>(k, sc, R, xd, vd, gpd, gaxd, vpd, wd, on2);
+                    lin[d] = dot(ders(out), lam);
+                }
+                lx_acc += f3(lin[0], lin[1], lin[2]);
+                lam = f3(lin[3], lin[4], lin[5]);
+                if (q >= 0) {
+                    add3(pa.ps0, q, f3(lin[6], lin[7], lin[8]));
+                    add3(pa.phs0, q, f3(lin[9], lin[10], lin[11]));
+                    add3(pa.vp, q, f3(lin[12], lin[13], lin[14]));
+                    add3(pa.w, q, f3(lin[15], lin[16], lin[17]));
+                }
+            }
+            // v1 = v + h (-w g + gravity - c_d v)
+            const float wi = x4.w;
+            lvn = f4((1.f - h * R.cd) * lam, 0.f);
+            lg = f4((-h * wi) * lam, 0.f);
+            gm[4] += -(double)h * (double)dot(f3(vn), lam);
+            a.LX[i] = f4(f3(a.LX[i]) + lx_acc, 0.f);
+        } else if (kind >= 2) {
+            // d = target(pose at the substep end) - x0
+            const int q = kind - 2;
+            add3(pa.ps1, q, ld0);
+            add3(pa.phs1, q, cross(mul(gR1[q], f3(kin)), ld0));
+            a.LX[i] = f4(f3(a.LX[i]) - ld0, 0.f);
+        }
+        const bool has_e = closed || i < nv - 1;
+        if (has_e) {
+            const float lw1 = a.LV[i].w + h * a.LE[i].w;     // d theta_{n+1} / d omega_1 = h
+            const float invI = P.ES[e0 + i].y;
+            lvn.w = (1.f - h * R.cd) * lw1;
+            lg.w = -h * invI * lw1;
+            gm[4] += -(double)h * (double)vn.w * (double)lw1;
+        }
+        a.LV[i] = lvn;
+        a.LG[i] = lg;
+    }
+    __syncwarp();
+    // ---- B8: per edge, reverse of the new reference-frame base and stretching second order
+    for (int j = lane; j < ne; j += 32) {
+        const int j1 = (j + 1 == nv) ? 0 : j + 1;
+        const float4 ed = s.ED[j], et = s.ET[j];
+        EdgeF<float> E;
+        edge_forward(E, f3(s.X0[j]), f3(s.X0[j1]), f3(et), f3(ed), ed.w);
+        V3<float> gtb, gd1b;
+        V3<float> le = edge_reverse<float, true>(E, f3(et), f3(ed), f3(a.LT[j]), f3(a.LE[j]), 0.f, &gtb, &gd1b);
+        if (R.kA > 0.f) {
+            const V3<float> les = f3(a.LG[j1]) - f3(a.LG[j]);
+            const float eb = P.ES[e0 + j].x;
+            const float tl = dot(E.t, les);
+            le += R.kA * ((tl / eb) * E.t + (E.ell / eb - 1.f) / E.ell * (les - tl * E.t));
+            gm[0] += (double)(E.ell / eb - 1.f) * (double)tl;
+        }
+        s.HB1[j] = f4(le, 0.f);
+        a.LT[j] = f4(gtb, 0.f);
+        a.LE[j] = f4(gd1b, a.LE[j].w);
+    }
+    __syncwarp();
+    for (int i = lane; i < nv; i += 32) {
+        V3<float> l = f3(a.LX[i]);
+        if (closed || i < nv - 1) l -= f3(s.HB1[i]);
+        if (closed || i > 0) l += f3(s.HB1[i == 0 ? ne - 1 : i - 1]);
+        a.LX[i] = f4(l, 0.f);
+    }
+    __syncwarp();
+    // ---- B7: hinges: force second order (dual numbers), plasticity, its first-order reverse
+    for (int k = lane; k < nh; k += 32) {
+        const int i = closed ? k : k + 1;
+        const int ea = (i == 0) ? ne - 1 : i - 1, eb = i;
+        const int im = (i == 0) ? nv - 1 : i - 1, ip = (i + 1 == nv) ? 0 : i + 1;
+        const float4 EDa = s.ED[ea], EDb = s.ED[eb], ETa = s.ET[ea], ETb = s.ET[eb], hg = s.HG[i];
+        const float lbar = 0.5f * (ETa.w + ETb.w), il = 1.f / lbar;
+        HingeF<float> Hf;
+        hinge_forward(Hf, f3(s.X0[im]), f3(s.X0[i]), f3(s.X0[ip]), f3(ETa), f3(EDa), f3(ETb), f3(EDb), EDa.w, EDb.w,
+                      hg.w);
+        float kb0 = hg.x, kb1 = hg.y;
+        const bool plastic = R.flags & ROD_PLASTIC;
+        const bool yielded = plastic && plastic_update(Hf.k0, Hf.k1, kb0, kb1, R.sy * lbar, R.rc);
+        // second order of the elastic force: tangents = cotangents of the gradient
+        HingeF<dualf> Hd;
+        const float4 gm_ = a.LG[im], gi_ = a.LG[i], gp_ = a.LG[ip];
+        hinge_forward(Hd, lift(f3(s.X0[im]), f3(gm_)), lift(f3(s.X0[i]), f3(gi_)), lift(f3(s.X0[ip]), f3(gp_)),
+                      lift(f3(ETa)), lift(f3(EDa)), lift(f3(ETb)), lift(f3(EDb)), mkd(EDa.w, a.LG[ea].w),
+                      mkd(EDb.w, a.LG[eb].w), mkd(hg.w));
+        dualf e0d = Hd.k0 - kb0, e1d = Hd.k1 - kb1, emd = Hd.m - hg.z;
+        dualf gk0 = (R.Bm * il) * e0d, gk1 = (R.Bm * il) * e1d, gmt = (R.beta * il) * emd;
+        V3<dualf> gxm, gxi, gxp, gtba, gd1ba, gtbb, gd1bb;
+        dualf gta, gtb;
+        hinge_reverse<dualf, true>(Hd, lift(f3(ETa)), lift(f3(EDa)), lift(f3(ETb)), lift(f3(EDb)), gk0, gk1, gmt,
+                                   mkd(0.f), gxm, gxi, gxp, gta, gtb, &gtba, &gd1ba, &gtbb, &gd1bb);
+        atomic_add3(&a.LX[im], ders(gxm));
+        atomic_add3(&a.LX[i], ders(gxi));
+        atomic_add3(&a.LX[ip], ders(gxp));
+        atomicAdd(&a.LE[ea].w, gta.d);
+        atomicAdd(&a.LE[eb].w, gtb.d);
+        atomic_add3(&a.LT[ea], ders(gtba));
+        atomic_add3(&a.LE[ea], ders(gd1ba));
+        atomic_add3(&a.LT[eb], ders(gtbb));
+        atomic_add3(&a.LE[eb], ders(gd1bb));
+        gm[1] += (double)il * ((double)e0d.v * e0d.d + (double)e1d.v * e1d.d);
+        gm[2] += (double)il * (double)emd.v * (double)emd.d;
+        // rest curvature: cotangent of the one used (-d gk / d .) plus the carried one
+        float lk0 = a.LK[i].x - gk0.d, lk1 = a.LK[i].y - gk1.d;
+        if (yielded) {
+            const float el0 = Hf.k0 - hg.x, el1 = Hf.k1 - hg.y;
+            const float n = sqrtf(el0 * el0 + el1 * el1), thr = R.sy * lbar;
+            const float g = R.rc * (n - thr) / n;
+            const float kk = R.rc * thr / (n * n * n) * (el0 * lk0 + el1 * lk1);
+            const float le0 = g * lk0 + kk * el0, le1 = g * lk1 + kk * el1;     // cotangent of kappa_el
+            gm[3] += -(double)R.rc * lbar * ((double)el0 * lk0 + (double)el1 * lk1) / n;
+            V3<float> fxm, fxi, fxp, ftba, fd1ba, ftbb, fd1bb;
+            float fta, ftb;
+            hinge_reverse<float, true>(Hf, f3(ETa), f3(EDa), f3(ETb), f3(EDb), le0, le1, 0.f, 0.f, fxm, fxi, fxp,
+                                       fta, ftb, &ftba, &fd1ba, &ftbb, &fd1bb);
+            atomic_add3(&a.LX[im], fxm);
+            atomic_add3(&a.LX[i], fxi);
+            atomic_add3(&a.LX[ip], fxp);
+            atomicAdd(&a.LE[ea].w, fta);
+            atomicAdd(&a.LE[eb].w, ftb);
+            atomic_add3(&a.LT[ea], ftba);
+            atomic_add3(&a.LE[ea], fd1ba);
+            atomic_add3(&a.LT[eb], ftbb);
+            atomic_add3(&a.LE[eb], fd1bb);
+            lk0 -= le0;
+            lk1 -= le1;
+        }
+        a.LK[i] = make_float4(lk0, lk1, 0.f, 0.f);
+    }
+    __syncwarp();
+    // ---- pose cotangents of this substep -> frame-start pose and the frame's actions
+    const float idt = 1.f / sc.dt;
+    for (int q = 0; q < R.ngrip; ++q) {
+        const V3<float> dphi = f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
+        const V3<float> ps = get3(pa.ps0, q) + get3(pa.ps1, q);
+        add3(lpf, q, ps);
+        const V3<float> gdp = c0 * get3(pa.ps0, q) + c1 * get3(pa.ps1, q) + idt * get3(pa.vp, q);
+        const V3<float> gdr = c0 * jl_t(c0 * dphi, get3(pa.phs0, q)) + c1 * jl_t(c1 * dphi, get3(pa.phs1, q)) +
+                              idt * get3(pa.w, q);
+        ga[6 * q] += gdp.x;
+        ga[6 * q + 1] += gdp.y;
+        ga[6 * q + 2] += gdp.z;
+        ga[6 * q + 3] += gdr.x;
+        ga[6 * q + 4] += gdr.y;
+        ga[6 * q + 5] += gdr.z;
+        const M3 M0 = expmap(c0 * dphi), M1 = expmap(c1 * dphi);
+        add3(lphif, q, mulT(M0, get3(pa.phs0, q)) + mulT(M1, get3(pa.phs1, q)));
+    }
+}
+
+// ------------------------------------------------------------------ the backward kernel
+template <int NV, bool CONTACT>
+__global__ void __launch_bounds__(256) bwd_kernel(BwdParams P) {
+    extern __shared__ float4 dyn_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4* base = dyn_smem + warp * (bwd_smem_bytes(NV, CONTACT) / 16);
+    Smem<NV, CONTACT> s(base);
+    AdjArrays<NV, CONTACT> a(base + warp_smem_bytes(NV, CONTACT) / 16);
+    const size_t slot = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    float4* L2 = reinterpret_cast<float4*>(P.scratch + slot * P.slot_bytes);
+    const size_t E2 = 5 * NV + 6, E3 = 5 * NV;
+    float4* L3 = L2 + (size_t)P.K * E2;
+    float4* SN = L3 + (size_t)P.nsub_max * E3;
+    const SceneDev& sc = P.scene;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(P.counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= P.n_order) break;
+        const int rod = P.order[item];
+        const RodInfo R = P.rods[rod];
+        const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
+        const float h = sc.dt / (float)nsub;
+        for (int i = lane; i < R.nv; i += 32) {
+            float4 dx = P.dLdx ? P.dLdx[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 dv = P.dLdv ? P.dLdv[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!(R.flags & ROD_CLOSED) && i == R.nv - 1) dv.w = 0.f;
+            a.LX[i] = make_float4(dx.x, dx.y, dx.z, 0.f);
+            a.LV[i] = dv;
+            a.LK[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int j = lane; j < R.ne; j += 32) {
+            a.LE[j] = make_float4(0.f, 0.f, 0.f, P.dLdth ? P.dLdth[R.e0 + j] : 0.f);
+            a.LT[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        double gm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // FP64: these sums cancel strongly
+        float lpf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, lphif[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float ga[12];
+        bool ovf = false;
+        for (int seg = P.ck_count - 1; seg >= 0; --seg) {
+            const int f0 = seg * P.ck_every, f1 = min(f0 + P.ck_every, P.frames);
+            // reload the checkpoint of the segment
+            {
+                const long long oV = seg * P.ck_strideV, oE = seg * P.ck_strideE;
+                for (int i = lane; i < R.nv; i += 32) {
+                    float4 x = P.ck.X[oV + R.v0 + i];
+                    s.X0[i] = x;
+                    s.X[i] = x;
+                    s.V[i] = P.ck.Vl[oV + R.v0 + i];
+                    s.HG[i] = P.ck.HG[oV + R.v0 + i];
+                }
+                for (int j = lane; j < R.ne; j += 32) {
+                    s.ED[j] = P.ck.ED[oE + R.e0 + j];
+                    s.ET[j] = P.ck.ET[oE + R.e0 + j];
+                }
+                __syncwarp();
+            }
+            Pose F;
+            F.load(P.ck.GP + seg * P.ck_strideB + 24LL * rod);
+            // level 2: frame-start states of the segment
+            for (int f = f0; f < f1; ++f) {
+                float4* e = L2 + (size_t)(f - f0) * E2;
+                save_state<NV, CONTACT>(e, R, lane, s);
+                if (lane < 24) reinterpret_cast<float*>(e + 5 * NV)[lane] = F.p[lane];
+                __syncwarp();
+                const float* act = P.actions + ((size_t)f * P.B + rod) * 12;
+                float ac[12];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) ac[k] = act[k];
+                run_frame<NV, CONTACT>(sc, P.KIN, P.ES, R, s, lane, nsub, h, F, ac, ovf, [](int) {});
+            }
+            for (int f = f1 - 1; f >= f0; --f) {
+                float ac[12];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) ac[k] = P.actions[((size_t)f * P.B + rod) * 12 + k];
+                // carry the pose cotangent of frame f+1's start into this frame's actions
+#pragma unroll
+                for (int k = 0; k < 12; ++k) ga[k] = 0.f;
+                for (int q = 0; q < R.ngrip; ++q) {
+                    const V3<float> dphi = f3(ac[6 * q + 3], ac[6 * q + 4], ac[6 * q + 5]);
+                    const V3<float> lp = get3(lpf, q), lr = get3(lphif, q);
+                    ga[6 * q] = lp.x;
+                    ga[6 * q + 1] = lp.y;
+                    ga[6 * q + 2] = lp.z;
+                    const V3<float> jr = jl_t(dphi, lr);
+                    ga[6 * q + 3] = jr.x;
+                    ga[6 * q + 4] = jr.y;
+                    ga[6 * q + 5] = jr.z;
+                    const V3<float> nr = mulT(expmap(dphi), lr);
+                    lphif[3 * q] = nr.x;
+                    lphif[3 * q + 1] = nr.y;
+                    lphif[3 * q + 2] = nr.z;
+                }
+                // level 3: substep-start states of this frame
+                const float4* e = L2 + (size_t)(f - f0) * E2;
+                load_state<NV, CONTACT>(e, R, lane, s);
+                Pose F0;
+                F0.load(reinterpret_cast<const float*>(e + 5 * NV));
+                Pose Fw = F0;
+                const int np = run_frame<NV, CONTACT>(sc, P.KIN, P.ES, R, s, lane, nsub, h, Fw, ac, ovf,
+                                                      [&](int sb) { save_state<NV, CONTACT>(L3 + (size_t)sb * E3, R, lane, s); });
+                __syncwarp();
+                for (int sb = nsub - 1; sb >= 0; --sb) {
+                    const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
+                    M3 gR0[2], gR1[2];
+                    gR0[0] = F0.R[0];
+                    gR0[1] = F0.R[1];
+                    if (sb > 0) substep_rot(F0, ac, R.ngrip, c0, gR0);
+                    substep_rot(F0, ac, R.ngrip, c1, gR1);
+                    // level 4: the substep's intermediates
+                    load_state<NV, CONTACT>(L3 + (size_t)sb * E3, R, lane, s);
+                    Rec rec{SN, a.V1, a.DF, NV};
+                    substep<NV, CONTACT, true>(sc, P.KIN, P.ES, R, s, lane, h, F0.p, gR0, gR1, c0, c1, ac, np, &rec);
+                    load_state<NV, CONTACT>(L3 + (size_t)sb * E3, R, lane, s);
+                    reverse_substep<NV, CONTACT>(P, R, s, a, SN, lane, h, F0, ac, gR0, gR1, c0, c1, np, gm, lpf,
+                                                 lphif, ga);
+                }
+                if (P.gact) {
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) {
+                        float v = ga[k];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                        if (lane == 0) P.gact[((size_t)f * P.B + rod) * 12 + k] = v;
+                    }
+                }
+            }
+        }
+        // outputs
+        for (int i = lane; i < R.nv; i += 32) {
+            if (P.gx0) P.gx0[R.v0 + i] = a.LX[i];
+            if (P.gv0) P.gv0[R.v0 + i] = a.LV[i];
+        }
+        for (int j = lane; j < R.ne; j += 32) {
+            if (P.gth0) P.gth0[R.e0 + j] = a.LE[j].w;
+            P.gtb0[R.e0 + j] = a.LT[j];
+            P.gd1b0[R.e0 + j] = make_float4(a.LE[j].x, a.LE[j].y, a.LE[j].z, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            double v = gm[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+            gm[k] = v;
+        }
+        if (lane == 0 && P.gmat) {
+            const double r = R.radius, A = 3.14159265358979323846 * r * r, r2 = r * r;
+            P.gmat[5 * rod + 0] = R.kA > 0.f ? (float)(gm[0] * A) : 0.f;   // K_stretch
+            P.gmat[5 * rod + 1] = (float)(gm[1] * A * r2 / 4.0);            // E_bend
+            P.gmat[5 * rod + 2] = (float)(gm[2] * A * r2 / 2.0);            // G_twist
+            P.gmat[5 * rod + 3] = (float)gm[3];                             // yield curvature
+            P.gmat[5 * rod + 4] = (float)gm[4];                             // damping
+        }
+        __syncwarp();
+    }
+}
+
+template <int NV, bool C>
+static int bwd_occ_t(int warps) {
+    size_t smem = bwd_smem_bytes(NV, C) * warps;
+    auto k = bwd_kernel<NV, C>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * warps, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+template <int NV, bool C>
+static cudaError_t launch_bwd_t(const BwdParams& P, int grid, int warps, cudaStream_t st) {
+    size_t smem = bwd_smem_bytes(NV, C) * warps;
+    auto k = bwd_kernel<NV, C>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 32 * warps, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace dlo

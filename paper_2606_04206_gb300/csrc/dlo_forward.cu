@@ -1,626 +1,25 @@
-// dlo_forward.cu -- persistent forward kernel: one warp per rod, rod state in shared memory
-// across all substeps and frames of a launch.
-//
-// Per substep (DLO-Lab Sec. 3.1 / 3.2 / App. A.1), for one rod:
-//   hinge phase   reference frames by time-parallel transport, curvature and twist, bending
-//                 plasticity on the rest curvature, exact energy gradient of each hinge
-//   vertex phase  gradient gather + stretching, gravity, damping, symplectic-Euler velocity,
-//                 soft SDF contact (planes, boxes, capsule grippers), position predict,
-//                 kinematic vertices, new reference-frame base
-//   PBD phase     N_C x (red-black inextensibility / strain limit, Jacobi self-collision)
-//   velocity      v = (x* - x)/h, self-contact Coulomb friction
-// Per frame: self-contact candidates by a per-rod spatial hash, gripper pose update,
-// checkpoints, non-finite detection and the FP64 inextensibility residual.
-#include "dlo_internal.h"
-#include "dlo_physics.cuh"
+// dlo_forward.cu -- dispatch of the persistent forward kernel to its size classes (the kernel
+// is in dlo_fwd_kernel.cuh, instantiated per size class in dlo_nv*.cu).
 #include "dlo_kernels.h"
 
 namespace dlo {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr float kFixPos = 1073741824.f;     // 2^30: fixed-point scale of position corrections
-constexpr float kFixVel = 16777216.f;       // 2^24: fixed-point scale of velocity corrections
-
-__device__ __forceinline__ int to_fix(float v, float scale) {
-    float q = v * scale;
-    q = fminf(fmaxf(q, -2147483520.f), 2147483520.f);
-    return __float2int_rn(q);
-}
-
-__device__ __forceinline__ unsigned cell_hash(int ix, int iy, int iz, int mask) {
-    return ((unsigned)ix * 73856093u ^ (unsigned)iy * 19349663u ^ (unsigned)iz * 83492791u) & (unsigned)mask;
-}
-
-// Rigid contact of one vertex against the scene and the rod's grippers (Sec. 3.2).
-__device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const RodInfo& R, V3<float> x,
-                                                    V3<float> v, const float* gp0, const M3* gR0,
-                                                    const float* act) {
-    bool on;
-    for (int k = 0; k < sc.n_planes; ++k) {
-        V3<float> n = f3(sc.planes[k]);
-        float sdf = dot(x, n) - sc.planes[k].w;
-        v = contact_respond(v, sdf, n, zf3(), R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
-    }
-    for (int k = 0; k < sc.n_boxes; ++k) {
-        V3<float> n;
-        float sdf = sdf_box(x, f3(sc.box_c[k]), f3(sc.box_h[k]), n);
-        v = contact_respond(v, sdf, n, zf3(), R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
-    }
-    for (int g = 0; g < R.ngrip; ++g) {
-        V3<float> p = f3(gp0[3 * g], gp0[3 * g + 1], gp0[3 * g + 2]);
-        V3<float> ax = col(gR0[g], 2);
-        V3<float> a = p - sc.grip_hl * ax, b = p + sc.grip_hl * ax, n;
-        float sdf = sdf_capsule(x, a, b, sc.grip_r, n);
-        const float inv_dt = 1.f / sc.dt;
-        V3<float> vp = f3(act[6 * g] * inv_dt, act[6 * g + 1] * inv_dt, act[6 * g + 2] * inv_dt);
-        V3<float> w = f3(act[6 * g + 3] * inv_dt, act[6 * g + 4] * inv_dt, act[6 * g + 5] * inv_dt);
-        V3<float> vrig = vp + cross(w, x - p);
-        v = contact_respond(v, sdf, n, vrig, R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
-    }
-    return v;
-}
-
-template <int NV, bool CONTACT>
-struct Smem {
-    float4 *X, *X0, *V, *ED, *ET, *HG, *HB0, *HB1, *HB2, *ND;
-    float4 *fr0, *fr1;
-    int4* acc;
-    uint32_t* pairs;
-    __device__ Smem(float4* base) {
-        X = base;
-        X0 = base + NV;
-        V = base + 2 * NV;
-        ED = base + 3 * NV;
-        ET = base + 4 * NV;
-        HG = base + 5 * NV;
-        HB0 = base + 6 * NV;
-        HB1 = base + 7 * NV;
-        HB2 = base + 8 * NV;
-        ND = base + 9 * NV;
-        fr0 = base + 10 * NV;
-        fr1 = fr0 + 2 * NV;
-        acc = reinterpret_cast<int4*>(fr1 + 2 * NV);
-        pairs = reinterpret_cast<uint32_t*>(acc + NV);
-    }
-};
-
-// ------------------------------------------------------------------ broad phase
-// Per-rod spatial hash of edge midpoints (cells of R.cell >= candidate distance + longest
-// edge, so the 27 neighbouring cells hold every candidate); candidates are the edge pairs
-// outside the exclusion window whose segments are closer than R.contact_d.
-template <int NV, bool CONTACT>
-__device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, bool closed, bool& overflow) {
-    constexpr int TBL = NV <= 32 ? 64 : (NV <= 64 ? 128 : (NV <= 128 ? 256 : 512));
-    int* keys = reinterpret_cast<int*>(s.HB0);
-    int* cnt = keys + NV;          // TBL bucket counters + 1 pair counter
-    int* sorted = cnt + TBL + 1;
-    const int ne = R.ne, nv = R.nv;
-    const V3<float> org = f3(s.X[0]);
-    const float inv_cell = 1.f / R.cell;
-    for (int k = lane; k <= TBL; k += 32) cnt[k] = 0;
-    __syncwarp();
-    for (int j = lane; j < ne; j += 32) {
-        int j1 = (j + 1 == nv) ? 0 : j + 1;
-        V3<float> m = 0.5f * (f3(s.X[j]) + f3(s.X[j1])) - org;
-        int ix = min(max(__float2int_rd(m.x * inv_cell), -510), 510) + 512;
-        int iy = min(max(__float2int_rd(m.y * inv_cell), -510), 510) + 512;
-        int iz = min(max(__float2int_rd(m.z * inv_cell), -510), 510) + 512;
-        keys[j] = (ix << 20) | (iy << 10) | iz;
-        atomicAdd(&cnt[cell_hash(ix, iy, iz, TBL - 1)], 1);
-    }
-    __syncwarp();
-    {   // exclusive scan of the bucket counts (TBL/32 consecutive buckets per lane)
-        constexpr int PER = TBL / 32;
-        int loc[PER];
-        int sum = 0;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            loc[k] = cnt[lane * PER + k];
-            sum += loc[k];
-        }
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int run = incl - sum;
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            cnt[lane * PER + k] = run;
-            run += loc[k];
-        }
-    }
-    __syncwarp();
-    for (int j = lane; j < ne; j += 32) {
-        int key = keys[j];
-        int pos = atomicAdd(&cnt[cell_hash(key >> 20, (key >> 10) & 1023, key & 1023, TBL - 1)], 1);
-        sorted[pos] = j;
-    }
-    __syncwarp();
-    // after the scatter cnt[h] is the end of bucket h (and the start of bucket h + 1)
-    const int cap = R.pair_cap;
-    bool ovf = false;
-    for (int a = lane; a < ne; a += 32) {
-        int key = keys[a];
-        int ix = key >> 20, iy = (key >> 10) & 1023, iz = key & 1023;
-        int a1 = (a + 1 == nv) ? 0 : a + 1;
-        V3<float> pa0 = f3(s.X[a]), pa1 = f3(s.X[a1]);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int cx = ix + dx, cy = iy + dy, cz = iz + dz;
-                    int nk = (cx << 20) | (cy << 10) | cz;
-                    unsigned hh = cell_hash(cx, cy, cz, TBL - 1);
-                    int beg = hh ? cnt[hh - 1] : 0, end = cnt[hh];
-                    for (int q = beg; q < end; ++q) {
-                        int b = sorted[q];
-                        if (b <= a || keys[b] != nk) continue;
-                        int sep = b - a;
-                        if (closed) sep = min(sep, ne - sep);
-                        if (sep <= R.excl) continue;
-                        int b1 = (b + 1 == nv) ? 0 : b + 1;
-                        V3<float> pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
-                        float su, uu;
-                        closest_params(pa0, pa1, pb0, pb1, su, uu);
-                        V3<float> dd = (pa0 + su * (pa1 - pa0)) - (pb0 + uu * (pb1 - pb0));
-                        float dist = sqrtf(dot(dd, dd));
-                        if (!(dist < R.contact_d)) continue;
-                        int idx = atomicAdd(&cnt[TBL], 1);
-                        if (idx < cap)
-                            s.pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
-                        else
-                            ovf = true;
-                    }
-                }
-    }
-    __syncwarp();
-    overflow = __any_sync(kFull, ovf);
-    int np = cnt[TBL];
-    __syncwarp();
-    return min(np, cap);
-}
-
-// ------------------------------------------------------------------ PBD pieces
-template <int NV, bool CONTACT>
-__device__ __forceinline__ void inext_color(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, int color,
-                                            bool closed) {
-    const int ne = R.ne, nv = R.nv;
-    const bool three = closed && (ne & 1);
-    int first, last;   // edges first, first+2, ... < last
-    if (color == 2) {
-        first = ne - 1;
-        last = ne;
-    } else {
-        first = color;
-        last = (color == 0 && three) ? ne - 1 : ne;
-    }
-    const bool inext = R.flags & ROD_INEXT;
-    for (int j = first + 2 * lane; j < last; j += 64) {
-        int j1 = (j + 1 == nv) ? 0 : j + 1;
-        float4 A = s.X[j], B = s.X[j1];              // displacements (w = inverse mass)
-        V3<float> e = (f3(s.X0[j1]) - f3(s.X0[j])) + (f3(B) - f3(A));
-        float ell = sqrtf(dot(e, e));
-        float eb = s.ET[j].w;
-        float target;
-        bool active;
-        if (inext) {
-            target = eb;
-            active = true;
-        } else {
-            float hi = (1.f + R.slim) * eb, lo = (1.f - R.slim) * eb;
-            active = (ell > hi) || (ell < lo);
-            target = ell > hi ? hi : lo;
-        }
-        float ws = A.w + B.w;
-        if (!active || !(ws > 0.f)) continue;
-        float lam = (ell - target) / ws;
-        V3<float> t = e / ell;
-        V3<float> da = (lam * A.w) * t, db = (lam * B.w) * t;
-        s.X[j] = make_float4(A.x + da.x, A.y + da.y, A.z + da.z, A.w);
-        s.X[j1] = make_float4(B.x - db.x, B.y - db.y, B.z - db.z, B.w);
-    }
-    __syncwarp();
-}
-
-template <int NV, bool CONTACT>
-__device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, int np,
-                                              bool first) {
-    const int nv = R.nv;
-    for (int i = lane; i < nv; i += 32) s.acc[i] = make_int4(0, 0, 0, 0);
-    __syncwarp();
-    const float rsum = 2.f * R.radius;
-    for (int p = lane; p < np; p += 32) {
-        uint32_t pr = s.pairs[p];
-        int a0 = pr & 0xffff, c0 = pr >> 16;
-        int a1 = (a0 + 1 == nv) ? 0 : a0 + 1, c1 = (c0 + 1 == nv) ? 0 : c0 + 1;
-        // current positions in coordinates local to the start position of vertex a0
-        const V3<float> o = f3(s.X0[a0]);
-        float4 A0 = s.X[a0], A1 = s.X[a1], C0 = s.X[c0], C1 = s.X[c1];
-        V3<float> pa0 = f3(A0), pa1 = (f3(s.X0[a1]) - o) + f3(A1);
-        V3<float> pc0 = (f3(s.X0[c0]) - o) + f3(C0), pc1 = (f3(s.X0[c1]) - o) + f3(C1);
-        V3<float> dx[4], n;
-        float su, uu, d, W;
-        bool on = pair_correction(pa0, pa1, pc0, pc1, A0.w, A1.w, C0.w, C1.w, rsum, dx, su, uu, n, d, W);
-        if (first) {
-            s.fr0[p] = f4(on ? n : zf3(), on ? d : 0.f);
-            s.fr1[p] = make_float4(su, uu, W, on ? 1.f : 0.f);
-        }
-        if (on) {
-            const int idx[4] = {a0, a1, c0, c1};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                atomicAdd(&s.acc[idx[k]].x, to_fix(dx[k].x, kFixPos));
-                atomicAdd(&s.acc[idx[k]].y, to_fix(dx[k].y, kFixPos));
-                atomicAdd(&s.acc[idx[k]].z, to_fix(dx[k].z, kFixPos));
-            }
-        }
-    }
-    __syncwarp();
-    for (int i = lane; i < nv; i += 32) {
-        int4 q = s.acc[i];
-        if (q.x | q.y | q.z) {
-            float4 x = s.X[i];
-            const float inv = 1.f / kFixPos;
-            s.X[i] = make_float4(x.x + q.x * inv, x.y + q.y * inv, x.z + q.z * inv, x.w);
-        }
-    }
-    __syncwarp();
-}
-
-template <int NV, bool CONTACT>
-__device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, int np,
-                                              float h, float mu) {
-    const int nv = R.nv;
-    for (int i = lane; i < nv; i += 32) s.acc[i] = make_int4(0, 0, 0, 0);
-    __syncwarp();
-    for (int p = lane; p < np; p += 32) {
-        float4 F1 = s.fr1[p];
-        if (!(F1.w > 0.f)) continue;
-        float4 F0 = s.fr0[p];
-        uint32_t pr = s.pairs[p];
-        int a0 = pr & 0xffff, c0 = pr >> 16;
-        int a1 = (a0 + 1 == nv) ? 0 : a0 + 1, c1 = (c0 + 1 == nv) ? 0 : c0 + 1;
-        float su = F1.x, uu = F1.y, W = F1.z;
-        V3<float> n = f3(F0);
-        V3<float> vrel = (1.f - su) * f3(s.V[a0]) + su * f3(s.V[a1]) - (1.f - uu) * f3(s.V[c0]) - uu * f3(s.V[c1]);
-        V3<float> vt = vrel - dot(vrel, n) * n;
-        float vt2 = dot(vt, vt);
-        if (!(vt2 > 1e-24f)) continue;
-        float coef = fminf(mu * F0.w / (h * sqrtf(vt2)), 1.f);
-        V3<float> dv = (-(coef / W)) * vt;
-        const int idx[4] = {a0, a1, c0, c1};
-        const float wt[4] = {s.X[a0].w * (1.f - su), s.X[a1].w * su, -s.X[c0].w * (1.f - uu), -s.X[c1].w * uu};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            atomicAdd(&s.acc[idx[k]].x, to_fix(wt[k] * dv.x, kFixVel));
-            atomicAdd(&s.acc[idx[k]].y, to_fix(wt[k] * dv.y, kFixVel));
-            atomicAdd(&s.acc[idx[k]].z, to_fix(wt[k] * dv.z, kFixVel));
-        }
-    }
-    __syncwarp();
-    for (int i = lane; i < nv; i += 32) {
-        int4 q = s.acc[i];
-        if (q.x | q.y | q.z) {
-            float4 v = s.V[i];
-            const float inv = 1.f / kFixVel;
-            s.V[i] = make_float4(v.x + q.x * inv, v.y + q.y * inv, v.z + q.z * inv, v.w);
-        }
-    }
-    __syncwarp();
-}
-
-// ------------------------------------------------------------------ one substep
-template <int NV, bool CONTACT>
-__device__ void substep(const FwdParams& P, const RodInfo& R, Smem<NV, CONTACT>& s, int lane, float h,
-                        const float* gpF, const M3* gRF, const M3* gR0, const M3* gR1, float c0, float c1,
-                        const float* act, int np) {
-    const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
-    const bool closed = R.flags & ROD_CLOSED;
-    const int nh = closed ? nv : nv - 2;
-    // --- hinge phase
-    for (int k = lane; k < nh; k += 32) {
-        const int i = closed ? k : k + 1;
-        const int a = (i == 0) ? ne - 1 : i - 1;
-        const int b = i;
-        const int im = (i == 0) ? nv - 1 : i - 1;
-        const int ip = (i + 1 == nv) ? 0 : i + 1;
-        float4 EDa = s.ED[a], EDb = s.ED[b], ETa = s.ET[a], ETb = s.ET[b], hg = s.HG[i];
-        HingeF<float> H;
-        hinge_forward(H, f3(s.X0[im]), f3(s.X0[i]), f3(s.X0[ip]), f3(ETa), f3(EDa), f3(ETb), f3(EDb), EDa.w,
-                      EDb.w, hg.w);
-        const float lbar = 0.5f * (ETa.w + ETb.w);
-        if (R.flags & ROD_PLASTIC) plastic_update(H.k0, H.k1, hg.x, hg.y, R.sy * lbar, R.rc);
-        const float il = 1.f / lbar;
-        const float gk0 = R.Bm * il * (H.k0 - hg.x), gk1 = R.Bm * il * (H.k1 - hg.y);
-        const float gm = R.beta * il * (H.m - hg.z);
-        V3<float> gxm, gxi, gxp;
-        float gta, gtb;
-        hinge_reverse<float, false>(H, f3(ETa), f3(EDa), f3(ETb), f3(EDb), gk0, gk1, gm, 0.f, gxm, gxi, gxp, gta,
-                                    gtb, nullptr, nullptr, nullptr, nullptr);
-        s.HB0[i] = f4(gxm, gta);
-        s.HB1[i] = f4(gxi, gtb);
-        s.HB2[i] = f4(gxp, 0.f);
-        s.ND[b] = f4(H.b.d1r, 0.f);
-        if (!closed && i == 1) s.ND[0] = f4(H.a.d1r, 0.f);
-        s.HG[i] = make_float4(hg.x, hg.y, hg.z, H.mref);
-    }
-    __syncwarp();
-    // --- vertex phase
-    const SceneDev& sc = P.scene;
-    for (int i = lane; i < nv; i += 32) {
-        const float4 xi4 = s.X0[i];
-        const V3<float> xi = f3(xi4);
-        V3<float> g = zf3();
-        auto has_h = [&](int j) { return closed || (j >= 1 && j <= nv - 2); };
-        const int ip = (i + 1 == nv) ? 0 : i + 1;
-        const int im = (i == 0) ? nv - 1 : i - 1;
-        float gth = 0.f;
-        const bool has_e = closed || i < nv - 1;          // edge i starts here
-        if (has_h(i)) {
-            float4 q = s.HB1[i];
-            g += f3(q);
-            gth += q.w;
-        }
-        if ((closed || i + 1 <= nv - 2) && has_h(ip) && (closed || i + 1 < nv)) {
-            float4 q = s.HB0[ip];
-            g += f3(q);
-            if (has_e) gth += q.w;
-        }
-        if ((closed || i >= 2) && has_h(im)) g += f3(s.HB2[im]);
-        V3<float> t_i = zf3();
-        float ell_i = 0.f;
-        if (has_e) {
-            V3<float> e = f3(s.X0[ip]) - xi;
-            ell_i = sqrtf(dot(e, e));
-            t_i = e / ell_i;
-            if (R.kA > 0.f) {
-                float eb = P.ES[e0 + i].x;
-                g -= (R.kA * (ell_i / eb - 1.f)) * t_i;
-            }
-        }
-        if (R.kA > 0.f && (closed || i >= 1)) {
-            const int j = im;   // edge i-1 ends here
-            V3<float> e = xi - f3(s.X0[j]);
-            float ell = sqrtf(dot(e, e));
-            float eb = P.ES[e0 + j].x;
-            g += (R.kA * (ell / eb - 1.f) / ell) * e;
-        }
-        float4 vi = s.V[i];
-        const float4 kin = P.KIN[v0 + i];
-        const int kind = (int)kin.w;
-        // displacement d of this substep (positions are only formed at its end, so the rebuilt
-        // velocity d/h carries no cancellation error from |x| >> |h v|)
-        V3<float> v2 = zf3(), d = zf3();
-        float4 nd_out = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (kind == 0) {
-            V3<float> grav = f3(0.f, 0.f, -sc.gravity);
-            V3<float> acc = (-xi4.w) * g + grav - R.cd * f3(vi);
-            V3<float> v1 = f3(vi) + h * acc;
-            // pose at the substep start for the rigid contact
-            float gp0[6];
-            for (int q = 0; q < R.ngrip; ++q)
-                for (int c = 0; c < 3; ++c) gp0[3 * q + c] = gpF[12 * q + c] + c0 * act[6 * q + c];
-            v2 = rigid_contact(sc, R, xi, v1, gp0, gR0, act);
-            d = h * v2;
-        } else if (kind >= 2) {
-            const int q = kind - 2;
-            const V3<float> off = f3(kin);
-            V3<float> p1 = f3(gpF[12 * q] + c1 * act[6 * q], gpF[12 * q + 1] + c1 * act[6 * q + 1],
-                              gpF[12 * q + 2] + c1 * act[6 * q + 2]);
-            nd_out = f4(p1 + mul(gR1[q], off), 1.f);      // absolute target at the substep end
-            d = (c1 - c0) * f3(act[6 * q], act[6 * q + 1], act[6 * q + 2]) + (mul(gR1[q], off) - mul(gR0[q], off));
-            v2 = d / h;
-        }
-        float om1 = vi.w;
-        if (has_e) {
-            const float invI = P.ES[e0 + i].y;
-            om1 = vi.w + h * (-gth * invI - R.cd * vi.w);
-            float4 ed = s.ED[i];
-            V3<float> d1r = nh > 0 ? f3(s.ND[i]) : zf3();
-            if (nh == 0) {   // a single open edge has no hinge: transport its frame here
-                EdgeF<float> E;
-                edge_forward(E, xi, f3(s.X0[ip]), f3(s.ET[i]), f3(ed), ed.w);
-                d1r = E.d1r;
-            }
-            s.ED[i] = f4(d1r, ed.w + h * om1);
-            s.ET[i] = f4(t_i, P.ES[e0 + i].x);
-        }
-        s.ND[i] = nd_out;
-        s.X[i] = f4(d, xi4.w);
-        s.V[i] = f4(v2, om1);
-    }
-    __syncwarp();
-    // --- PBD
-    const bool lenc = R.flags & (ROD_INEXT | ROD_SLIMIT);
-    if (lenc || np > 0) {
-        for (int it = 0; it < sc.n_iter; ++it) {
-            if (lenc) {
-                inext_color(R, s, lane, 0, closed);
-                inext_color(R, s, lane, 1, closed);
-                if (closed && (ne & 1)) inext_color(R, s, lane, 2, closed);
-            }
-            if (CONTACT && np > 0) contact_sweep(R, s, lane, np, it == 0);
-        }
-    }
-    // --- velocity from the displacement, friction, new positions
-    const float ih = 1.f / h;
-    for (int i = lane; i < nv; i += 32) {
-        float4 d = s.X[i], v = s.V[i];
-        s.V[i] = make_float4(d.x * ih, d.y * ih, d.z * ih, v.w);
-    }
-    __syncwarp();
-    if (CONTACT && np > 0) self_friction(R, s, lane, np, h, sc.mu_self);
-    for (int i = lane; i < nv; i += 32) {
-        float4 x0 = s.X0[i], d = s.X[i], nd = s.ND[i];
-        float4 x = nd.w > 0.5f ? make_float4(nd.x, nd.y, nd.z, x0.w)
-                               : make_float4(x0.x + d.x, x0.y + d.y, x0.z + d.z, x0.w);
-        s.X0[i] = x;
-        s.X[i] = x;
-    }
-    __syncwarp();
-}
-
-// ------------------------------------------------------------------ the persistent kernel
-__device__ __forceinline__ void write_state(const StateRef& D, long long offV, long long offE, long long offB,
-                                            const RodInfo& R, int rod, int lane, const float4* X, const float4* V,
-                                            const float4* ED, const float4* ET, const float4* HG, const float* gp) {
-    for (int i = lane; i < R.nv; i += 32) {
-        D.X[offV + R.v0 + i] = X[i];
-        D.Vl[offV + R.v0 + i] = V[i];
-        D.HG[offV + R.v0 + i] = HG[i];
-    }
-    for (int j = lane; j < R.ne; j += 32) {
-        D.ED[offE + R.e0 + j] = ED[j];
-        D.ET[offE + R.e0 + j] = ET[j];
-    }
-    if (lane < 24) D.GP[offB + 24LL * rod + lane] = gp[lane];
-}
-
-template <int NV, bool CONTACT>
-__global__ void __launch_bounds__(256) fwd_kernel(FwdParams P) {
-    extern __shared__ float4 dyn_smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Smem<NV, CONTACT> s(dyn_smem + warp * (warp_smem_bytes(NV, CONTACT) / 16));
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(P.counter, 1);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= P.n_order) break;
-        const int rod = P.order[item];
-        const RodInfo R = P.rods[rod];
-        const bool closed = R.flags & ROD_CLOSED;
-        const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
-        const float h = P.scene.dt / (float)nsub;
-        for (int i = lane; i < R.nv; i += 32) {
-            float4 x = P.S.X[R.v0 + i];
-            s.X[i] = x;
-            s.X0[i] = x;
-            s.V[i] = P.S.Vl[R.v0 + i];
-            s.HG[i] = P.S.HG[R.v0 + i];
-        }
-        for (int j = lane; j < R.ne; j += 32) {
-            s.ED[j] = P.S.ED[R.e0 + j];
-            s.ET[j] = P.S.ET[R.e0 + j];
-        }
-        // gripper poses of the frame start (every lane holds a copy)
-        float gpF[24];
-#pragma unroll
-        for (int k = 0; k < 24; ++k) gpF[k] = P.S.GP[24LL * rod + k];
-        M3 gRF[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int k = 0; k < 9; ++k) gRF[q].m[k] = gpF[12 * q + 3 + k];
-        __syncwarp();
-        unsigned bad = 0;
-        for (int f = 0; f < P.frames; ++f) {
-            const int gf = P.frame0 + f;
-            if (P.ck_every > 0 && gf % P.ck_every == 0 && gf / P.ck_every < P.ck_count) {
-                const long long c = gf / P.ck_every;
-                write_state(P.ck, c * P.ck_strideV, c * P.ck_strideE, c * P.ck_strideB, R, rod, lane, s.X, s.V,
-                            s.ED, s.ET, s.HG, gpF);
-            }
-            float act[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-                act[k] = P.actions ? P.actions[((long long)f * P.B + rod) * 12 + k] : 0.f;
-            int np = 0;
-            if (CONTACT && (R.flags & ROD_SELF)) {
-                bool ovf = false;
-                np = broad_phase(R, s, lane, closed, ovf);
-                if (ovf) bad |= 2u;
-            }
-            M3 gR0[2], gR1[2];
-            gR0[0] = gRF[0];
-            gR0[1] = gRF[1];
-            for (int sb = 0; sb < nsub; ++sb) {
-                const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
-                for (int q = 0; q < R.ngrip; ++q)
-                    gR1[q] = matmul(expmap(f3(c1 * act[6 * q + 3], c1 * act[6 * q + 4], c1 * act[6 * q + 5])), gRF[q]);
-                substep<NV, CONTACT>(P, R, s, lane, h, gpF, gRF, gR0, gR1, c0, c1, act, np);
-                gR0[0] = gR1[0];
-                gR0[1] = gR1[1];
-            }
-            // frame end: gripper poses, diagnostics
-            for (int q = 0; q < R.ngrip; ++q) {
-                gRF[q] = matmul(expmap(f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5])), gRF[q]);
-                for (int c = 0; c < 3; ++c) gpF[12 * q + c] += act[6 * q + c];
-                for (int k = 0; k < 9; ++k) gpF[12 * q + 3 + k] = gRF[q].m[k];
-            }
-            bool nf = false;
-            for (int i = lane; i < R.nv; i += 32) {
-                float4 x = s.X[i], v = s.V[i];
-                nf |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) && isfinite(v.y) &&
-                        isfinite(v.z) && isfinite(v.w));
-                if (P.xframes) reinterpret_cast<float4*>(P.xframes)[(long long)f * P.nvert_total + R.v0 + i] = x;
-            }
-            if (__any_sync(kFull, nf)) bad |= 1u;
-            if (f + 1 == P.frames) {
-                if (R.flags & ROD_INEXT) {
-                    double r = 0.0;
-                    for (int j = lane; j < R.ne; j += 32) {
-                        int j1 = (j + 1 == R.nv) ? 0 : j + 1;
-                        V3<float> e = f3(s.X[j1]) - f3(s.X[j]);
-                        r += fabs((double)sqrtf(dot(e, e)) - (double)s.ET[j].w);
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
-                    if (lane == 0) P.residual[rod] = r;
-                }
-                if (lane == 0) P.npairs[rod] = np;
-            }
-        }
-        write_state(P.S, 0, 0, 0, R, rod, lane, s.X, s.V, s.ED, s.ET, s.HG, gpF);
-        if (lane == 0 && bad) atomicOr(&P.status[rod], bad);
-        __syncwarp();
-    }
-}
-
-// ------------------------------------------------------------------ launchers
-template <int NV, bool C>
-static cudaError_t launch_fwd_t(const FwdParams& P, int grid, int warps, cudaStream_t st) {
-    size_t smem = warp_smem_bytes(NV, C) * warps;
-    auto k = fwd_kernel<NV, C>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, 32 * warps, smem, st>>>(P);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_forward(const FwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st) {
     switch (nv_max) {
-        case 32: return contact ? launch_fwd_t<32, true>(P, grid, warps, st) : launch_fwd_t<32, false>(P, grid, warps, st);
-        case 64: return contact ? launch_fwd_t<64, true>(P, grid, warps, st) : launch_fwd_t<64, false>(P, grid, warps, st);
-        case 128: return contact ? launch_fwd_t<128, true>(P, grid, warps, st) : launch_fwd_t<128, false>(P, grid, warps, st);
-        case 256: return contact ? launch_fwd_t<256, true>(P, grid, warps, st) : launch_fwd_t<256, false>(P, grid, warps, st);
+        case 32: return launch_forward_nv32(P, contact, grid, warps, st);
+        case 64: return launch_forward_nv64(P, contact, grid, warps, st);
+        case 128: return launch_forward_nv128(P, contact, grid, warps, st);
+        case 256: return launch_forward_nv256(P, contact, grid, warps, st);
     }
     return cudaErrorInvalidValue;
 }
 
-template <int NV, bool C>
-static int occ_t(int warps) {
-    size_t smem = warp_smem_bytes(NV, C) * warps;
-    auto k = fwd_kernel<NV, C>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * warps, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return nb;
-}
-
 int forward_blocks_per_sm(int nv_max, bool contact, int warps) {
     switch (nv_max) {
-        case 32: return contact ? occ_t<32, true>(warps) : occ_t<32, false>(warps);
-        case 64: return contact ? occ_t<64, true>(warps) : occ_t<64, false>(warps);
-        case 128: return contact ? occ_t<128, true>(warps) : occ_t<128, false>(warps);
-        case 256: return contact ? occ_t<256, true>(warps) : occ_t<256, false>(warps);
+        case 32: return forward_occ_nv32(contact, warps);
+        case 64: return forward_occ_nv64(contact, warps);
+        case 128: return forward_occ_nv128(contact, warps);
+        case 256: return forward_occ_nv256(contact, warps);
     }
     return 0;
 }

@@ -68,4 +68,32 @@ struct FwdParams {
     SceneDev scene;
 };
 
+struct BwdParams {
+    const RodInfo* rods;
+    const int* order;
+    int n_order;
+    int* counter;
+    StateRef ck;
+    long long ck_strideV, ck_strideE, ck_strideB;
+    int ck_every, ck_count;
+    const float4* KIN;
+    const float2* ES;
+    const float* actions;   // recorded [F][B][12]
+    int frames, B, force_nsub;
+    const float4* dLdx;     // [V] or null
+    const float4* dLdv;     // [V] or null
+    const float* dLdth;     // [Etot] or null
+    float* gact;            // [F][B][12] or null
+    float* gmat;            // [B][5] or null
+    float4* gx0;            // [V] or null
+    float4* gv0;            // [V] or null
+    float* gth0;            // [Etot] or null
+    float4* gtb0;           // [Etot] cotangent of the initial base tangents
+    float4* gd1b0;          // [Etot] cotangent of the initial base d1
+    char* scratch;
+    size_t slot_bytes;
+    int K, nsub_max;
+    SceneDev scene;
+};
+
 }  // namespace dlo

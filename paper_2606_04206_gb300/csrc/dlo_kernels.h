@@ -15,6 +15,25 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int NV, bool contact) {
     return (size_t)(10 * NV) * 16 + (contact ? ((size_t)(4 * NV) * 16 + (size_t)NV * 16 + (size_t)(2 * NV) * 4) : 0);
 }
 
+// Per size class (dlo_nv*.cu).
+cudaError_t launch_forward_nv32(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int forward_occ_nv32(bool c, int warps);
+cudaError_t launch_backward_nv32(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int backward_occ_nv32(bool c, int warps);
+cudaError_t launch_forward_nv64(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int forward_occ_nv64(bool c, int warps);
+cudaError_t launch_backward_nv64(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int backward_occ_nv64(bool c, int warps);
+cudaError_t launch_forward_nv128(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int forward_occ_nv128(bool c, int warps);
+cudaError_t launch_backward_nv128(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int backward_occ_nv128(bool c, int warps);
+cudaError_t launch_forward_nv256(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int forward_occ_nv256(bool c, int warps);
+cudaError_t launch_backward_nv256(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int backward_occ_nv256(bool c, int warps);
+cudaError_t launch_backward(const BwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
+int backward_blocks_per_sm(int nv_max, bool contact, int warps);
 cudaError_t launch_forward(const FwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
 int forward_blocks_per_sm(int nv_max, bool contact, int warps);
 

@@ -3,8 +3,3 @@ extern "C" dlo_status dlo_step_plain(dlo_ctx* c, const float*, int, int) {
     if (!c) return DLO_ERR_INVALID_ARG;
     return set_err(c, DLO_ERR_STATE, "plain comparator not built");
 }
-extern "C" dlo_status dlo_backward(dlo_ctx* c, const float*, const float*, const float*, float*, float*, float*,
-                                   float*, float*) {
-    if (!c) return DLO_ERR_INVALID_ARG;
-    return set_err(c, DLO_ERR_STATE, "backward not built");
-}

@@ -25,3 +25,62 @@ def actions_dev(prob, f0=0, f1=None):
 
 def rel_inf(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+def oracle_gradients(prob, frames, wx, wv, wth):
+    """Autograd gradients of L = sum(wx * x_T) + sum(wv * (v_T, twist rate)) + sum(wth * theta_T)
+    through the FP64 oracle rollout, with respect to the initial state, the actions and the
+    per-rod material (K, E, G, yield curvature, damping)."""
+    import torch as T
+    p = prob
+    leaves = dict(x0=T.tensor(p.x0, requires_grad=True), v0=T.tensor(p.v0, requires_grad=True),
+                  th0=T.tensor(p.theta0, requires_grad=True), om0=T.tensor(p.omega0, requires_grad=True),
+                  act=T.tensor(p.actions[:frames], requires_grad=True))
+    mats = {k: T.tensor(np.asarray(getattr(p, k), np.float64), requires_grad=True)
+            for k in ("K", "E", "G", "yield_curv", "damping")}
+    sim = OracleSim(p, params=mats)
+    sim.set_state(leaves["x0"], leaves["v0"], leaves["th0"], leaves["om0"])
+    sim.step(leaves["act"], frames, diff=True)
+    st = sim.get_state(as_numpy=False)
+    om_w = np.zeros(int(p.edge_off[-1]))
+    vo, eo = p.vert_off, p.edge_off
+    for b in range(p.batch):
+        ne = eo[b + 1] - eo[b]
+        om_w[eo[b]:eo[b + 1]] = wv[vo[b]:vo[b] + ne, 3]
+    L = ((st["x"] * T.tensor(wx[:, :3])).sum() + (st["v"] * T.tensor(wv[:, :3])).sum()
+         + (st["omega"] * T.tensor(om_w)).sum() + (st["theta"] * T.tensor(wth)).sum())
+    names = ["x0", "v0", "th0", "om0", "act"] + list(mats)
+    inputs_ = [leaves[n] for n in names[:5]] + [mats[n] for n in names[5:]]
+    g = T.autograd.grad(L, inputs_, allow_unused=True)
+    out = {n: (gi.numpy() if gi is not None else np.zeros(tuple(x.shape))) for n, gi, x in zip(names, g, inputs_)}
+    out["material"] = np.stack([out[k] for k in ("K", "E", "G", "yield_curv", "damping")], 1)
+    return out, float(L.detach())
+
+
+def device_gradients(sim, prob, frames, wx, wv, wth, substeps=0):
+    """The C-ABI backward for the same loss; returns numpy arrays in the oracle's layout."""
+    import torch as T
+    dev = sim.device
+    sim.reset()
+    sim.begin_rollout(frames)
+    sim.step(T.as_tensor(np.ascontiguousarray(prob.actions[:frames], np.float32), device=dev), frames, substeps)
+    g = sim.backward(T.as_tensor(wx, dtype=T.float32, device=dev), T.as_tensor(wv, dtype=T.float32, device=dev),
+                     T.as_tensor(wth, dtype=T.float32, device=dev))
+    g = {k: v.double().cpu().numpy() for k, v in g.items()}
+    vo, eo = prob.vert_off, prob.edge_off
+    om = np.zeros(int(eo[-1]))
+    for b in range(prob.batch):
+        ne = eo[b + 1] - eo[b]
+        om[eo[b]:eo[b + 1]] = g["v0"][vo[b]:vo[b] + ne, 3]
+    return dict(x0=g["x0"][:, :3], v0=g["v0"][:, :3], om0=om, th0=g["theta0"], act=g["actions"],
+                material=g["material"])
+
+
+def grad_agreement(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    nb = np.linalg.norm(b)
+    if nb == 0:
+        return (0.0 if np.linalg.norm(a) == 0 else np.inf), 1.0
+    rel = np.linalg.norm(a - b) / nb
+    cos = float(a @ b / (np.linalg.norm(a) * nb + 1e-300))
+    return rel, cos
