@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput of the batched differentiable rod stepper (one JSON line on stdout).
+
+Workload: trajectory optimisation at scale -- 4096 rods x 128 vertices per GPU (one third
+each inextensible cable, elastic rope, plastic wire; App. B Table "sim_params" rows
+Wiring-post, Unknotting, Letter Art), two capsule grippers per rod with smooth random 6-DoF
+actions, ground plane, self-contact on, dt = 1e-3 s with 5 substeps (App. B.1), a 2000-frame
+rollout per step.  One step = the forward rollout (with HBM checkpoints) plus the backward
+pass for dL/d(actions, material, initial state) of L = mean |x_T - target|^2.
+
+value        rod-vertex-steps/s of forward + backward (rods x vertices x frames / time)
+fwd_value    the same for the forward rollout alone
+e2e          the same through the public API from pinned host buffers (copies included)
+roofline     the dominant kernel (the backward) against the FP32 CUDA-core peak, with
+             algorithmic operation counts per vertex-substep from tests/flop_count.cu
+cpu_baseline the FP64 oracle on the host cores, on a bounded sample of the same workload
+plain        the plain per-phase GPU step (dlo_step_plain) on the same rods
+
+`--impl reference` times the oracle instead (the reference arm of this benchmark).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rod-vertex-steps/s fwd and fwd+bwd at B=4096, vs plain GPU step at stated accuracy"
+UNIT = "rod-vertex-steps/s"
+# algorithmic FP32 operations per vertex-substep (tests/flop_count.cu counts them from the
+# kernels' own element templates; tests/test_flop_count.py keeps these in step)
+FLOPS_FWD_PER_VS = 921.3
+FLOPS_BWD_PER_VS = 3668.0
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--frames", type=int, default=2000)
+    ap.add_argument("--rods", type=int, default=4096)
+    ap.add_argument("--verts", type=int, default=128)
+    ap.add_argument("--no-self-contact", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--plain-frames", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "native" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, ws
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(tempfile.mkdtemp(), "clocks.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        load = [float(r[1]) for r in rows if float(r[3]) > 200.0] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- reference arm
+def oracle_rollout_rate(prob, frames, rods):
+    """FP64 oracle forward + reverse-mode backward on `rods` rods of the workload; returns
+    (rod-vertex-steps/s, seconds)."""
+    import numpy as np
+    import torch
+    from oracle import OracleSim
+    sub = prob.subset(rods, frames=frames)
+    t0 = time.perf_counter()
+    act = torch.tensor(sub.actions[:frames], requires_grad=True)
+    x0 = torch.tensor(sub.x0, requires_grad=True)
+    sim = OracleSim(sub)
+    sim.set_state(x0, torch.tensor(sub.v0), torch.tensor(sub.theta0), torch.tensor(sub.omega0))
+    sim.step(act, frames, diff=True)
+    x = sim.get_state(as_numpy=False)["x"]
+    L = ((x - torch.tensor(sub.target)) ** 2).sum(1).mean()
+    torch.autograd.grad(L, [act, x0])
+    dt = time.perf_counter() - t0
+    units = float(np.sum(sub.n_verts)) * frames
+    return units / dt, dt
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    import torch
+    from paper_2606_04206_gb300 import inputs
+    prob = inputs.trajopt(n_rods=4, frames=4, n=args.verts, self_contact=not args.no_self_contact)
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, dt = oracle_rollout_rate(prob, 2, [0, 1])
+        if i >= args.warmup:
+            rates.append((r, dt))
+    value = sum(r for r, _ in rates) / len(rates)
+    ms = 1e3 * sum(dt for _, dt in rates) / len(rates)
+    cores = torch.get_num_threads()
+    sample = f"2 rods x {args.verts} vertices x 2 frames (5 substeps) per step, FP64 forward + autograd backward"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"trajopt {args.rods} rods x {args.verts} vertices (oracle sample)",
+                       "frames_per_step": 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- native arm
+def run_native(args, rank, ws):
+    import numpy as np
+    import torch
+    from paper_2606_04206_gb300 import build, dlo, inputs
+
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    F, R, N = args.frames, args.rods, args.verts
+    prob = inputs.trajopt(n_rods=R, frames=F, seed=4000 + rank, n=N, self_contact=not args.no_self_contact)
+    sim = dlo.DloSim(prob)
+    V = sim.V
+    units = float(R) * N * F
+    acts = torch.as_tensor(np.ascontiguousarray(prob.actions, np.float32), device=dev)
+    target = torch.zeros(V, 4, device=dev)
+    target[:, :3] = torch.as_tensor(prob.target, dtype=torch.float32, device=dev)
+    x0, v0, th0 = sim.tensors_from_problem()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def dL_dx():
+        x, _, _ = sim.get_state()
+        return (2.0 / V) * (x - target)
+
+    def one_step(record):
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        l0 = sim.query(dlo.Q_LAUNCHES)
+        ev[0].record(stream)
+        sim.set_state(x0, v0, th0)
+        sim.begin_rollout(F)
+        sim.step(acts, F)
+        ev[1].record(stream)
+        g = dL_dx()
+        gb = torch.cuda.Event(enable_timing=True)
+        gb.record(stream)
+        sim.backward(dL_dx=g, want=("actions", "material", "x0"))
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        l1 = sim.query(dlo.Q_LAUNCHES)
+        return ev[0].elapsed_time(ev[1]), gb.elapsed_time(ev[2]), ev[0].elapsed_time(ev[2]), l1 - l0
+
+    for _ in range(args.warmup):
+        one_step(False)
+    clocks = Clocks(torch.cuda.current_device())
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_fwd, t_bwd, t_all, launches = [], [], [], []
+    for _ in range(args.steps):
+        a, b, c, n = one_step(True)
+        t_fwd.append(a)
+        t_bwd.append(b)
+        t_all.append(c)
+        launches.append(n)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms_step = max_over_ranks(sum(t_all) / len(t_all), ws)
+    ms_fwd = max_over_ranks(sum(t_fwd) / len(t_fwd), ws)
+    ms_bwd = max_over_ranks(sum(t_bwd) / len(t_bwd), ws)
+    value = units * ws / (ms_step / 1e3)
+    fwd_value = units * ws / (ms_fwd / 1e3)
+
+    # end-to-end through the public API from pinned host memory
+    h_acts = torch.empty_like(acts, device="cpu").pin_memory()
+    h_acts.copy_(acts)
+    h_state = [t.cpu().pin_memory() for t in (x0, v0, th0)]
+    h_target = target.cpu().pin_memory()
+    h_gact = torch.empty(F, R, 2, 6).pin_memory()
+    h_loss = torch.empty(1).pin_memory()
+    e2e = []
+    for _ in range(args.e2e_steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_acts = h_acts.to(dev, non_blocking=True)
+        xs, vs, ts = (t.to(dev, non_blocking=True) for t in h_state)
+        tg = h_target.to(dev, non_blocking=True)
+        sim.set_state(xs, vs, ts)
+        sim.begin_rollout(F)
+        sim.step(d_acts, F)
+        x, _, _ = sim.get_state()
+        loss = ((x - tg)[:, :3] ** 2).sum(1).mean()
+        g = sim.backward(dL_dx=(2.0 / V) * (x - tg), want=("actions",))
+        h_gact.copy_(g["actions"], non_blocking=True)
+        h_loss.copy_(loss.reshape(1), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    ms_e2e = max_over_ranks(sum(e2e) / len(e2e), ws)
+    h2d = h_acts.numel() * 4 + sum(t.numel() * 4 for t in h_state) + h_target.numel() * 4
+    d2h = h_gact.numel() * 4 + 4
+
+    # roofline of the dominant kernel (the backward): algorithmic FP32 operations per launch
+    nsub = int(np.max(sim.query(dlo.Q_SUBSTEPS)))
+    vs_units = float(R) * N * F * nsub
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    peak_tflops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    bwd_tflops = FLOPS_BWD_PER_VS * vs_units / (ms_bwd / 1e3) / 1e12
+    fwd_tflops = FLOPS_FWD_PER_VS * vs_units / (ms_fwd / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "bwd_kernel (dlo_backward)", "achieved": bwd_tflops,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": bwd_tflops / peak_tflops, "traffic": None,
+                "peak_basis": f"FP32 CUDA cores: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                              f"{max_mhz:.0f} MHz", "forward": {"achieved": fwd_tflops,
+                                                                "frac": fwd_tflops / peak_tflops}}
+
+    # plain per-phase GPU step on the same rods (short rollout, forward only)
+    plain = None
+    try:
+        pf = args.plain_frames
+        sim.set_state(x0, v0, th0)
+        sim.step_plain(acts[:2].contiguous(), 2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sim.set_state(x0, v0, th0)
+        e0.record(stream)
+        sim.step_plain(acts[:pf].contiguous(), pf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        pv = float(R) * N * pf / (ms_p / 1e3)
+        plain = {"fwd_value": pv, "unit": UNIT, "frames": pf, "speedup_fwd": fwd_value / ws / pv}
+    except Exception as exc:   # the comparator is optional for the line; say why it is missing
+        plain = {"unavailable": str(exc)[:200]}
+
+    # CPU baseline: the FP64 oracle on a bounded sample of the same workload (rank 0 only)
+    cpu = None
+    if rank == 0:
+        rate, dt = oracle_rollout_rate(prob, 1, [0, 1])
+        frames = max(1, min(20, int(args.cpu_seconds / max(dt, 1e-3))))
+        rate, dt = oracle_rollout_rate(prob, frames, [0, 1])
+        cpu = {"value": rate, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": f"2 rods x {N} vertices x {frames} frames of the same workload, FP64 forward + "
+                         f"autograd backward, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"trajopt: {R} rods x {N} vertices per GPU, {F} frames (dt 1e-3 s, "
+                                       f"{nsub} substeps), cable/rope/wire thirds, 2 grippers, ground, "
+                                       f"self-contact={'on' if not args.no_self_contact else 'off'}",
+                           "rods_per_gpu": R, "verts_per_rod": N, "frames": F, "substeps": nsub,
+                           "n_iter_pbd": 10, "checkpoint_every": int(sim.query(dlo.Q_CONFIG)[1]),
+                           "l2": "256 MiB buffer written before every timed step"},
+                "fwd_value": fwd_value, "ms_fwd": ms_fwd, "ms_bwd": ms_bwd,
+                "e2e": {"value": units * ws / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(max(launches)), "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+    else:
+        run_native(args, rank, ws)
+
+
+if __name__ == "__main__":
+    main()

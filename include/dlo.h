@@ -162,7 +162,8 @@ enum {
     DLO_Q_CONFIG = 4,        /* int [4]: warps per CTA, checkpoint interval, CTAs, smem/CTA */
     DLO_Q_RESIDUAL = 5,      /* double [B]: sum |C_j| of the inextensibility constraints
                                 after the last frame, accumulated in FP64 */
-    DLO_Q_PAIRS = 6,         /* int [B]: self-contact candidate pairs in the last frame */
+    DLO_Q_PAIRS = 6,         /* int [B]: largest self-contact candidate count of any frame of the
+                                last dlo_step (capacity: 4 per vertex of the rod's size class) */
     DLO_Q_LAUNCHES = 7,      /* long long: kernels launched by this context so far */
     DLO_Q_MASS = 8           /* float [V][4]: (mass, inverse mass, kind, 0); kind 0 free,
                                 1 pinned, 2/3 grasped by gripper 0/1 (host out) */

@@ -159,8 +159,14 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
     std::vector<int> warps(c->buckets.size()), grid(c->buckets.size()), nsmax(c->buckets.size());
     for (size_t k = 0; k < c->buckets.size(); ++k) {
         const Bucket& bk = c->buckets[k];
-        int w = bk.warps, nb = 0;
-        while (w >= 1 && (nb = backward_blocks_per_sm(bk.nv_max, bk.contact, w)) < 1) w >>= 1;
+        int w = 0, nb = 0;
+        for (int rpc = 1; rpc <= 16; ++rpc) {
+            const int b = backward_blocks_per_sm(bk.nv_max, bk.contact, rpc);
+            if (b >= 1 && rpc * b >= w * nb) {
+                w = rpc;
+                nb = b;
+            }
+        }
         if (w < 1) return set_err(c, DLO_ERR_INVALID_ARG, "rod too large for the backward kernel's shared memory");
         int ns = force;
         if (!ns)

@@ -246,7 +246,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         R.contact_d = (float)(2.0 * r + opt->contact_margin * r);
         R.cell = (float)(R.contact_d + 1.5 * lmax);
         R.eps = (float)(opt->eps_soft * r);
-        R.pair_cap = std::min(2 * ne, 2 * nv_bucket(nv));
+        R.pair_cap = kPairsPerVertex * nv_bucket(nv);
         R.pair_off = 0;
     }
     c->rods_h = rods;

@@ -18,8 +18,10 @@
 
 namespace dlo {
 
+constexpr int kBwdMaxThreads = 256;   // per CTA (register budget of the backward kernel)
+
 __host__ __device__ constexpr size_t bwd_smem_bytes(int NV, bool contact) {
-    return warp_smem_bytes(NV, contact) + (size_t)(10 * NV) * 16;
+    return rod_smem_bytes(NV, contact) + (size_t)(10 * NV) * 16;
 }
 
 // ------------------------------------------------------------------ small helpers
@@ -105,35 +107,35 @@ struct AdjArrays {
 };
 
 // State snapshot layout in the per-warp scratch: X[NV], V[NV], HG[NV], ED[NV], ET[NV].
-template <int NV, bool C>
-__device__ __forceinline__ void save_state(float4* dst, const RodInfo& R, int lane, const Smem<NV, C>& s) {
-    for (int i = lane; i < R.nv; i += 32) {
+template <int NV, bool C, int TPR>
+__device__ __forceinline__ void save_state(float4* dst, const RodInfo& R, const Grp<TPR>& g, const Smem<NV, C>& s) {
+    for (int i = g.tid; i < R.nv; i += TPR) {
         dst[i] = s.X0[i];
         dst[NV + i] = s.V[i];
         dst[2 * NV + i] = s.HG[i];
     }
-    for (int j = lane; j < R.ne; j += 32) {
+    for (int j = g.tid; j < R.ne; j += TPR) {
         dst[3 * NV + j] = s.ED[j];
         dst[4 * NV + j] = s.ET[j];
     }
 }
-template <int NV, bool C>
-__device__ __forceinline__ void load_state(const float4* src, const RodInfo& R, int lane, Smem<NV, C>& s) {
-    for (int i = lane; i < R.nv; i += 32) {
+template <int NV, bool C, int TPR>
+__device__ __forceinline__ void load_state(const float4* src, const RodInfo& R, const Grp<TPR>& g, Smem<NV, C>& s) {
+    for (int i = g.tid; i < R.nv; i += TPR) {
         float4 x = src[i];
         s.X0[i] = x;
         s.X[i] = x;
         s.V[i] = src[NV + i];
         s.HG[i] = src[2 * NV + i];
     }
-    for (int j = lane; j < R.ne; j += 32) {
+    for (int j = g.tid; j < R.ne; j += TPR) {
         s.ED[j] = src[3 * NV + j];
         s.ET[j] = src[4 * NV + j];
     }
-    __syncwarp();
+    g.sync();
 }
 
-// Per-lane pose cotangents of one substep (two grippers x 3).
+// Per-g.tid pose cotangents of one substep (two grippers x 3).
 struct PoseAdj {
     float ps0[6], phs0[6], ps1[6], phs1[6], vp[6], w[6];
     __device__ void zero() {
@@ -153,10 +155,10 @@ __device__ __forceinline__ V3<float> get3(const float* a, int q) { return f3(a[3
 // for a self-contact rod, the frame's pair list and the projection data of the first
 // iteration; the cotangent arrays hold the cotangents of S_{n+1}.  On exit they hold those
 // of S_n.  gm accumulates (kA, Bm, beta, sigma_y, c_d) cotangents, lpf/lphif the frame-start
-// pose cotangents and ga the frame's action cotangents (all per lane).
-template <int NV, bool CONTACT>
+// pose cotangents and ga the frame's action cotangents (all per g.tid).
+template <int NV, bool CONTACT, int TPR>
 __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, CONTACT>& s,
-                                AdjArrays<NV, CONTACT>& a, const float4* SN, int lane, float h, const Pose& F0,
+                                AdjArrays<NV, CONTACT>& a, const float4* SN, const Grp<TPR>& g, float h, const Pose& F0,
                                 const float* act, const M3* gR0, const M3* gR1, float c0, float c1, int np,
                                 double* gm, float* lpf, float* lphif, float* ga) {
     const SceneDev& sc = P.scene;
@@ -168,9 +170,9 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
     const float rsum = 2.f * R.radius;
     PoseAdj pa;
     pa.zero();
-    for (int i = lane; i < nv; i += 32) a.LP0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = g.tid; i < nv; i += TPR) a.LP0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     // ---- B1: positions at the substep end
-    for (int i = lane; i < nv; i += 32) {
+    for (int i = g.tid; i < nv; i += TPR) {
         const float4 kin = P.KIN[v0 + i];
         const int kind = (int)kin.w;
         float4 lx = a.LX[i];
@@ -185,22 +187,22 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
             a.LD[i] = make_float4(lx.x, lx.y, lx.z, 0.f);
         }
     }
-    __syncwarp();
+    g.sync();
     // ---- B2: self-contact friction
     if (CONTACT && np > 0) {
         float4* T0 = s.ND;        // displacements at the first contact sweep
         float4* LTMP = s.HB0;
-        for (int i = lane; i < nv; i += 32) {
+        for (int i = g.tid; i < nv; i += TPR) {
             T0[i] = SN[i];
             LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncwarp();
+        g.sync();
         if (lenc) {
-            inext_color_arr(R, s.X0, T0, s.ET, lane, 0, closed);
-            inext_color_arr(R, s.X0, T0, s.ET, lane, 1, closed);
-            if (closed && (ne & 1)) inext_color_arr(R, s.X0, T0, s.ET, lane, 2, closed);
+            inext_color_arr<TPR>(R, s.X0, T0, s.ET, g, 0, closed);
+            inext_color_arr<TPR>(R, s.X0, T0, s.ET, g, 1, closed);
+            if (closed && (ne & 1)) inext_color_arr<TPR>(R, s.X0, T0, s.ET, g, 2, closed);
         }
-        for (int p = lane; p < np; p += 32) {
+        for (int p = g.tid; p < np; p += TPR) {
             if (!(s.fr1[p].w > 0.f)) continue;
             uint32_t pr = s.pairs[p];
             const int a0 = pr & 0xffff, q0 = pr >> 16;
@@ -239,15 +241,15 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
                 atomic_add3(&LTMP[idx[k]], f3(lin[12 + 3 * k], lin[13 + 3 * k], lin[14 + 3 * k]));
             }
         }
-        __syncwarp();
-        for (int i = lane; i < nv; i += 32) {
+        g.sync();
+        for (int i = g.tid; i < nv; i += TPR) {
             float4 l = a.LV[i], t = LTMP[i];
             a.LV[i] = make_float4(l.x + t.x, l.y + t.y, l.z + t.z, l.w);
         }
-        __syncwarp();
+        g.sync();
     }
     // ---- B3: velocity rebuilt from the displacement
-    for (int i = lane; i < nv; i += 32) {
+    for (int i = g.tid; i < nv; i += TPR) {
         const float4 kin = P.KIN[v0 + i];
         const int kind = (int)kin.w;
         (void)kin;
@@ -258,25 +260,25 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
         a.LD[i] = make_float4(d.x + lv.x, d.y + lv.y, d.z + lv.z, 0.f);
         a.LV[i] = make_float4(0.f, 0.f, 0.f, l.w);
     }
-    __syncwarp();
+    g.sync();
     // ---- B4: PBD iterations in reverse
     if (lenc || (CONTACT && np > 0)) {
         const int ncol = lenc ? ((closed && (ne & 1)) ? 3 : 2) : 0;
         float4* Cpre[4] = {s.HB0, s.HB1, s.HB2, s.ND};
         for (int it = sc.n_iter - 1; it >= 0; --it) {
-            for (int i = lane; i < nv; i += 32) Cpre[0][i] = SN[(size_t)it * NV + i];
-            __syncwarp();
+            for (int i = g.tid; i < nv; i += TPR) Cpre[0][i] = SN[(size_t)it * NV + i];
+            g.sync();
             for (int k = 0; k < ncol; ++k) {
-                for (int i = lane; i < nv; i += 32) Cpre[k + 1][i] = Cpre[k][i];
-                __syncwarp();
-                inext_color_arr(R, s.X0, Cpre[k + 1], s.ET, lane, k, closed);
+                for (int i = g.tid; i < nv; i += TPR) Cpre[k + 1][i] = Cpre[k][i];
+                g.sync();
+                inext_color_arr<TPR>(R, s.X0, Cpre[k + 1], s.ET, g, k, closed);
             }
             if (CONTACT && np > 0) {
                 const float4* Dc = Cpre[ncol];
                 float4* LTMP = a.LG;
-                for (int i = lane; i < nv; i += 32) LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                __syncwarp();
-                for (int p = lane; p < np; p += 32) {
+                for (int i = g.tid; i < nv; i += TPR) LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                g.sync();
+                for (int p = g.tid; p < np; p += TPR) {
                     uint32_t pr = s.pairs[p];
                     const int a0 = pr & 0xffff, q0 = pr >> 16;
                     const int idx[4] = {a0, (a0 + 1 == nv) ? 0 : a0 + 1, q0, (q0 + 1 == nv) ? 0 : q0 + 1};
@@ -317,8 +319,8 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
 #pragma unroll
                     for (int k = 0; k < 4; ++k) atomic_add3(&LTMP[idx[k]], f3(lin[3 * k], lin[3 * k + 1], lin[3 * k + 2]));
                 }
-                __syncwarp();
-                for (int i = lane; i < nv; i += 32) {
+                g.sync();
+                for (int i = g.tid; i < nv; i += TPR) {
                     float4 t = LTMP[i];
                     if (it == 0) {
                         float4 q = a.LP0[i];
@@ -328,14 +330,14 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
                     a.LD[i] = make_float4(ld.x + t.x, ld.y + t.y, ld.z + t.z, 0.f);
                     a.LX[i] = make_float4(lx.x + t.x, lx.y + t.y, lx.z + t.z, 0.f);
                 }
-                __syncwarp();
+                g.sync();
             }
             for (int k = ncol - 1; k >= 0; --k) {
                 const float4* D = Cpre[k];
                 int first, last;
                 color_range(ne, closed, k, first, last);
                 const bool inext = R.flags & ROD_INEXT;
-                for (int j = first + 2 * lane; j < last; j += 64) {
+                for (int j = first + 2 * g.tid; j < last; j += 2 * TPR) {
                     const int j1 = (j + 1 == nv) ? 0 : j + 1;
                     float4 A = D[j], B = D[j1];
                     V3<float> e = (f3(s.X0[j1]) - f3(s.X0[j])) + (f3(B) - f3(A));
@@ -361,12 +363,12 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
                     a.LX[j] = f4(f3(a.LX[j]) - le, 0.f);
                     a.LX[j1] = f4(f3(a.LX[j1]) + le, 0.f);
                 }
-                __syncwarp();
+                g.sync();
             }
         }
     }
     // ---- B5: vertex phase (rigid contact, symplectic Euler, gravity, damping, twist rate)
-    for (int i = lane; i < nv; i += 32) {
+    for (int i = g.tid; i < nv; i += TPR) {
         const float4 kin = P.KIN[v0 + i];
         const int kind = (int)kin.w;
         const float4 x4 = s.X0[i];
@@ -409,6 +411,16 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
                 bool on;
                 prim_respond<float>(k, sc, R, x, vs[k], gp, gax, vp, w, on);
                 if (!on) continue;
+                if (k < sc.n_planes) {   // plane: closed-form reverse (sdf = n.x - o, constant n)
+                    const V3<float> n = f3(sc.planes[k]);
+                    V3<float> lv, ln, lvr;
+                    float lsdf;
+                    contact_respond_rev(vs[k], dot(x, n) - sc.planes[k].w, n, zf3(), R.radius, R.eps, sc.mu_rigid,
+                                        sc.restitution, lam, lv, lsdf, ln, lvr);
+                    lx_acc += lsdf * n;
+                    lam = lv;
+                    continue;
+                }
                 const int nin = q >= 0 ? 18 : 6;
                 float lin[18];
 #pragma unroll 1
@@ -456,9 +468,9 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
         a.LV[i] = lvn;
         a.LG[i] = lg;
     }
-    __syncwarp();
+    g.sync();
     // ---- B8: per edge, reverse of the new reference-frame base and stretching second order
-    for (int j = lane; j < ne; j += 32) {
+    for (int j = g.tid; j < ne; j += TPR) {
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
         const float4 ed = s.ED[j], et = s.ET[j];
         EdgeF<float> E;
@@ -476,16 +488,16 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
         a.LT[j] = f4(gtb, 0.f);
         a.LE[j] = f4(gd1b, a.LE[j].w);
     }
-    __syncwarp();
-    for (int i = lane; i < nv; i += 32) {
+    g.sync();
+    for (int i = g.tid; i < nv; i += TPR) {
         V3<float> l = f3(a.LX[i]);
         if (closed || i < nv - 1) l -= f3(s.HB1[i]);
         if (closed || i > 0) l += f3(s.HB1[i == 0 ? ne - 1 : i - 1]);
         a.LX[i] = f4(l, 0.f);
     }
-    __syncwarp();
+    g.sync();
     // ---- B7: hinges: force second order (dual numbers), plasticity, its first-order reverse
-    for (int k = lane; k < nh; k += 32) {
+    for (int k = g.tid; k < nh; k += TPR) {
         const int i = closed ? k : k + 1;
         const int ea = (i == 0) ? ne - 1 : i - 1, eb = i;
         const int im = (i == 0) ? nv - 1 : i - 1, ip = (i + 1 == nv) ? 0 : i + 1;
@@ -547,7 +559,7 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
         }
         a.LK[i] = make_float4(lk0, lk1, 0.f, 0.f);
     }
-    __syncwarp();
+    g.sync();
     // ---- pose cotangents of this substep -> frame-start pose and the frame's actions
     const float idt = 1.f / sc.dt;
     for (int q = 0; q < R.ngrip; ++q) {
@@ -570,28 +582,28 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
 
 // ------------------------------------------------------------------ the backward kernel
 template <int NV, bool CONTACT>
-__global__ void __launch_bounds__(256) bwd_kernel(BwdParams P) {
+__global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
+    constexpr int TPR = threads_per_rod(NV);
     extern __shared__ float4 dyn_smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float4* base = dyn_smem + warp * (bwd_smem_bytes(NV, CONTACT) / 16);
+    const int rs = threadIdx.x / TPR;
+    float4* base = dyn_smem + rs * (bwd_smem_bytes(NV, CONTACT) / 16);
     Smem<NV, CONTACT> s(base);
-    AdjArrays<NV, CONTACT> a(base + warp_smem_bytes(NV, CONTACT) / 16);
-    const size_t slot = (size_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    AdjArrays<NV, CONTACT> a(base + rod_smem_bytes(NV, CONTACT) / 16);
+    const Grp<TPR> g{(int)(threadIdx.x % TPR), 1 + rs, s.red};
+    const size_t slot = (size_t)blockIdx.x * (blockDim.x / TPR) + rs;
     float4* L2 = reinterpret_cast<float4*>(P.scratch + slot * P.slot_bytes);
     const size_t E2 = 5 * NV + 6, E3 = 5 * NV;
     float4* L3 = L2 + (size_t)P.K * E2;
     float4* SN = L3 + (size_t)P.nsub_max * E3;
     const SceneDev& sc = P.scene;
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(P.counter, 1);
-        item = __shfl_sync(kFull, item, 0);
+        const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (item >= P.n_order) break;
         const int rod = P.order[item];
         const RodInfo R = P.rods[rod];
         const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
         const float h = sc.dt / (float)nsub;
-        for (int i = lane; i < R.nv; i += 32) {
+        for (int i = g.tid; i < R.nv; i += TPR) {
             float4 dx = P.dLdx ? P.dLdx[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 dv = P.dLdv ? P.dLdv[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
             if (!(R.flags & ROD_CLOSED) && i == R.nv - 1) dv.w = 0.f;
@@ -599,11 +611,11 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdParams P) {
             a.LV[i] = dv;
             a.LK[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int j = lane; j < R.ne; j += 32) {
+        for (int j = g.tid; j < R.ne; j += TPR) {
             a.LE[j] = make_float4(0.f, 0.f, 0.f, P.dLdth ? P.dLdth[R.e0 + j] : 0.f);
             a.LT[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncwarp();
+        g.sync();
         double gm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // FP64: these sums cancel strongly
         float lpf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, lphif[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float ga[12];
@@ -613,32 +625,33 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdParams P) {
             // reload the checkpoint of the segment
             {
                 const long long oV = seg * P.ck_strideV, oE = seg * P.ck_strideE;
-                for (int i = lane; i < R.nv; i += 32) {
+                for (int i = g.tid; i < R.nv; i += TPR) {
                     float4 x = P.ck.X[oV + R.v0 + i];
                     s.X0[i] = x;
                     s.X[i] = x;
                     s.V[i] = P.ck.Vl[oV + R.v0 + i];
                     s.HG[i] = P.ck.HG[oV + R.v0 + i];
                 }
-                for (int j = lane; j < R.ne; j += 32) {
+                for (int j = g.tid; j < R.ne; j += TPR) {
                     s.ED[j] = P.ck.ED[oE + R.e0 + j];
                     s.ET[j] = P.ck.ET[oE + R.e0 + j];
                 }
-                __syncwarp();
+                g.sync();
             }
             Pose F;
             F.load(P.ck.GP + seg * P.ck_strideB + 24LL * rod);
             // level 2: frame-start states of the segment
             for (int f = f0; f < f1; ++f) {
                 float4* e = L2 + (size_t)(f - f0) * E2;
-                save_state<NV, CONTACT>(e, R, lane, s);
-                if (lane < 24) reinterpret_cast<float*>(e + 5 * NV)[lane] = F.p[lane];
-                __syncwarp();
+                save_state<NV, CONTACT, TPR>(e, R, g, s);
+                if (g.tid == 0)
+                    for (int k = 0; k < 24; ++k) reinterpret_cast<float*>(e + 5 * NV)[k] = F.p[k];
+                g.sync();
                 const float* act = P.actions + ((size_t)f * P.B + rod) * 12;
                 float ac[12];
 #pragma unroll
                 for (int k = 0; k < 12; ++k) ac[k] = act[k];
-                run_frame<NV, CONTACT>(sc, P.KIN, P.ES, R, s, lane, nsub, h, F, ac, ovf, [](int) {});
+                run_frame<NV, CONTACT, TPR>(sc, P.KIN, P.ES, R, s, g, nsub, h, F, ac, ovf, [](int) {});
             }
             for (int f = f1 - 1; f >= f0; --f) {
                 float ac[12];
@@ -664,13 +677,14 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdParams P) {
                 }
                 // level 3: substep-start states of this frame
                 const float4* e = L2 + (size_t)(f - f0) * E2;
-                load_state<NV, CONTACT>(e, R, lane, s);
+                load_state<NV, CONTACT, TPR>(e, R, g, s);
                 Pose F0;
                 F0.load(reinterpret_cast<const float*>(e + 5 * NV));
                 Pose Fw = F0;
-                const int np = run_frame<NV, CONTACT>(sc, P.KIN, P.ES, R, s, lane, nsub, h, Fw, ac, ovf,
-                                                      [&](int sb) { save_state<NV, CONTACT>(L3 + (size_t)sb * E3, R, lane, s); });
-                __syncwarp();
+                const int np = run_frame<NV, CONTACT, TPR>(
+                    sc, P.KIN, P.ES, R, s, g, nsub, h, Fw, ac, ovf,
+                    [&](int sb) { save_state<NV, CONTACT, TPR>(L3 + (size_t)sb * E3, R, g, s); });
+                g.sync();
                 for (int sb = nsub - 1; sb >= 0; --sb) {
                     const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
                     M3 gR0[2], gR1[2];
@@ -679,42 +693,37 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdParams P) {
                     if (sb > 0) substep_rot(F0, ac, R.ngrip, c0, gR0);
                     substep_rot(F0, ac, R.ngrip, c1, gR1);
                     // level 4: the substep's intermediates
-                    load_state<NV, CONTACT>(L3 + (size_t)sb * E3, R, lane, s);
+                    load_state<NV, CONTACT, TPR>(L3 + (size_t)sb * E3, R, g, s);
                     Rec rec{SN, a.V1, a.DF, NV};
-                    substep<NV, CONTACT, true>(sc, P.KIN, P.ES, R, s, lane, h, F0.p, gR0, gR1, c0, c1, ac, np, &rec);
-                    load_state<NV, CONTACT>(L3 + (size_t)sb * E3, R, lane, s);
-                    reverse_substep<NV, CONTACT>(P, R, s, a, SN, lane, h, F0, ac, gR0, gR1, c0, c1, np, gm, lpf,
-                                                 lphif, ga);
+                    substep<NV, CONTACT, TPR, true>(sc, P.KIN, P.ES, R, s, g, h, F0.p, gR0, gR1, c0, c1, ac, np,
+                                                    &rec);
+                    load_state<NV, CONTACT, TPR>(L3 + (size_t)sb * E3, R, g, s);
+                    reverse_substep<NV, CONTACT, TPR>(P, R, s, a, SN, g, h, F0, ac, gR0, gR1, c0, c1, np, gm, lpf,
+                                                      lphif, ga);
                 }
                 if (P.gact) {
-#pragma unroll
-                    for (int k = 0; k < 12; ++k) {
-                        float v = ga[k];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-                        if (lane == 0) P.gact[((size_t)f * P.B + rod) * 12 + k] = v;
+                    for (int k = 0; k < 6 * R.ngrip; ++k) {
+                        const float v = (float)grp_sum<TPR>((double)ga[k], g);
+                        if (g.tid == 0) P.gact[((size_t)f * P.B + rod) * 12 + k] = v;
                     }
+                    if (g.tid == 0)
+                        for (int k = 6 * R.ngrip; k < 12; ++k) P.gact[((size_t)f * P.B + rod) * 12 + k] = 0.f;
                 }
             }
         }
         // outputs
-        for (int i = lane; i < R.nv; i += 32) {
+        for (int i = g.tid; i < R.nv; i += TPR) {
             if (P.gx0) P.gx0[R.v0 + i] = a.LX[i];
             if (P.gv0) P.gv0[R.v0 + i] = a.LV[i];
         }
-        for (int j = lane; j < R.ne; j += 32) {
+        for (int j = g.tid; j < R.ne; j += TPR) {
             if (P.gth0) P.gth0[R.e0 + j] = a.LE[j].w;
             P.gtb0[R.e0 + j] = a.LT[j];
             P.gd1b0[R.e0 + j] = make_float4(a.LE[j].x, a.LE[j].y, a.LE[j].z, 0.f);
         }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            double v = gm[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            gm[k] = v;
-        }
-        if (lane == 0 && P.gmat) {
+        for (int k = 0; k < 5; ++k) gm[k] = grp_sum<TPR>(gm[k], g);
+        if (g.tid == 0 && P.gmat) {
             const double r = R.radius, A = 3.14159265358979323846 * r * r, r2 = r * r;
             P.gmat[5 * rod + 0] = R.kA > 0.f ? (float)(gm[0] * A) : 0.f;   // K_stretch
             P.gmat[5 * rod + 1] = (float)(gm[1] * A * r2 / 4.0);            // E_bend
@@ -722,32 +731,33 @@ __global__ void __launch_bounds__(256) bwd_kernel(BwdParams P) {
             P.gmat[5 * rod + 3] = (float)gm[3];                             // yield curvature
             P.gmat[5 * rod + 4] = (float)gm[4];                             // damping
         }
-        __syncwarp();
+        g.sync();
     }
 }
 
 template <int NV, bool C>
-static int bwd_occ_t(int warps) {
-    size_t smem = bwd_smem_bytes(NV, C) * warps;
+static int bwd_occ_t(int rpc) {
+    if (rpc < 1 || rpc * threads_per_rod(NV) > kBwdMaxThreads) return 0;
+    size_t smem = bwd_smem_bytes(NV, C) * rpc;
     auto k = bwd_kernel<NV, C>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * warps, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_rod(NV) * rpc, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return nb;
 }
 template <int NV, bool C>
-static cudaError_t launch_bwd_t(const BwdParams& P, int grid, int warps, cudaStream_t st) {
-    size_t smem = bwd_smem_bytes(NV, C) * warps;
+static cudaError_t launch_bwd_t(const BwdParams& P, int grid, int rpc, cudaStream_t st) {
+    size_t smem = bwd_smem_bytes(NV, C) * rpc;
     auto k = bwd_kernel<NV, C>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 32 * warps, smem, st>>>(P);
+    k<<<grid, threads_per_rod(NV) * rpc, smem, st>>>(P);
     return cudaGetLastError();
 }
 

@@ -1,120 +1,131 @@
-// dlo_fwd_kernel.cuh -- the persistent forward kernel: one warp per rod, rod state in shared
-// memory across all substeps and frames of a launch (the substep itself is in dlo_step.cuh).
+// dlo_fwd_kernel.cuh -- the persistent forward kernel: a group of TPR threads per rod, rod
+// state in shared memory across all substeps and frames of a launch (the substep itself is in
+// dlo_step.cuh).  Rods are taken from a work queue in decreasing cost.
 #pragma once
 #include "dlo_step.cuh"
 
 namespace dlo {
 
-// ------------------------------------------------------------------ the persistent kernel
+constexpr int kFwdMaxThreads = 512;   // per CTA (register budget of the forward kernel)
+
+template <int TPR>
 __device__ __forceinline__ void write_state(const StateRef& D, long long offV, long long offE, long long offB,
-                                            const RodInfo& R, int rod, int lane, const float4* X, const float4* V,
-                                            const float4* ED, const float4* ET, const float4* HG, const float* gp) {
-    for (int i = lane; i < R.nv; i += 32) {
+                                            const RodInfo& R, int rod, const Grp<TPR>& g, const float4* X,
+                                            const float4* V, const float4* ED, const float4* ET, const float4* HG,
+                                            const float* gp) {
+    for (int i = g.tid; i < R.nv; i += TPR) {
         D.X[offV + R.v0 + i] = X[i];
         D.Vl[offV + R.v0 + i] = V[i];
         D.HG[offV + R.v0 + i] = HG[i];
     }
-    for (int j = lane; j < R.ne; j += 32) {
+    for (int j = g.tid; j < R.ne; j += TPR) {
         D.ED[offE + R.e0 + j] = ED[j];
         D.ET[offE + R.e0 + j] = ET[j];
     }
-    if (lane < 24) D.GP[offB + 24LL * rod + lane] = gp[lane];
+    if (g.tid == 0)
+        for (int k = 0; k < 24; ++k) D.GP[offB + 24LL * rod + k] = gp[k];
 }
 
 template <int NV, bool CONTACT>
-__global__ void __launch_bounds__(256) fwd_kernel(FwdParams P) {
+__global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
+    constexpr int TPR = threads_per_rod(NV);
     extern __shared__ float4 dyn_smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Smem<NV, CONTACT> s(dyn_smem + warp * (warp_smem_bytes(NV, CONTACT) / 16));
+    const int slot = threadIdx.x / TPR;
+    Smem<NV, CONTACT> s(dyn_smem + slot * (rod_smem_bytes(NV, CONTACT) / 16));
+    const Grp<TPR> g{(int)(threadIdx.x % TPR), 1 + slot, s.red};
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(P.counter, 1);
-        item = __shfl_sync(kFull, item, 0);
+        const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (item >= P.n_order) break;
         const int rod = P.order[item];
         const RodInfo R = P.rods[rod];
         const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
         const float h = P.scene.dt / (float)nsub;
-        for (int i = lane; i < R.nv; i += 32) {
+        for (int i = g.tid; i < R.nv; i += TPR) {
             float4 x = P.S.X[R.v0 + i];
             s.X[i] = x;
             s.X0[i] = x;
             s.V[i] = P.S.Vl[R.v0 + i];
             s.HG[i] = P.S.HG[R.v0 + i];
         }
-        for (int j = lane; j < R.ne; j += 32) {
+        for (int j = g.tid; j < R.ne; j += TPR) {
             s.ED[j] = P.S.ED[R.e0 + j];
             s.ET[j] = P.S.ET[R.e0 + j];
         }
-        // gripper poses of the frame start (every lane holds a copy)
+        // gripper poses of the frame start (every thread holds a copy)
         Pose F;
         F.load(P.S.GP + 24LL * rod);
-        __syncwarp();
+        g.sync();
         unsigned bad = 0;
+        int np_max = 0;
         for (int f = 0; f < P.frames; ++f) {
             const int gf = P.frame0 + f;
             if (P.ck_every > 0 && gf % P.ck_every == 0 && gf / P.ck_every < P.ck_count) {
                 const long long c = gf / P.ck_every;
-                write_state(P.ck, c * P.ck_strideV, c * P.ck_strideE, c * P.ck_strideB, R, rod, lane, s.X, s.V,
-                            s.ED, s.ET, s.HG, F.p);
+                write_state<TPR>(P.ck, c * P.ck_strideV, c * P.ck_strideE, c * P.ck_strideB, R, rod, g, s.X, s.V,
+                                 s.ED, s.ET, s.HG, F.p);
             }
             float act[12];
 #pragma unroll
             for (int k = 0; k < 12; ++k)
                 act[k] = P.actions ? P.actions[((long long)f * P.B + rod) * 12 + k] : 0.f;
             bool ovf = false;
-            const int np = run_frame<NV, CONTACT>(P.scene, P.KIN, P.ES, R, s, lane, nsub, h, F, act, ovf,
-                                                  [](int) {});
+            const int np = run_frame<NV, CONTACT, TPR>(P.scene, P.KIN, P.ES, R, s, g, nsub, h, F, act, ovf,
+                                                       [](int) {});
             if (ovf) bad |= 2u;
+            np_max = max(np_max, np);
             bool nf = false;
-            for (int i = lane; i < R.nv; i += 32) {
+            for (int i = g.tid; i < R.nv; i += TPR) {
                 float4 x = s.X[i], v = s.V[i];
                 nf |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) && isfinite(v.y) &&
                         isfinite(v.z) && isfinite(v.w));
                 if (P.xframes) reinterpret_cast<float4*>(P.xframes)[(long long)f * P.nvert_total + R.v0 + i] = x;
             }
-            if (__any_sync(kFull, nf)) bad |= 1u;
+            if (grp_any<TPR>(nf, g)) bad |= 1u;
             if (f + 1 == P.frames) {
                 if (R.flags & ROD_INEXT) {
                     double r = 0.0;
-                    for (int j = lane; j < R.ne; j += 32) {
+                    for (int j = g.tid; j < R.ne; j += TPR) {
                         int j1 = (j + 1 == R.nv) ? 0 : j + 1;
                         V3<float> e = f3(s.X[j1]) - f3(s.X[j]);
                         r += fabs((double)sqrtf(dot(e, e)) - (double)s.ET[j].w);
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
-                    if (lane == 0) P.residual[rod] = r;
+                    r = grp_sum<TPR>(r, g);
+                    if (g.tid == 0) P.residual[rod] = r;
                 }
-                if (lane == 0) P.npairs[rod] = np;
+                if (g.tid == 0) P.npairs[rod] = np_max;
             }
         }
-        write_state(P.S, 0, 0, 0, R, rod, lane, s.X, s.V, s.ED, s.ET, s.HG, F.p);
-        if (lane == 0 && bad) atomicOr(&P.status[rod], bad);
-        __syncwarp();
+        write_state<TPR>(P.S, 0, 0, 0, R, rod, g, s.X, s.V, s.ED, s.ET, s.HG, F.p);
+        if (g.tid == 0 && bad) atomicOr(&P.status[rod], bad);
+        g.sync();
     }
 }
 
+// rods per CTA allowed by the thread budget
+template <int NV>
+__host__ __device__ constexpr int fwd_max_rpc() { return kFwdMaxThreads / threads_per_rod(NV); }
+
 template <int NV, bool C>
-static cudaError_t launch_fwd_t(const FwdParams& P, int grid, int warps, cudaStream_t st) {
-    size_t smem = warp_smem_bytes(NV, C) * warps;
+static cudaError_t launch_fwd_t(const FwdParams& P, int grid, int rpc, cudaStream_t st) {
+    size_t smem = rod_smem_bytes(NV, C) * rpc;
     auto k = fwd_kernel<NV, C>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 32 * warps, smem, st>>>(P);
+    k<<<grid, threads_per_rod(NV) * rpc, smem, st>>>(P);
     return cudaGetLastError();
 }
 
 template <int NV, bool C>
-static int fwd_occ_t(int warps) {
-    size_t smem = warp_smem_bytes(NV, C) * warps;
+static int fwd_occ_t(int rpc) {
+    if (rpc > fwd_max_rpc<NV>() || rpc < 1) return 0;
+    size_t smem = rod_smem_bytes(NV, C) * rpc;
     auto k = fwd_kernel<NV, C>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * warps, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_rod(NV) * rpc, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

@@ -9,10 +9,13 @@ namespace dlo {
 // Shared memory of one warp (one rod of at most NV vertices) in the persistent kernels:
 // ten float4 arrays of NV (positions, start positions, velocities, base frames + twist,
 // base tangents + rest lengths, hinge state, three per-hinge gradient slots, new reference
-// frames) and, with self-contact, 2 NV pair slots (two float4 of projection data each,
+// frames) and, with self-contact, 4 NV pair slots (two float4 of projection data each,
 // one packed index pair) plus an int4 fixed-point accumulator per vertex.
+constexpr int kPairsPerVertex = 4;
 __host__ __device__ constexpr size_t warp_smem_bytes(int NV, bool contact) {
-    return (size_t)(10 * NV) * 16 + (contact ? ((size_t)(4 * NV) * 16 + (size_t)NV * 16 + (size_t)(2 * NV) * 4) : 0);
+    return (size_t)(10 * NV) * 16 +
+           (contact ? ((size_t)(2 * kPairsPerVertex * NV) * 16 + (size_t)NV * 16 + (size_t)(kPairsPerVertex * NV) * 4)
+                    : 0);
 }
 
 // Per size class (dlo_nv*.cu).
@@ -34,6 +37,12 @@ cudaError_t launch_backward_nv256(const BwdParams& P, bool c, int grid, int warp
 int backward_occ_nv256(bool c, int warps);
 cudaError_t launch_backward(const BwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
 int backward_blocks_per_sm(int nv_max, bool contact, int warps);
+// Shared memory of one rod: its arrays plus a 256-byte header for group reductions.
+__host__ __device__ constexpr size_t rod_smem_bytes(int NV, bool contact) { return warp_smem_bytes(NV, contact) + 256; }
+
+// Threads that step one rod of size class NV (one vertex per thread up to 128 vertices).
+__host__ __device__ constexpr int threads_per_rod(int NV) { return NV < 128 ? NV : 128; }
+
 cudaError_t launch_forward(const FwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
 int forward_blocks_per_sm(int nv_max, bool contact, int warps);
 

@@ -243,6 +243,57 @@ DLO_HD V3<T> contact_respond(V3<T> v, T sdf, V3<T> n, V3<T> vrig, float r, float
     return v + f * (vr2 - vr);
 }
 
+// Reverse of contact_respond on its active branch (the caller has seen act == true): given the
+// cotangent lo of the output velocity, the cotangents of v, sdf, the normal and the rigid
+// velocity.  Branches (min / max selections) follow the forward values.
+DLO_HD void contact_respond_rev(V3<float> v, float sdf, V3<float> n, V3<float> vrig, float r, float eps_s,
+                                float mu, float rest, V3<float> lo, V3<float>& lv, float& lsdf, V3<float>& ln,
+                                V3<float>& lvrig) {
+    const float f0 = expf((r - sdf) / eps_s);
+    const float f = f0 > 1.f ? 1.f : f0;
+    const V3<float> vr = v - vrig;
+    const float vn = dot(vr, n);
+    const V3<float> vt = vr - vn * n;
+    const bool keep = vn >= -rest * vn;
+    const float vn2 = keep ? vn : -rest * vn;
+    const float dvn = vn2 - vn;
+    const float vt2 = dot(vt, vt);
+    float sc = 1.f, s = 0.f, q = 1.f;
+    const bool fr = vt2 > 1e-24f;
+    if (fr) {
+        s = sqrtf(vt2);
+        q = 1.f - mu * dvn / s;
+        sc = q >= 0.f ? q : 0.f;
+    }
+    const V3<float> vr2 = vn2 * n + sc * vt;
+    // out = v + f (vr2 - vr)
+    lv = lo;
+    const float lf = dot(lo, vr2 - vr);
+    const V3<float> lvr2 = f * lo;
+    V3<float> lvr = -f * lo;
+    float lvn2 = dot(lvr2, n);
+    ln = vn2 * lvr2;
+    const float lsc = dot(lvr2, vt);
+    V3<float> lvt = sc * lvr2;
+    float lvn = 0.f;
+    if (fr && q >= 0.f) {
+        const float ldvn = -mu * lsc / s;
+        const float ls = mu * dvn * lsc / (s * s);
+        lvt += (ls / s) * vt;
+        lvn2 += ldvn;
+        lvn -= ldvn;
+    }
+    lvn += keep ? lvn2 : -rest * lvn2;
+    lvr += lvt;
+    lvn -= dot(lvt, n);
+    ln -= vn * lvt;
+    lvr += lvn * n;
+    ln += lvn * vr;
+    lv += lvr;
+    lvrig = -lvr;
+    lsdf = f0 < 1.f ? -lf * f0 / eps_s : 0.f;
+}
+
 // ------------------------------------------------------------------ segment closest points
 // Clamped closed-form closest points of segments p1q1 and p2q2 (Ericson, Real-Time Collision
 // Detection, Sec. 5.1.9); near-parallel segments take s = 0 and u clamped.

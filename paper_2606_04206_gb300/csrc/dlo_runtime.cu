@@ -78,13 +78,20 @@ dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const 
         bk.n = (int)ids.size();
         bk.d_order = alloc_up(c, ids, st);
         if (st != DLO_OK) return st;
-        int w = c->opt.warps_per_cta > 0 ? c->opt.warps_per_cta : 4;
-        int nb = 0;
-        while (w >= 1 && (nb = forward_blocks_per_sm(bk.nv_max, bk.contact, w)) < 1) w >>= 1;
-        if (w < 1 || nb < 1) return set_err(c, DLO_ERR_INVALID_ARG, "rod too large for shared memory");
-        bk.warps = w;
-        long long want = (bk.n + w - 1) / w;
-        bk.grid = (int)std::min<long long>((long long)nb * c->sm_count, want);
+        // rods per CTA: the count (within the thread budget) that keeps the most rods resident
+        int best = 0, best_nb = 0;
+        for (int rpc = 1; rpc <= 16; ++rpc) {
+            if (c->opt.warps_per_cta > 0 && rpc != c->opt.warps_per_cta) continue;
+            const int nb = forward_blocks_per_sm(bk.nv_max, bk.contact, rpc);
+            if (nb >= 1 && rpc * nb >= best * best_nb) {
+                best = rpc;
+                best_nb = nb;
+            }
+        }
+        if (best < 1) return set_err(c, DLO_ERR_INVALID_ARG, "rod too large for shared memory");
+        bk.warps = best;
+        long long want = (bk.n + best - 1) / best;
+        bk.grid = (int)std::min<long long>((long long)best_nb * c->sm_count, want);
         c->buckets.push_back(bk);
     }
     c->d_counters = reinterpret_cast<int*>(alloc_zero(c, sizeof(int) * 8, st));

@@ -15,7 +15,7 @@ struct Bucket {
     bool contact = false;
     int n = 0;              // rods in the bucket
     int* d_order = nullptr; // rod ids by decreasing cost (vertices x substeps)
-    int warps = 0;          // warps (= rods in flight) per CTA
+    int warps = 0;          // rods in flight per CTA of the forward kernel
     int grid = 0;           // persistent CTAs
 };
 }  // namespace dlo

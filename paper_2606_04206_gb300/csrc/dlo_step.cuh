@@ -17,6 +17,89 @@
 
 namespace dlo {
 
+// A rod is stepped by a group of TPR threads (one or more whole warps); elements are spread
+// over the group with stride TPR and phases are separated by the group's barrier (the warp's
+// own for TPR = 32, else a named barrier of TPR threads).
+template <int TPR>
+struct Grp {
+    int tid;      // thread index within the rod's group
+    int bar;      // named barrier id (1..15) of the group
+    float* red;   // 64 floats of the rod's shared header, for group reductions
+    __device__ __forceinline__ void sync() const {
+        if (TPR == 32)
+            __syncwarp();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(TPR) : "memory");
+    }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the group (deterministic order: warps' partial sums added in warp order).
+template <int TPR>
+__device__ __forceinline__ double grp_sum(double v, const Grp<TPR>& g) {
+    v = warp_sum(v);
+    if (TPR == 32) return v;
+    double* r = reinterpret_cast<double*>(g.red);
+    if ((g.tid & 31) == 0) r[g.tid >> 5] = v;
+    g.sync();
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < TPR / 32; ++k) s += r[k];
+    g.sync();
+    return s;
+}
+
+template <int TPR>
+__device__ __forceinline__ bool grp_any(bool p, const Grp<TPR>& g) {
+    const bool w = __any_sync(0xffffffffu, p);
+    if (TPR == 32) return w;
+    int* r = reinterpret_cast<int*>(g.red) + 32;
+    if ((g.tid & 31) == 0) r[g.tid >> 5] = w ? 1 : 0;
+    g.sync();
+    bool s = false;
+#pragma unroll
+    for (int k = 0; k < TPR / 32; ++k) s |= r[k] != 0;
+    g.sync();
+    return s;
+}
+
+// Value held by thread 0 of the group.
+template <int TPR>
+__device__ __forceinline__ int grp_bcast0(int v, const Grp<TPR>& g) {
+    if (TPR == 32) return __shfl_sync(0xffffffffu, v, 0);
+    int* r = reinterpret_cast<int*>(g.red) + 48;
+    if (g.tid == 0) *r = v;
+    g.sync();
+    const int out = *r;
+    g.sync();
+    return out;
+}
+
+// Exclusive prefix sum over the group.
+template <int TPR>
+__device__ __forceinline__ int grp_excl_scan(int v, const Grp<TPR>& g) {
+    const int l = g.tid & 31, w = g.tid >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += y;
+    }
+    if (TPR == 32) return incl - v;
+    int* r = reinterpret_cast<int*>(g.red) + 16;
+    if (l == 31) r[w] = incl;
+    g.sync();
+    int off = 0;
+    for (int k = 0; k < w; ++k) off += r[k];
+    g.sync();
+    return off + incl - v;
+}
+
 // Optional recording of a substep's intermediates for the adjoint (RECORD = true).
 struct Rec {
     float4* snap;   // global [n_iter][NV]: displacements at the start of each PBD iteration
@@ -25,7 +108,6 @@ struct Rec {
     int nvmax;
 };
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr float kFixPos = 1073741824.f;     // 2^30: fixed-point scale of position corrections
 constexpr float kFixVel = 16777216.f;       // 2^24: fixed-point scale of velocity corrections
 
@@ -74,7 +156,9 @@ struct Smem {
     float4 *fr0, *fr1;
     int4* acc;
     uint32_t* pairs;
+    float* red;
     __device__ Smem(float4* base) {
+        red = reinterpret_cast<float*>(base + warp_smem_bytes(NV, CONTACT) / 16);
         X = base;
         X0 = base + NV;
         V = base + 2 * NV;
@@ -86,8 +170,8 @@ struct Smem {
         HB2 = base + 8 * NV;
         ND = base + 9 * NV;
         fr0 = base + 10 * NV;
-        fr1 = fr0 + 2 * NV;
-        acc = reinterpret_cast<int4*>(fr1 + 2 * NV);
+        fr1 = fr0 + kPairsPerVertex * NV;
+        acc = reinterpret_cast<int4*>(fr1 + kPairsPerVertex * NV);
         pairs = reinterpret_cast<uint32_t*>(acc + NV);
     }
 };
@@ -96,8 +180,8 @@ struct Smem {
 // Per-rod spatial hash of edge midpoints (cells of R.cell >= candidate distance + longest
 // edge, so the 27 neighbouring cells hold every candidate); candidates are the edge pairs
 // outside the exclusion window whose segments are closer than R.contact_d.
-template <int NV, bool CONTACT>
-__device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, bool closed, bool& overflow) {
+template <int NV, bool CONTACT, int TPR>
+__device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, bool closed, bool& overflow) {
     constexpr int TBL = NV <= 32 ? 64 : (NV <= 64 ? 128 : (NV <= 128 ? 256 : 512));
     int* keys = reinterpret_cast<int*>(s.HB0);
     int* cnt = keys + NV;          // TBL bucket counters + 1 pair counter
@@ -105,9 +189,9 @@ __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, boo
     const int ne = R.ne, nv = R.nv;
     const V3<float> org = f3(s.X[0]);
     const float inv_cell = 1.f / R.cell;
-    for (int k = lane; k <= TBL; k += 32) cnt[k] = 0;
-    __syncwarp();
-    for (int j = lane; j < ne; j += 32) {
+    for (int k = g.tid; k <= TBL; k += TPR) cnt[k] = 0;
+    g.sync();
+    for (int j = g.tid; j < ne; j += TPR) {
         int j1 = (j + 1 == nv) ? 0 : j + 1;
         V3<float> m = 0.5f * (f3(s.X[j]) + f3(s.X[j1])) - org;
         int ix = min(max(__float2int_rd(m.x * inv_cell), -510), 510) + 512;
@@ -116,41 +200,34 @@ __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, boo
         keys[j] = (ix << 20) | (iy << 10) | iz;
         atomicAdd(&cnt[cell_hash(ix, iy, iz, TBL - 1)], 1);
     }
-    __syncwarp();
-    {   // exclusive scan of the bucket counts (TBL/32 consecutive buckets per lane)
-        constexpr int PER = TBL / 32;
+    g.sync();
+    {   // exclusive scan of the bucket counts (TBL/TPR consecutive buckets per thread)
+        constexpr int PER = TBL / TPR;
         int loc[PER];
         int sum = 0;
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            loc[k] = cnt[lane * PER + k];
+            loc[k] = cnt[g.tid * PER + k];
             sum += loc[k];
         }
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int run = incl - sum;
-        __syncwarp();
+        int run = grp_excl_scan<TPR>(sum, g);
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
-            cnt[lane * PER + k] = run;
+            cnt[g.tid * PER + k] = run;
             run += loc[k];
         }
     }
-    __syncwarp();
-    for (int j = lane; j < ne; j += 32) {
+    g.sync();
+    for (int j = g.tid; j < ne; j += TPR) {
         int key = keys[j];
         int pos = atomicAdd(&cnt[cell_hash(key >> 20, (key >> 10) & 1023, key & 1023, TBL - 1)], 1);
         sorted[pos] = j;
     }
-    __syncwarp();
+    g.sync();
     // after the scatter cnt[h] is the end of bucket h (and the start of bucket h + 1)
     const int cap = R.pair_cap;
     bool ovf = false;
-    for (int a = lane; a < ne; a += 32) {
+    for (int a = g.tid; a < ne; a += TPR) {
         int key = keys[a];
         int ix = key >> 20, iy = (key >> 10) & 1023, iz = key & 1023;
         int a1 = (a + 1 == nv) ? 0 : a + 1;
@@ -183,10 +260,10 @@ __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, boo
                     }
                 }
     }
-    __syncwarp();
-    overflow = __any_sync(kFull, ovf);
+    g.sync();
+    overflow = grp_any<TPR>(ovf, g);
     int np = cnt[TBL];
-    __syncwarp();
+    g.sync();
     return min(np, cap);
 }
 
@@ -205,13 +282,14 @@ __device__ __forceinline__ void color_range(int ne, bool closed, int color, int&
 
 // One colour of inextensibility / strain-limit projections (App. A.1) on displacements D
 // from start positions X0: C = |x_{j+1} - x_j| - |ebar|, lambda = C / (w_j + w_{j+1}).
+template <int TPR>
 __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* X0, float4* D, const float4* ET,
-                                                int lane, int color, bool closed) {
+                                                const Grp<TPR>& g, int color, bool closed) {
     const int ne = R.ne, nv = R.nv;
     int first, last;
     color_range(ne, closed, color, first, last);
     const bool inext = R.flags & ROD_INEXT;
-    for (int j = first + 2 * lane; j < last; j += 64) {
+    for (int j = first + 2 * g.tid; j < last; j += 2 * TPR) {
         int j1 = (j + 1 == nv) ? 0 : j + 1;
         float4 A = D[j], B = D[j1];              // displacements (w = inverse mass)
         V3<float> e = (f3(X0[j1]) - f3(X0[j])) + (f3(B) - f3(A));
@@ -235,23 +313,23 @@ __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* 
         D[j] = make_float4(A.x + da.x, A.y + da.y, A.z + da.z, A.w);
         D[j1] = make_float4(B.x - db.x, B.y - db.y, B.z - db.z, B.w);
     }
-    __syncwarp();
+    g.sync();
 }
 
-template <int NV, bool CONTACT>
-__device__ __forceinline__ void inext_color(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, int color,
+template <int NV, bool CONTACT, int TPR>
+__device__ __forceinline__ void inext_color(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int color,
                                             bool closed) {
-    inext_color_arr(R, s.X0, s.X, s.ET, lane, color, closed);
+    inext_color_arr<TPR>(R, s.X0, s.X, s.ET, g, color, closed);
 }
 
-template <int NV, bool CONTACT>
-__device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, int np,
+template <int NV, bool CONTACT, int TPR>
+__device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int np,
                                               bool first) {
     const int nv = R.nv;
-    for (int i = lane; i < nv; i += 32) s.acc[i] = make_int4(0, 0, 0, 0);
-    __syncwarp();
+    for (int i = g.tid; i < nv; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
+    g.sync();
     const float rsum = 2.f * R.radius;
-    for (int p = lane; p < np; p += 32) {
+    for (int p = g.tid; p < np; p += TPR) {
         uint32_t pr = s.pairs[p];
         int a0 = pr & 0xffff, c0 = pr >> 16;
         int a1 = (a0 + 1 == nv) ? 0 : a0 + 1, c1 = (c0 + 1 == nv) ? 0 : c0 + 1;
@@ -277,8 +355,8 @@ __device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT
             }
         }
     }
-    __syncwarp();
-    for (int i = lane; i < nv; i += 32) {
+    g.sync();
+    for (int i = g.tid; i < nv; i += TPR) {
         int4 q = s.acc[i];
         if (q.x | q.y | q.z) {
             float4 x = s.X[i];
@@ -286,16 +364,16 @@ __device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT
             s.X[i] = make_float4(x.x + q.x * inv, x.y + q.y * inv, x.z + q.z * inv, x.w);
         }
     }
-    __syncwarp();
+    g.sync();
 }
 
-template <int NV, bool CONTACT>
-__device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT>& s, int lane, int np,
+template <int NV, bool CONTACT, int TPR>
+__device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int np,
                                               float h, float mu) {
     const int nv = R.nv;
-    for (int i = lane; i < nv; i += 32) s.acc[i] = make_int4(0, 0, 0, 0);
-    __syncwarp();
-    for (int p = lane; p < np; p += 32) {
+    for (int i = g.tid; i < nv; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
+    g.sync();
+    for (int p = g.tid; p < np; p += TPR) {
         float4 F1 = s.fr1[p];
         if (!(F1.w > 0.f)) continue;
         float4 F0 = s.fr0[p];
@@ -319,8 +397,8 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
             atomicAdd(&s.acc[idx[k]].z, to_fix(wt[k] * dv.z, kFixVel));
         }
     }
-    __syncwarp();
-    for (int i = lane; i < nv; i += 32) {
+    g.sync();
+    for (int i = g.tid; i < nv; i += TPR) {
         int4 q = s.acc[i];
         if (q.x | q.y | q.z) {
             float4 v = s.V[i];
@@ -328,20 +406,20 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
             s.V[i] = make_float4(v.x + q.x * inv, v.y + q.y * inv, v.z + q.z * inv, v.w);
         }
     }
-    __syncwarp();
+    g.sync();
 }
 
 // ------------------------------------------------------------------ one substep
-template <int NV, bool CONTACT, bool RECORD = false>
+template <int NV, bool CONTACT, int TPR, bool RECORD = false>
 __device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
-                        const RodInfo& R, Smem<NV, CONTACT>& s, int lane, float h, const float* gpF,
+                        const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, float h, const float* gpF,
                         const M3* gR0, const M3* gR1, float c0, float c1, const float* act, int np,
                         const Rec* rec = nullptr) {
     const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
     const bool closed = R.flags & ROD_CLOSED;
     const int nh = closed ? nv : nv - 2;
     // --- hinge phase
-    for (int k = lane; k < nh; k += 32) {
+    for (int k = g.tid; k < nh; k += TPR) {
         const int i = closed ? k : k + 1;
         const int a = (i == 0) ? ne - 1 : i - 1;
         const int b = i;
@@ -367,9 +445,9 @@ __device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, cons
         if (!closed && i == 1) s.ND[0] = f4(H.a.d1r, 0.f);
         s.HG[i] = make_float4(hg.x, hg.y, hg.z, H.mref);
     }
-    __syncwarp();
+    g.sync();
     // --- vertex phase
-    for (int i = lane; i < nv; i += 32) {
+    for (int i = g.tid; i < nv; i += TPR) {
         const float4 xi4 = s.X0[i];
         const V3<float> xi = f3(xi4);
         V3<float> g = zf3();
@@ -453,40 +531,40 @@ __device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, cons
         s.X[i] = f4(d, xi4.w);
         s.V[i] = f4(v2, om1);
     }
-    __syncwarp();
+    g.sync();
     // --- PBD
     const bool lenc = R.flags & (ROD_INEXT | ROD_SLIMIT);
     if (lenc || np > 0) {
         for (int it = 0; it < sc.n_iter; ++it) {
             if (RECORD) {
-                for (int i = lane; i < nv; i += 32) rec->snap[(size_t)it * rec->nvmax + i] = s.X[i];
-                __syncwarp();
+                for (int i = g.tid; i < nv; i += TPR) rec->snap[(size_t)it * rec->nvmax + i] = s.X[i];
+                g.sync();
             }
             if (lenc) {
-                inext_color(R, s, lane, 0, closed);
-                inext_color(R, s, lane, 1, closed);
-                if (closed && (ne & 1)) inext_color(R, s, lane, 2, closed);
+                inext_color<NV, CONTACT, TPR>(R, s, g, 0, closed);
+                inext_color<NV, CONTACT, TPR>(R, s, g, 1, closed);
+                if (closed && (ne & 1)) inext_color<NV, CONTACT, TPR>(R, s, g, 2, closed);
             }
-            if (CONTACT && np > 0) contact_sweep(R, s, lane, np, it == 0);
+            if (CONTACT && np > 0) contact_sweep<NV, CONTACT, TPR>(R, s, g, np, it == 0);
         }
     }
     // --- velocity from the displacement, friction, new positions
     const float ih = 1.f / h;
-    for (int i = lane; i < nv; i += 32) {
+    for (int i = g.tid; i < nv; i += TPR) {
         float4 d = s.X[i], v = s.V[i];
         if (RECORD) rec->dfin[i] = d;
         s.V[i] = make_float4(d.x * ih, d.y * ih, d.z * ih, v.w);
     }
-    __syncwarp();
-    if (CONTACT && np > 0) self_friction(R, s, lane, np, h, sc.mu_self);
-    for (int i = lane; i < nv; i += 32) {
+    g.sync();
+    if (CONTACT && np > 0) self_friction<NV, CONTACT, TPR>(R, s, g, np, h, sc.mu_self);
+    for (int i = g.tid; i < nv; i += TPR) {
         float4 x0 = s.X0[i], d = s.X[i], nd = s.ND[i];
         float4 x = nd.w > 0.5f ? make_float4(nd.x, nd.y, nd.z, x0.w)
                                : make_float4(x0.x + d.x, x0.y + d.y, x0.z + d.z, x0.w);
         s.X0[i] = x;
         s.X[i] = x;
     }
-    __syncwarp();
+    g.sync();
 }
 
 
@@ -520,12 +598,12 @@ __device__ __forceinline__ void substep_rot(const Pose& F, const float* act, int
 
 // One frame of one rod: candidates (if self-contact), nsub substeps, pose update.
 // pre(sb) runs before substep sb (after a warp barrier), e.g. to store the substep state.
-template <int NV, bool CONTACT, class PreSub>
+template <int NV, bool CONTACT, int TPR, class PreSub>
 __device__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
-                         const RodInfo& R, Smem<NV, CONTACT>& s, int lane, int nsub, float h, Pose& F,
+                         const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int nsub, float h, Pose& F,
                          const float* act, bool& ovf, PreSub pre) {
     int np = 0;
-    if (CONTACT && (R.flags & ROD_SELF)) np = broad_phase(R, s, lane, (R.flags & ROD_CLOSED) != 0, ovf);
+    if (CONTACT && (R.flags & ROD_SELF)) np = broad_phase<NV, CONTACT, TPR>(R, s, g, (R.flags & ROD_CLOSED) != 0, ovf);
     M3 gR0[2], gR1[2];
     gR0[0] = F.R[0];
     gR0[1] = F.R[1];
@@ -533,7 +611,7 @@ __device__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, con
         pre(sb);
         const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
         substep_rot(F, act, R.ngrip, c1, gR1);
-        substep<NV, CONTACT>(sc, KIN, ES, R, s, lane, h, F.p, gR0, gR1, c0, c1, act, np);
+        substep<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, F.p, gR0, gR1, c0, c1, act, np);
         gR0[0] = gR1[0];
         gR0[1] = gR1[1];
     }

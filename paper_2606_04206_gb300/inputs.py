@@ -75,7 +75,7 @@ class Problem:
     mu_rigid: float = 0.5
     restitution: float = 0.0
     eps_soft: float = 0.5          # softness epsilon_s as a multiple of the radius
-    contact_margin: float = 2.0    # self-contact candidate margin as a multiple of the radius
+    contact_margin: float = 1.0    # self-contact candidate margin as a multiple of the radius
     self_contact: bool = False
     gravity: float = 9.81
     checkpoint_every: int = 50
