@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--rods", type=int, default=4096)
     ap.add_argument("--verts", type=int, default=128)
     ap.add_argument("--no-self-contact", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--plain-frames", type=int, default=20)
     return ap.parse_args()

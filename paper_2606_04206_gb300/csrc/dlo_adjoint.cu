@@ -175,7 +175,8 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
                     ns = std::max(ns, c->nsub[b]);
         nsmax[k] = ns;
         const size_t NV = bk.nv_max;
-        slot_b[k] = 16 * ((size_t)c->ck_every * (5 * NV + 6) + (size_t)ns * 5 * NV + (size_t)std::max(c->opt.n_iter_pbd, 1) * NV);
+        slot_b[k] = 16 * ((size_t)c->ck_every * (5 * NV + 6) +
+                          (size_t)ns * ((7 + 2 * kPairsPerVertex) * NV + (size_t)4 * c->opt.n_iter_pbd * NV));
         warps[k] = w;
         grid[k] = (int)std::min<long long>((long long)nb * c->sm_count, (bk.n + w - 1) / w);
         need = std::max(need, slot_b[k] * (size_t)grid[k] * w);

@@ -157,8 +157,8 @@ __device__ __forceinline__ V3<float> get3(const float* a, int q) { return f3(a[3
 // of S_n.  gm accumulates (kA, Bm, beta, sigma_y, c_d) cotangents, lpf/lphif the frame-start
 // pose cotangents and ga the frame's action cotangents (all per g.tid).
 template <int NV, bool CONTACT, int TPR>
-__device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, CONTACT>& s,
-                                AdjArrays<NV, CONTACT>& a, const float4* SN, const Grp<TPR>& g, float h, const Pose& F0,
+__device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, CONTACT>& s,
+                                AdjArrays<NV, CONTACT>& a, const float4* SN, const float4* CS, const Grp<TPR>& g, float h, const Pose& F0,
                                 const float* act, const M3* gR0, const M3* gR1, float c0, float c1, int np,
                                 double* gm, float* lpf, float* lphif, float* ga) {
     const SceneDev& sc = P.scene;
@@ -190,18 +190,12 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
     g.sync();
     // ---- B2: self-contact friction
     if (CONTACT && np > 0) {
-        float4* T0 = s.ND;        // displacements at the first contact sweep
+        // displacements at the first contact sweep (after the colours of iteration 0)
+        const int ncol0 = lenc ? ((closed && (ne & 1)) ? 3 : 2) : 0;
+        const float4* T0 = ncol0 ? CS + (size_t)(ncol0 - 1) * NV : SN;
         float4* LTMP = s.HB0;
-        for (int i = g.tid; i < nv; i += TPR) {
-            T0[i] = SN[i];
-            LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        for (int i = g.tid; i < nv; i += TPR) LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         g.sync();
-        if (lenc) {
-            inext_color_arr<TPR>(R, s.X0, T0, s.ET, g, 0, closed);
-            inext_color_arr<TPR>(R, s.X0, T0, s.ET, g, 1, closed);
-            if (closed && (ne & 1)) inext_color_arr<TPR>(R, s.X0, T0, s.ET, g, 2, closed);
-        }
         for (int p = g.tid; p < np; p += TPR) {
             if (!(s.fr1[p].w > 0.f)) continue;
             uint32_t pr = s.pairs[p];
@@ -264,15 +258,10 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
     // ---- B4: PBD iterations in reverse
     if (lenc || (CONTACT && np > 0)) {
         const int ncol = lenc ? ((closed && (ne & 1)) ? 3 : 2) : 0;
-        float4* Cpre[4] = {s.HB0, s.HB1, s.HB2, s.ND};
         for (int it = sc.n_iter - 1; it >= 0; --it) {
-            for (int i = g.tid; i < nv; i += TPR) Cpre[0][i] = SN[(size_t)it * NV + i];
-            g.sync();
-            for (int k = 0; k < ncol; ++k) {
-                for (int i = g.tid; i < nv; i += TPR) Cpre[k + 1][i] = Cpre[k][i];
-                g.sync();
-                inext_color_arr<TPR>(R, s.X0, Cpre[k + 1], s.ET, g, k, closed);
-            }
+            // displacements before colour k (k < ncol) and before the contact sweep (k = ncol)
+            const float4* Cpre[4] = {SN + (size_t)it * NV, CS + ((size_t)it * 3) * NV, CS + ((size_t)it * 3 + 1) * NV,
+                                     CS + ((size_t)it * 3 + 2) * NV};
             if (CONTACT && np > 0) {
                 const float4* Dc = Cpre[ncol];
                 float4* LTMP = a.LG;
@@ -411,6 +400,20 @@ __device__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, C
                 bool on;
                 prim_respond<float>(k, sc, R, x, vs[k], gp, gax, vp, w, on);
                 if (!on) continue;
+                V3<float> ntmp;
+                if (q >= 0 && sdf_capsule(x, gp - sc.grip_hl * gax, gp + sc.grip_hl * gax, sc.grip_r, ntmp) > -sc.grip_r) {
+                    // capsule gripper: closed-form reverse (the degenerate on-axis case keeps dual numbers)
+                    V3<float> lxk, lvk, lpk, lphik, lvpk, lwk;
+                    capsule_contact_rev(x, vs[k], gp, col(gR0[q], 2), sc.grip_hl, sc.grip_r, vp, w, R.radius, R.eps,
+                                        sc.mu_rigid, sc.restitution, lam, lxk, lvk, lpk, lphik, lvpk, lwk);
+                    lx_acc += lxk;
+                    lam = lvk;
+                    add3(pa.ps0, q, lpk);
+                    add3(pa.phs0, q, lphik);
+                    add3(pa.vp, q, lvpk);
+                    add3(pa.w, q, lwk);
+                    continue;
+                }
                 if (k < sc.n_planes) {   // plane: closed-form reverse (sdf = n.x - o, constant n)
                     const V3<float> n = f3(sc.planes[k]);
                     V3<float> lv, ln, lvr;
@@ -592,9 +595,11 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
     const Grp<TPR> g{(int)(threadIdx.x % TPR), 1 + rs, s.red};
     const size_t slot = (size_t)blockIdx.x * (blockDim.x / TPR) + rs;
     float4* L2 = reinterpret_cast<float4*>(P.scratch + slot * P.slot_bytes);
-    const size_t E2 = 5 * NV + 6, E3 = 5 * NV;
+    // per-rod scratch: frame-start states of one segment (L2), then per substep of one frame
+    // its start state and recorded intermediates (L3): state 5 NV, v1 NV, dfin NV, pair data
+    // 2 x kPairsPerVertex NV, PBD iteration snapshots n_iter NV, colour snapshots 3 n_iter NV
+    const size_t E2 = 5 * NV + 6, E3 = (size_t)(7 + 2 * kPairsPerVertex) * NV + (size_t)4 * P.scene.n_iter * NV;
     float4* L3 = L2 + (size_t)P.K * E2;
-    float4* SN = L3 + (size_t)P.nsub_max * E3;
     const SceneDev& sc = P.scene;
     for (;;) {
         const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
@@ -651,7 +656,8 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                 float ac[12];
 #pragma unroll
                 for (int k = 0; k < 12; ++k) ac[k] = act[k];
-                run_frame<NV, CONTACT, TPR>(sc, P.KIN, P.ES, R, s, g, nsub, h, F, ac, ovf, [](int) {});
+                run_frame<NV, CONTACT, TPR, false>(sc, P.KIN, P.ES, R, s, g, nsub, h, F, ac, ovf,
+                                            [](int) -> const Rec* { return nullptr; });
             }
             for (int f = f1 - 1; f >= f0; --f) {
                 float ac[12];
@@ -681,9 +687,16 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                 Pose F0;
                 F0.load(reinterpret_cast<const float*>(e + 5 * NV));
                 Pose Fw = F0;
-                const int np = run_frame<NV, CONTACT, TPR>(
-                    sc, P.KIN, P.ES, R, s, g, nsub, h, Fw, ac, ovf,
-                    [&](int sb) { save_state<NV, CONTACT, TPR>(L3 + (size_t)sb * E3, R, g, s); });
+                Rec recs;
+                const int np = run_frame<NV, CONTACT, TPR, false>(
+                    sc, P.KIN, P.ES, R, s, g, nsub, h, Fw, ac, ovf, [&](int sb) -> const Rec* {
+                        float4* e3 = L3 + (size_t)sb * E3;
+                        save_state<NV, CONTACT, TPR>(e3, R, g, s);
+                        float4* sn = e3 + (7 + 2 * kPairsPerVertex) * NV;
+                        recs = Rec{sn, e3 + 5 * NV, e3 + 6 * NV, e3 + 7 * NV, e3 + (7 + kPairsPerVertex) * NV,
+                                   sn + (size_t)sc.n_iter * NV, NV};
+                        return &recs;
+                    });
                 g.sync();
                 for (int sb = nsub - 1; sb >= 0; --sb) {
                     const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
@@ -692,14 +705,22 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                     gR0[1] = F0.R[1];
                     if (sb > 0) substep_rot(F0, ac, R.ngrip, c0, gR0);
                     substep_rot(F0, ac, R.ngrip, c1, gR1);
-                    // level 4: the substep's intermediates
-                    load_state<NV, CONTACT, TPR>(L3 + (size_t)sb * E3, R, g, s);
-                    Rec rec{SN, a.V1, a.DF, NV};
-                    substep<NV, CONTACT, TPR, true>(sc, P.KIN, P.ES, R, s, g, h, F0.p, gR0, gR1, c0, c1, ac, np,
-                                                    &rec);
-                    load_state<NV, CONTACT, TPR>(L3 + (size_t)sb * E3, R, g, s);
-                    reverse_substep<NV, CONTACT, TPR>(P, R, s, a, SN, g, h, F0, ac, gR0, gR1, c0, c1, np, gm, lpf,
-                                                      lphif, ga);
+                    // the substep's start state and recorded intermediates
+                    const float4* e3 = L3 + (size_t)sb * E3;
+                    load_state<NV, CONTACT, TPR>(e3, R, g, s);
+                    for (int i = g.tid; i < R.nv; i += TPR) {
+                        a.V1[i] = e3[5 * NV + i];
+                        a.DF[i] = e3[6 * NV + i];
+                    }
+                    if (CONTACT)
+                        for (int p = g.tid; p < np; p += TPR) {
+                            s.fr0[p] = e3[7 * NV + p];
+                            s.fr1[p] = e3[(7 + kPairsPerVertex) * NV + p];
+                        }
+                    g.sync();
+                    const float4* sn = e3 + (7 + 2 * kPairsPerVertex) * NV;
+                    reverse_substep<NV, CONTACT, TPR>(P, R, s, a, sn, sn + (size_t)sc.n_iter * NV, g, h, F0, ac,
+                                                      gR0, gR1, c0, c1, np, gm, lpf, lphif, ga);
                 }
                 if (P.gact) {
                     for (int k = 0; k < 6 * R.ngrip; ++k) {

@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
             for (int k = 0; k < 12; ++k)
                 act[k] = P.actions ? P.actions[((long long)f * P.B + rod) * 12 + k] : 0.f;
             bool ovf = false;
-            const int np = run_frame<NV, CONTACT, TPR>(P.scene, P.KIN, P.ES, R, s, g, nsub, h, F, act, ovf,
-                                                       [](int) {});
+            const int np = run_frame<NV, CONTACT, TPR, true>(P.scene, P.KIN, P.ES, R, s, g, nsub, h, F, act, ovf,
+                                                       [](int) -> const Rec* { return nullptr; });
             if (ovf) bad |= 2u;
             np_max = max(np_max, np);
             bool nf = false;

@@ -294,6 +294,47 @@ DLO_HD void contact_respond_rev(V3<float> v, float sdf, V3<float> n, V3<float> v
     lsdf = f0 < 1.f ? -lf * f0 / eps_s : 0.f;
 }
 
+// Reverse of the soft contact of a vertex with a capsule gripper (segment p +- hl * ax, radius
+// rc, rigid velocity vp + w x (x - p)) on the active branch: from the cotangent lo of the output
+// velocity, the cotangents of x, v, the capsule position p, its axis rotation (as a world-frame
+// rotation vector), vp and w.
+DLO_HD void capsule_contact_rev(V3<float> x, V3<float> v, V3<float> p, V3<float> ax, float hl, float rc,
+                                V3<float> vp, V3<float> w, float r, float eps_s, float mu, float rest, V3<float> lo,
+                                V3<float>& lx, V3<float>& lv, V3<float>& lp, V3<float>& lphi, V3<float>& lvp,
+                                V3<float>& lw) {
+    const V3<float> a = p - hl * ax, b = p + hl * ax, ab = b - a;
+    const float L2 = dot(ab, ab);
+    const float q = dot(x - a, ab) / L2;
+    const float sc = q < 0.f ? 0.f : (q > 1.f ? 1.f : q);
+    const V3<float> c = a + sc * ab, dv = x - c;
+    const float d = sqrtf(dot(dv, dv));
+    const V3<float> n = dv / d;
+    const V3<float> y = x - p;
+    const V3<float> vrig = vp + cross(w, y);
+    V3<float> ln, lvrig;
+    float lsdf;
+    contact_respond_rev(v, d - rc, n, vrig, r, eps_s, mu, rest, lo, lv, lsdf, ln, lvrig);
+    lvp = lvrig;
+    lw = cross(y, lvrig);
+    lx = cross(lvrig, w);
+    lp = -lx;
+    const V3<float> ldv = (ln - dot(ln, n) * n) / d + lsdf * n;
+    lx += ldv;
+    const V3<float> lc = -ldv;
+    V3<float> la = lc, lab = sc * lc;
+    if (q > 0.f && q < 1.f) {
+        const float lq = dot(lc, ab);
+        lx += (lq / L2) * ab;
+        la -= (lq / L2) * ab;
+        lab += lq * ((x - a) / L2 - (2.f * q / L2) * ab);
+    }
+    const V3<float> lb = lab;
+    la -= lab;
+    lp += la + lb;
+    const V3<float> lax = hl * (lb - la);
+    lphi = cross(ax, lax);
+}
+
 // ------------------------------------------------------------------ segment closest points
 // Clamped closed-form closest points of segments p1q1 and p2q2 (Ericson, Real-Time Collision
 // Detection, Sec. 5.1.9); near-parallel segments take s = 0 and u clamped.

@@ -100,11 +100,15 @@ __device__ __forceinline__ int grp_excl_scan(int v, const Grp<TPR>& g) {
     return off + incl - v;
 }
 
-// Optional recording of a substep's intermediates for the adjoint (RECORD = true).
+// Optional recording of a substep's intermediates for the adjoint (rec != nullptr): all in
+// global memory, one record per substep of the frame being reversed.
 struct Rec {
-    float4* snap;   // global [n_iter][NV]: displacements at the start of each PBD iteration
-    float4* v1;     // shared [NV]: velocity after the force update, before rigid contact
-    float4* dfin;   // shared [NV]: displacement after the PBD iterations, before friction
+    float4* snap;   // [n_iter][NV]: displacements at the start of each PBD iteration
+    float4* v1;     // [NV]: velocity after the force update, before rigid contact
+    float4* dfin;   // [NV]: displacement after the PBD iterations, before friction
+    float4* fr0;    // [pair capacity]: first-iteration projection data of each pair
+    float4* fr1;
+    float4* csnap;  // [n_iter][3][NV]: displacements after each colour of each PBD iteration
     int nvmax;
 };
 
@@ -410,8 +414,8 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
 }
 
 // ------------------------------------------------------------------ one substep
-template <int NV, bool CONTACT, int TPR, bool RECORD = false>
-__device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
+template <int NV, bool CONTACT, int TPR>
+__device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
                         const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, float h, const float* gpF,
                         const M3* gR0, const M3* gR1, float c0, float c1, const float* act, int np,
                         const Rec* rec = nullptr) {
@@ -496,7 +500,7 @@ __device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, cons
             V3<float> grav = f3(0.f, 0.f, -sc.gravity);
             V3<float> acc = (-xi4.w) * g + grav - R.cd * f3(vi);
             V3<float> v1 = f3(vi) + h * acc;
-            if (RECORD) rec->v1[i] = f4(v1, 0.f);
+            if (rec) rec->v1[i] = f4(v1, 0.f);
             // pose at the substep start for the rigid contact
             float gp0[6];
             for (int q = 0; q < R.ngrip; ++q)
@@ -536,14 +540,19 @@ __device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, cons
     const bool lenc = R.flags & (ROD_INEXT | ROD_SLIMIT);
     if (lenc || np > 0) {
         for (int it = 0; it < sc.n_iter; ++it) {
-            if (RECORD) {
+            if (rec) {
                 for (int i = g.tid; i < nv; i += TPR) rec->snap[(size_t)it * rec->nvmax + i] = s.X[i];
                 g.sync();
             }
             if (lenc) {
-                inext_color<NV, CONTACT, TPR>(R, s, g, 0, closed);
-                inext_color<NV, CONTACT, TPR>(R, s, g, 1, closed);
-                if (closed && (ne & 1)) inext_color<NV, CONTACT, TPR>(R, s, g, 2, closed);
+                const int ncol = (closed && (ne & 1)) ? 3 : 2;
+                for (int k = 0; k < ncol; ++k) {
+                    inext_color<NV, CONTACT, TPR>(R, s, g, k, closed);
+                    if (rec) {
+                        for (int i = g.tid; i < nv; i += TPR) rec->csnap[((size_t)it * 3 + k) * rec->nvmax + i] = s.X[i];
+                        g.sync();
+                    }
+                }
             }
             if (CONTACT && np > 0) contact_sweep<NV, CONTACT, TPR>(R, s, g, np, it == 0);
         }
@@ -552,10 +561,15 @@ __device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, cons
     const float ih = 1.f / h;
     for (int i = g.tid; i < nv; i += TPR) {
         float4 d = s.X[i], v = s.V[i];
-        if (RECORD) rec->dfin[i] = d;
+        if (rec) rec->dfin[i] = d;
         s.V[i] = make_float4(d.x * ih, d.y * ih, d.z * ih, v.w);
     }
     g.sync();
+    if (CONTACT && rec)
+        for (int p = g.tid; p < np; p += TPR) {
+            rec->fr0[p] = s.fr0[p];
+            rec->fr1[p] = s.fr1[p];
+        }
     if (CONTACT && np > 0) self_friction<NV, CONTACT, TPR>(R, s, g, np, h, sc.mu_self);
     for (int i = g.tid; i < nv; i += TPR) {
         float4 x0 = s.X0[i], d = s.X[i], nd = s.ND[i];
@@ -567,6 +581,17 @@ __device__ void substep(const SceneDev& sc, const float4* __restrict__ KIN, cons
     g.sync();
 }
 
+
+// The substep inlined (forward kernel) and as one shared out-of-line copy (the backward
+// kernel calls it from several places; one copy keeps its instruction footprint small).
+template <int NV, bool CONTACT, int TPR>
+__device__ __noinline__ void substep_call(const SceneDev& sc, const float4* __restrict__ KIN,
+                                          const float2* __restrict__ ES, const RodInfo& R, Smem<NV, CONTACT>& s,
+                                          const Grp<TPR>& g, float h, const float* gpF, const M3* gR0,
+                                          const M3* gR1, float c0, float c1, const float* act, int np,
+                                          const Rec* rec) {
+    substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, gpF, gR0, gR1, c0, c1, act, np, rec);
+}
 
 // Gripper poses of a rod at the start of a frame (positions and rotations of both grippers).
 struct Pose {
@@ -597,9 +622,10 @@ __device__ __forceinline__ void substep_rot(const Pose& F, const float* act, int
 }
 
 // One frame of one rod: candidates (if self-contact), nsub substeps, pose update.
-// pre(sb) runs before substep sb (after a warp barrier), e.g. to store the substep state.
-template <int NV, bool CONTACT, int TPR, class PreSub>
-__device__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
+// pre(sb) runs before substep sb (after a group barrier), e.g. to store the substep state, and
+// returns the substep's record (or nullptr).
+template <int NV, bool CONTACT, int TPR, bool INLINE, class PreSub>
+__device__ __forceinline__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
                          const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int nsub, float h, Pose& F,
                          const float* act, bool& ovf, PreSub pre) {
     int np = 0;
@@ -608,10 +634,13 @@ __device__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, con
     gR0[0] = F.R[0];
     gR0[1] = F.R[1];
     for (int sb = 0; sb < nsub; ++sb) {
-        pre(sb);
+        const Rec* rec = pre(sb);
         const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
         substep_rot(F, act, R.ngrip, c1, gR1);
-        substep<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, F.p, gR0, gR1, c0, c1, act, np);
+        if (INLINE)
+            substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, F.p, gR0, gR1, c0, c1, act, np, rec);
+        else
+            substep_call<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, F.p, gR0, gR1, c0, c1, act, np, rec);
         gR0[0] = gR1[0];
         gR0[1] = gR1[1];
     }

@@ -101,3 +101,62 @@ extern "C" void expmap_host(const float* phi, float* R) {
     M3 m = expmap(ld3(phi));
     for (int k = 0; k < 9; ++k) R[k] = m.m[k];
 }
+
+// Capsule-gripper contact: closed-form reverse against dual-number directional derivatives.
+// in: x(3) v(3) p(3) ax(3) hl rc vp(3) w(3) r eps mu rest lo(3)  (29)
+// out: closed-form (lx, lv, lp, lphi, lvp, lw) then the same from dual numbers (36), active (1)
+template <class T>
+static V3<T> capsule_eval(V3<T> x, V3<T> v, V3<T> p, V3<T> ax, float hl, float rc, V3<T> vp, V3<T> w, float r,
+                          float eps, float mu, float rest, bool& act) {
+    V3<T> n;
+    T sdf = sdf_capsule(x, p - hl * ax, p + hl * ax, rc, n);
+    V3<T> vr = vp + cross(w, x - p);
+    return contact_respond(v, sdf, n, vr, r, eps, mu, rest, act);
+}
+extern "C" void capsule_rev_check(const float* in, float* out) {
+    V3<float> x = ld3(in), v = ld3(in + 3), p = ld3(in + 6), ax = ld3(in + 9), vp = ld3(in + 14), w = ld3(in + 17);
+    float hl = in[12], rc = in[13], r = in[20], eps = in[21], mu = in[22], rest = in[23];
+    V3<float> lo = ld3(in + 24);
+    bool on;
+    capsule_eval<float>(x, v, p, ax, hl, rc, vp, w, r, eps, mu, rest, on);
+    out[36] = on ? 1.f : 0.f;
+    V3<float> o[6];
+    capsule_contact_rev(x, v, p, ax, hl, rc, vp, w, r, eps, mu, rest, lo, o[0], o[1], o[2], o[3], o[4], o[5]);
+    for (int k = 0; k < 6; ++k) st3(out + 3 * k, o[k]);
+    for (int d = 0; d < 18; ++d) {
+        V3<float> e = zf3();
+        (d % 3 == 0 ? e.x : d % 3 == 1 ? e.y : e.z) = 1.f;
+        int gi = d / 3;
+        bool act;
+        V3<dualf> res = capsule_eval<dualf>(lift(x, gi == 0 ? e : zf3()), lift(v, gi == 1 ? e : zf3()),
+                                            lift(p, gi == 2 ? e : zf3()), lift(ax, gi == 3 ? cross(e, ax) : zf3()),
+                                            hl, rc, lift(vp, gi == 4 ? e : zf3()), lift(w, gi == 5 ? e : zf3()), r,
+                                            eps, mu, rest, act);
+        out[18 + d] = dot(ders(res), lo);
+    }
+}
+
+// Plane contact: closed-form reverse against dual numbers.  in: x(3) v(3) n(3) off r eps mu rest lo(3)
+// out: lx(3) lv(3) then the dual-number ones (12), active (1)
+extern "C" void plane_rev_check(const float* in, float* out) {
+    V3<float> x = ld3(in), v = ld3(in + 3), n = ld3(in + 6), lo = ld3(in + 14);
+    float off = in[9], r = in[10], eps = in[11], mu = in[12], rest = in[13];
+    V3<float> lv, ln, lvr;
+    float lsdf;
+    bool on;
+    contact_respond(v, dot(x, n) - off, n, zf3(), r, eps, mu, rest, on);
+    out[12] = on ? 1.f : 0.f;
+    contact_respond_rev(v, dot(x, n) - off, n, zf3(), r, eps, mu, rest, lo, lv, lsdf, ln, lvr);
+    st3(out, lsdf * n);
+    st3(out + 3, lv);
+    for (int d = 0; d < 6; ++d) {
+        V3<float> e = zf3();
+        (d % 3 == 0 ? e.x : d % 3 == 1 ? e.y : e.z) = 1.f;
+        V3<dualf> xd = lift(x, d < 3 ? e : zf3()), vd = lift(v, d >= 3 ? e : zf3());
+        V3<dualf> nd = lift(n);
+        dualf sdf = dot(xd, nd) - off;
+        bool act;
+        V3<dualf> res = contact_respond(vd, sdf, nd, lift(zf3()), r, eps, mu, rest, act);
+        out[6 + d] = dot(ders(res), lo);
+    }
+}

@@ -28,7 +28,8 @@ def H():
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     lib = C.CDLL(out)
-    for n in ("hinge_grad_host", "contact_host", "closest_host", "expmap_host"):
+    for n in ("hinge_grad_host", "contact_host", "closest_host", "expmap_host", "capsule_rev_check",
+              "plane_rev_check"):
         getattr(lib, n).argtypes = [C.c_void_p, C.c_void_p]
     lib.hinge_hvp_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     return lib
@@ -171,3 +172,33 @@ def test_closest_points_and_expmap(H):
         phi = rng.normal(size=3) * (10.0 ** rng.uniform(-6, 0))
         out = call(H.expmap_host, fl(phi), n_out=9)
         np.testing.assert_allclose(out.reshape(3, 3), expmap(torch.tensor(phi)).numpy(), atol=2e-7)
+
+
+def test_closed_form_contact_reverses_match_dual_numbers(H):
+    """The adjoint's closed-form reverses of the plane and capsule-gripper contact responses
+    equal the transpose-Jacobian products taken with dual numbers through the forward code."""
+    rng = np.random.default_rng(5)
+    n_active = 0
+    for trial in range(200):
+        x = rng.normal(size=3) * 0.006
+        x[2] = abs(x[2]) + 0.009                 # around the capsule surface
+        v = rng.normal(size=3) * 0.2
+        p = np.zeros(3)
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        inp = fl(np.concatenate([x, v, p, ax, [0.02, 0.01], rng.normal(size=3) * 0.05, rng.normal(size=3),
+                                 [0.002, 0.001, 0.5, 0.0], rng.normal(size=3)]))
+        out = call(H.capsule_rev_check, inp, n_out=37)
+        if out[36] == 0:
+            continue                             # not in contact
+        n_active += 1
+        np.testing.assert_allclose(out[:18], out[18:36], rtol=2e-3, atol=2e-3 * np.abs(out[18:36]).max())
+    assert n_active > 20
+    for trial in range(100):
+        x = np.array([0.0, 0.0, rng.uniform(-0.002, 0.004)])
+        inp = fl(np.concatenate([x, rng.normal(size=3) * 0.3, [0, 0, 1.0], [0.0, 0.002, 0.001, 0.5, 0.0],
+                                 rng.normal(size=3)]))
+        out = call(H.plane_rev_check, inp, n_out=13)
+        if out[12] == 0:
+            continue
+        np.testing.assert_allclose(out[:6], out[6:12], rtol=2e-3, atol=2e-3 * max(np.abs(out[6:12]).max(), 1e-6))
