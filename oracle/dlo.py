@@ -364,9 +364,11 @@ class OracleSim:
         if closed:
             kb[..., 1] = 2.0 * math.tan(math.pi / G["E"])
         R["kbar0"] = kb
-        # self-contact exclusion window (reading: pairs closer than k edges along the rod are
-        # never tested, k = max(2, ceil(2r / shortest rest edge) + 1))
-        R["excl"] = [max(2, int(math.ceil(2 * float(p.radius[b]) / float(self.ebar[b].min()))) + 1) for b in ids]
+        # self-contact exclusion window (reading: edge pairs at most k apart along the rod are
+        # never tested; k = max(1, ceil(2r / shortest rest edge)) is the smallest window that
+        # leaves a straight rod at its rest lengths with no pair inside the contact distance 2r,
+        # so edges two apart still collide and keep a hinge from folding through itself)
+        R["excl"] = [max(1, int(math.ceil(2 * float(p.radius[b]) / float(self.ebar[b].min())))) for b in ids]
         G["R"] = R
         G["gpos0"] = t64(p.grip_pos[ids])
         G["grot0"] = t64(p.grip_rot[ids])

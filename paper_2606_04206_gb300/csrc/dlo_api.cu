@@ -233,7 +233,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
                   (!inext && m.strain_limit > 0.f ? ROD_SLIMIT : 0) | (opt->self_contact ? ROD_SELF : 0) |
                   (closed ? ROD_CLOSED : 0);
         R.ngrip = ng;
-        R.excl = std::max(2, (int)std::ceil(2.0 * r / lmin) + 1);
+        R.excl = std::max(1, (int)std::ceil(2.0 * r / lmin));
         R.h = (float)(opt->dt / ns);
         R.kA = inext ? 0.f : (float)(m.K_stretch * A);
         R.Bm = (float)(m.E_bend * A * r * r / 4.0);

@@ -15,17 +15,25 @@ Workloads (seeds are ``numpy.random.default_rng(config_index*1000 + repeat)``):
                  pinned, K=E=1e6 Pa, G=4e5 Pa, no contact, 200 frames.
 * ``batching``   1024 rods, 16..256 vertices, 0.3..2 m, E log-uniform in
                  [1e4, 1e8] Pa (K=E, G=0.4E), plastic (yield 1..20 1/m),
-                 random smooth splines above a ground plane, two capsule
-                 grippers with smooth random 6-DoF trajectories, 1000 frames.
-* ``diff``       256 rods x 64 vertices, half elastic rope (Unknotting row),
-                 half plastic wire (Letter-Art row), 500 frames, checkpoints
-                 every 50, seeded spline targets.
+                 random smooth curves resting on a table (the ground plane),
+                 two capsule grippers with smooth random 6-DoF trajectories,
+                 1000 frames.
+* ``diff``       256 rods x 64 vertices on the table, half elastic rope
+                 (Unknotting row), half plastic wire (Letter-Art row), 500
+                 frames, checkpoints every 50, seeded smooth target curves.
 * ``selfcontact``4096 closed bands x 200 vertices (trefoil-like knots, 1 m
                  circumference), half inextensible, half 20 % strain-limited,
                  ground + box obstacle, self-contact, 300 frames.
-* ``trajopt``    4096 rods x 128 vertices, one third each inextensible cable
-                 (Wiring-post row), elastic rope (Unknotting row), plastic wire
-                 (Letter-Art row), two grippers, 2000 frames.
+* ``trajopt``    4096 rods x 128 vertices (1 m, radius 2 mm) resting on the
+                 table, one third each inextensible cable (Wiring-post row),
+                 elastic rope (Unknotting row), plastic wire (Letter-Art row),
+                 grasped at 1/4 and 3/4 of their length by two grippers with
+                 smooth random 6-DoF trajectories, 2000 frames.
+
+The open rods of batching, diff and trajopt are smooth curves whose unit tangent is a
+low-frequency random Fourier series (bending radius >= 2 cm), lying nearly horizontal
+just above the ground plane, as the rods of the paper's manipulation tasks start out on
+the table.
 """
 from __future__ import annotations
 
@@ -134,17 +142,33 @@ class Problem:
 
 # --------------------------------------------------------------------------- shapes
 
-def _catmull_rom(ctrl: np.ndarray, per_seg: int = 32) -> np.ndarray:
-    """Dense uniform Catmull-Rom polyline through the control points (open)."""
-    p = np.concatenate([ctrl[:1] * 2 - ctrl[1:2], ctrl, ctrl[-1:] * 2 - ctrl[-2:-1]])
-    s = np.linspace(0.0, 1.0, per_seg, endpoint=False)[:, None]
-    out = []
-    for i in range(1, len(p) - 2):
-        p0, p1, p2, p3 = p[i - 1], p[i], p[i + 1], p[i + 2]
-        out.append(0.5 * ((2 * p1) + (-p0 + p2) * s + (2 * p0 - 5 * p1 + 4 * p2 - p3) * s ** 2
-                          + (-p0 + 3 * p1 - 3 * p2 + p3) * s ** 3))
-    out.append(ctrl[-1:])
-    return np.concatenate(out)
+def _smooth_tangent_curve(rng, length: float, modes: int = 3, amp: float = 1.0,
+                          zscale: float = 0.15, dense: int = 4096) -> np.ndarray:
+    """Dense polyline of the given arc length whose unit tangent is a normalised
+    low-frequency random Fourier series (a horizontal heading plus ``modes`` sine/cosine
+    terms per axis, mode k at amplitude amp/k, the vertical terms scaled by ``zscale`` so
+    the curve stays nearly horizontal).  Curvature stays bounded because the tangent field
+    has no high-frequency content; there are no cusps."""
+    s = np.linspace(0.0, 1.0, dense)
+    d = np.append(rng.normal(size=2), 0.0)
+    d /= np.linalg.norm(d)
+    tan = np.tile(d, (dense, 1))
+    scale = np.array([1.0, 1.0, zscale])
+    for k in range(1, modes + 1):
+        a = rng.uniform(-1.0, 1.0, (2, 3)) * scale * amp / k
+        tan = tan + np.sin(2 * np.pi * k * s)[:, None] * a[0] + np.cos(2 * np.pi * k * s)[:, None] * a[1]
+    tan /= np.maximum(np.linalg.norm(tan, axis=1), 1e-9)[:, None]
+    step = 0.5 * (tan[1:] + tan[:-1]) * (length / (dense - 1))
+    return np.concatenate([np.zeros((1, 3)), np.cumsum(step, axis=0)])
+
+
+def _max_curvature(x: np.ndarray) -> float:
+    """Largest discrete curvature (turning angle / edge length) of an open polyline."""
+    e = np.diff(x, axis=0)
+    ln = np.linalg.norm(e, axis=1)
+    t = e / ln[:, None]
+    ang = np.arccos(np.clip((t[:-1] * t[1:]).sum(1), -1.0, 1.0))
+    return float((ang / (0.5 * (ln[:-1] + ln[1:]))).max()) if len(ang) else 0.0
 
 
 def _resample(poly: np.ndarray, n: int, closed: bool = False) -> np.ndarray:
@@ -173,19 +197,23 @@ def _too_close(x: np.ndarray, min_dist: float, skip: int, closed: bool) -> bool:
     return bool(len(i) and d[i, j].min() < min_dist)
 
 
-def _spline_rod(rng, n: int, length: float, radius: float, z_min: float = 0.08,
-                box=((-0.5, 0.5), (-0.5, 0.5), (0.3, 0.8))) -> np.ndarray:
+def _spline_rod(rng, n: int, length: float, radius: float, z_min: float = 0.005,
+                box=((-0.25, 0.25), (-0.25, 0.25)), max_curv: float = 50.0) -> np.ndarray:
+    """A random smooth open 3D curve of n vertices and the given length lying on a table:
+    nearly horizontal (a few cm of vertical undulation), its lowest vertex at ``z_min``
+    above the ground plane z = 0 and its centroid uniform in ``box`` (x, y); redrawn until
+    its bending radius stays above 1/max_curv everywhere and no two non-neighbouring
+    vertices are closer than 4r."""
+    amp = min(1.0, length)
     for _ in range(200):
-        ctrl = np.stack([rng.uniform(lo, hi, 6) for lo, hi in box], axis=1)
-        x = _resample(_catmull_rom(ctrl), n)
-        c = x.mean(0)
-        x = c + (x - c) * (length / _length(x))
-        x = _resample(x, n)
-        x[:, 2] += max(0.0, z_min - x[:, 2].min())
+        x = _resample(_smooth_tangent_curve(rng, length, amp=amp), n)
+        c = np.array([rng.uniform(lo, hi) for lo, hi in box])
+        x[:, :2] += c - x[:, :2].mean(0)
+        x[:, 2] += z_min - x[:, 2].min()
         skip = max(2, int(np.ceil(4 * radius * (n - 1) / length)) + 1)
-        if not _too_close(x, 4 * radius, skip, False):
+        if _max_curvature(x) <= max_curv and not _too_close(x, 4 * radius, skip, False):
             return x
-    raise RuntimeError("could not draw a non-self-intersecting spline")
+    raise RuntimeError("could not draw a smooth non-self-intersecting rod")
 
 
 def _knot_band(rng, n: int, circumference: float, radius: float, z_min: float) -> np.ndarray:

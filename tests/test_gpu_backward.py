@@ -1,9 +1,9 @@
 """The device adjoint (dlo_backward) against the FP64 oracle's reverse-mode gradients and
-against FP64 central differences.  Tolerances: relative L2 error <= 1e-3 and cosine >= 0.999
-for the gradients with respect to the actions and the initial positions, velocities, twist
-rates and twist angles.  Material gradients are compared as the scale-free sensitivities
-p * dL/dp (K, E, G, yield curvature, damping) to relative L2 <= 1e-2 and cosine >= 0.999:
-an exact float32 evaluation drifts a few 1e-3 there (tests/test_oracle_fp32_floor.py)."""
+against FP64 central differences.  Tolerance: relative L2 error <= 1e-3 and cosine >= 0.999
+for the gradients with respect to the actions, the initial positions, velocities, twist
+rates and twist angles, and the material parameters; the latter are compared as the
+scale-free sensitivities p * dL/dp (K, E, G, yield curvature, damping), since their raw
+gradients span many orders of magnitude."""
 import numpy as np
 import pytest
 import torch
@@ -29,7 +29,7 @@ def weights(prob, seed=0):
     return wx, wv, wth
 
 
-TOL = {"material": 1e-2}
+TOL = {}
 
 
 def log_sens(prob, g):
@@ -47,6 +47,7 @@ def check(prob, frames, seed=0, **opt):
     for k in GROUPS:
         rel, cos = grad_agreement(got[k], ref[k])
         report[k] = (rel, cos)
+    print("gradient agreement (rel L2, cosine):", {k: (f"{r:.2e}", f"{c:.6f}") for k, (r, c) in report.items()})
     bad = {k: v for k, v in report.items() if not (v[0] <= TOL.get(k, 1e-3) and v[1] >= 0.999)}
     assert not bad, report
     return report
@@ -121,8 +122,8 @@ def test_backward_matches_central_differences_sampled():
             g = got[name][idx]
         else:
             g = got["material"][idx, {"E": 1, "yield_curv": 3}[name]]
-        tol = 1e-2 if name in ("E", "yield_curv") else 1e-3
-        assert g == pytest.approx(fd, rel=tol, abs=1e-6 * np.abs(got["act"]).max()), (name, idx, g, fd)
+        print("central difference", name, idx, "device %.6e fd %.6e rel %.2e" % (g, fd, abs(g - fd) / max(abs(fd), 1e-300)))
+        assert g == pytest.approx(fd, rel=1e-3, abs=1e-6 * np.abs(got["act"]).max()), (name, idx, g, fd)
         n_ok += 1
     assert n_ok == 16
 
