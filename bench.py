@@ -37,6 +37,10 @@ UNIT = "rod-vertex-steps/s"
 # kernels' own element templates; tests/test_flop_count.py keeps these in step)
 FLOPS_FWD_PER_VS = 921.3
 FLOPS_BWD_PER_VS = 3668.0
+# DRAM bytes (read + write) of bwd_kernel per rod-frame of the 128-vertex self-contact
+# workload, from one ncu capture of a 304-rod x 50-frame case of it (its recompute scratch
+# grows with rod-frames; profiles/fwd_bwd_kernels_trajopt_304x128x50.md)
+BWD_DRAM_BYTES_PER_ROD_FRAME = (761.300736e6 + 3334.433e6) / (304 * 50)
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
@@ -277,8 +281,9 @@ def run_native(args, rank, ws):
     peak_tflops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     bwd_tflops = FLOPS_BWD_PER_VS * vs_units / (ms_bwd / 1e3) / 1e12
     fwd_tflops = FLOPS_FWD_PER_VS * vs_units / (ms_fwd / 1e3) / 1e12
+    traffic = BWD_DRAM_BYTES_PER_ROD_FRAME * R * F if (N == 128 and not args.no_self_contact) else None
     roofline = {"bound": "alu", "kernel": "bwd_kernel (dlo_backward)", "achieved": bwd_tflops,
-                "peak": peak_tflops, "unit": "TFLOP/s", "frac": bwd_tflops / peak_tflops, "traffic": None,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": bwd_tflops / peak_tflops, "traffic": traffic,
                 "peak_basis": f"FP32 CUDA cores: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                               f"{max_mhz:.0f} MHz", "forward": {"achieved": fwd_tflops,
                                                                 "frac": fwd_tflops / peak_tflops}}
