@@ -155,6 +155,33 @@ dlo_status dlo_backward(dlo_ctx* ctx, const float* dL_dx_T, const float* dL_dv_T
                         const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
                         float* dL_dx0, float* dL_dv0, float* dL_dtheta0);
 
+/* The same adjoint with no memory allocation.  The paper has no counterpart: this is an
+ * interface for callers that cannot allocate during the call, such as an optimisation loop
+ * whose device memory budget is already handed out (an allocator pool at capacity, or memory
+ * partitioned between simulation workers), where a workspace allocation would fail with
+ * out-of-memory in the middle of a run.  Arguments, outputs and results are those of
+ * dlo_backward.  Every temporary comes from one static device array of
+ * DLO_NOALLOC_SCRATCH_BYTES inside the library; the call makes no cudaMalloc, cudaFree or
+ * other allocating call on the device and no heap allocation on its success path.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture begins.
+ *   Zero state: nothing in the array needs to start at zero (every scratch word is written
+ *   before it is read); the per-launch work-queue heads, which live in context memory from
+ *   dlo_create, are reset with cudaMemsetAsync on the context's stream.
+ *   Capacity: the rods run with as many in flight as the array holds (fewer than
+ *   dlo_backward uses, so it can be slower).  When one rod's recompute buffers plus the
+ *   batch-wide frame cotangents (32 bytes per edge, plus 96 per vertex when dL_dx0 is asked
+ *   for after dlo_set_state) exceed the array, the call returns DLO_ERR_CAPACITY and
+ *   dlo_last_error states the sizes.
+ *   Concurrency: the array is shared by every context on the device, so calls must not
+ *   overlap (two calls in flight from different threads or streams race on it).  Each call
+ *   synchronises its stream before returning. */
+#define DLO_NOALLOC_SCRATCH_BYTES ((size_t)256 << 20)
+dlo_status dlo_backward_noalloc(dlo_ctx* ctx, const float* dL_dx_T, const float* dL_dv_T,
+                                const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
+                                float* dL_dx0, float* dL_dv0, float* dL_dtheta0);
+
 enum {
     DLO_Q_SUBSTEPS = 1,      /* int [B]: substeps per frame of each rod */
     DLO_Q_STATUS = 2,        /* unsigned [B]: status bits (1 non-finite, 2 pair overflow) */

@@ -127,6 +127,12 @@ cudaError_t launch_backward(const BwdParams& P, int nv, bool c, int grid, int wa
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_frames_adjoint(const RodInfo* rods, int B, const float4* X0, const float4* gtb0,
+                                  const float4* gd1b0, float4* gx0, V3<double>* work, cudaStream_t st) {
+    frames_adjoint_kernel<<<(B + 127) / 128, 128, 0, st>>>(rods, B, X0, gtb0, gd1b0, gx0, work);
+    return cudaGetLastError();
+}
+
 int backward_blocks_per_sm(int nv, bool c, int warps) {
     switch (nv) {
         case 32: return backward_occ_nv32(c, warps);

@@ -88,6 +88,8 @@ def load(path: str | None = None):
     lib.dlo_step_plain.restype = st
     lib.dlo_backward.argtypes = [vp] * 9
     lib.dlo_backward.restype = st
+    lib.dlo_backward_noalloc.argtypes = [vp] * 9
+    lib.dlo_backward_noalloc.restype = st
     lib.dlo_query.argtypes = [vp, ip, vp]
     lib.dlo_query.restype = st
     lib.dlo_status_string.argtypes = [st]
@@ -295,6 +297,21 @@ class DloSim:
                                    _ptr(out.get("material")), _ptr(out.get("x0")), _ptr(out.get("v0")),
                                    _ptr(out.get("theta0")))
         self._check(st, "dlo_backward")
+        return out
+
+    def backward_noalloc(self, dL_dx=None, dL_dv=None, dL_dtheta=None,
+                         want=("actions", "material", "x0", "v0", "theta0")):
+        """dlo_backward_noalloc: the same gradients with no allocation inside the library
+        (the output tensors are the caller's, allocated here by torch before the call)."""
+        torch = self.torch
+        n = getattr(self, "_rollout_frames", 0)
+        shapes = {"actions": (n, self.B, 2, 6), "material": (self.B, N_MAT_GRAD), "x0": (self.V, 4),
+                  "v0": (self.V, 4), "theta0": (self.E,)}
+        out = {k: torch.zeros(*shapes[k], device=self.device) for k in want}
+        st = self.lib.dlo_backward_noalloc(self.ctx, _ptr(dL_dx), _ptr(dL_dv), _ptr(dL_dtheta),
+                                           _ptr(out.get("actions")), _ptr(out.get("material")),
+                                           _ptr(out.get("x0")), _ptr(out.get("v0")), _ptr(out.get("theta0")))
+        self._check(st, "dlo_backward_noalloc")
         return out
 
     def query(self, what):
