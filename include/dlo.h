@@ -95,7 +95,8 @@ typedef struct {
     float  restitution;     /* rigid-contact restitution */
     float  eps_soft;        /* softness eps_s as a multiple of the rod radius */
     float  contact_margin;  /* self-contact candidate margin as a multiple of the radius */
-    int    self_contact;    /* 1: self-collision projections and friction on */
+    int    self_contact;    /* 1: self-collision projections and friction on (needs
+                               n_iter_pbd >= 1: friction uses the first iteration's contacts) */
     int    checkpoint_every;/* frames between rollout checkpoints; 0 = chosen by the library */
     size_t hbm_budget;      /* bytes for checkpoints + backward buffers; 0 = 80 GiB */
     int    warps_per_cta;   /* rods per CTA of the persistent kernels; 0 = autotune */

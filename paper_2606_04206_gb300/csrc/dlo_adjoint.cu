@@ -147,23 +147,18 @@ int backward_blocks_per_sm(int nv, bool c, int warps) {
 
 using namespace dlo;
 
-extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float* dL_dv_T, const float* dL_dtheta_T,
-                                   float* dL_dactions, float* dL_dmaterial, float* dL_dx0, float* dL_dv0,
-                                   float* dL_dtheta0) {
-    if (!c) return DLO_ERR_INVALID_ARG;
-    if (!c->rec_active || c->rec_done != c->rec_frames || c->rec_frames == 0)
-        return set_err(c, DLO_ERR_STATE, "dlo_backward needs a completed rollout armed by dlo_begin_rollout");
-    for (const void* p : {(const void*)dL_dx_T, (const void*)dL_dv_T, (const void*)dL_dx0, (const void*)dL_dv0})
-        if (p && ((uintptr_t)p & 15u)) return set_err(c, DLO_ERR_INVALID_ARG, "float4 arrays must be 16-byte aligned");
-    if (c->opt.self_contact && c->opt.n_iter_pbd < 1)
-        return set_err(c, DLO_ERR_INVALID_ARG, "self-contact gradients need at least one projection iteration");
-    const int force = c->rec_nsub > 0 ? c->rec_nsub : 0;
-    // per-bucket scratch: frame-start states of one segment, substep-start states of one
-    // frame and the PBD snapshots of one substep, per resident warp
+// Launch shape and workspace of the backward for checkpoint interval K: per size class the
+// rods per CTA and CTAs that keep the most rods resident, each resident rod's recompute
+// scratch (frame-start states of one segment, substep-start states and records of one
+// frame), plus the batch-wide frame cotangents and the FP64 work of the frame adjoint.
+dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out) {
+    const size_t nb_ = c->buckets.size();
+    out.slot_b.assign(nb_, 0);
+    out.warps.assign(nb_, 0);
+    out.grid.assign(nb_, 0);
+    out.nsmax.assign(nb_, 0);
     size_t need = 0;
-    std::vector<size_t> slot_b(c->buckets.size());
-    std::vector<int> warps(c->buckets.size()), grid(c->buckets.size()), nsmax(c->buckets.size());
-    for (size_t k = 0; k < c->buckets.size(); ++k) {
+    for (size_t k = 0; k < nb_; ++k) {
         const Bucket& bk = c->buckets[k];
         int w = 0, nb = 0;
         for (int rpc = 1; rpc <= 16; ++rpc) {
@@ -179,15 +174,35 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
             for (int b = 0; b < c->B; ++b)
                 if (((c->rods_h[b].nv <= 32) ? 32 : (c->rods_h[b].nv <= 64) ? 64 : (c->rods_h[b].nv <= 128) ? 128 : 256) == bk.nv_max)
                     ns = std::max(ns, c->nsub[b]);
-        nsmax[k] = ns;
+        out.nsmax[k] = ns;
         const size_t NV = bk.nv_max;
-        slot_b[k] = 16 * ((size_t)c->ck_every * (5 * NV + 6) +
-                          (size_t)ns * ((7 + 2 * kPairsPerVertex) * NV + (size_t)4 * c->opt.n_iter_pbd * NV));
-        warps[k] = w;
-        grid[k] = (int)std::min<long long>((long long)nb * c->sm_count, (bk.n + w - 1) / w);
-        need = std::max(need, slot_b[k] * (size_t)grid[k] * w);
+        out.slot_b[k] = 16 * ((size_t)K * (5 * NV + 6) +
+                              (size_t)ns * ((7 + 2 * kPairsPerVertex) * NV + (size_t)4 * c->opt.n_iter_pbd * NV));
+        out.warps[k] = w;
+        out.grid[k] = (int)std::min<long long>((long long)nb * c->sm_count, (bk.n + w - 1) / w);
+        need = std::max(need, out.slot_b[k] * (size_t)out.grid[k] * w);
     }
-    need += 2 * 16 * (size_t)c->Et + 4 * sizeof(V3<double>) * (size_t)c->V + 1024;
+    out.bytes = need + 2 * 16 * (size_t)c->Et + 4 * sizeof(V3<double>) * (size_t)c->V + 1024;
+    return DLO_OK;
+}
+
+extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float* dL_dv_T, const float* dL_dtheta_T,
+                                   float* dL_dactions, float* dL_dmaterial, float* dL_dx0, float* dL_dv0,
+                                   float* dL_dtheta0) {
+    if (!c) return DLO_ERR_INVALID_ARG;
+    if (!c->rec_active || c->rec_done != c->rec_frames || c->rec_frames == 0)
+        return set_err(c, DLO_ERR_STATE, "dlo_backward needs a completed rollout armed by dlo_begin_rollout");
+    for (const void* p : {(const void*)dL_dx_T, (const void*)dL_dv_T, (const void*)dL_dx0, (const void*)dL_dv0})
+        if (p && ((uintptr_t)p & 15u)) return set_err(c, DLO_ERR_INVALID_ARG, "float4 arrays must be 16-byte aligned");
+    if (c->opt.self_contact && c->opt.n_iter_pbd < 1)
+        return set_err(c, DLO_ERR_INVALID_ARG, "self-contact gradients need at least one projection iteration");
+    const int force = c->rec_nsub > 0 ? c->rec_nsub : 0;
+    BwdPlan plan;
+    dlo_status pst = bwd_plan(c, force, c->ck_every, plan);
+    if (pst != DLO_OK) return pst;
+    const size_t need = plan.bytes;
+    const std::vector<size_t>& slot_b = plan.slot_b;
+    const std::vector<int>&warps = plan.warps, &grid = plan.grid, &nsmax = plan.nsmax;
     if (need > c->bw_bytes) {
         dev_free(c, c->bw_mem);
         c->bw_mem = dev_alloc(c, need);

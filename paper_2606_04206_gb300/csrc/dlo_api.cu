@@ -86,6 +86,8 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         opt->checkpoint_every < 0 || opt->warps_per_cta < 0 || opt->warps_per_cta > 8 || !(opt->eps_soft > 0.f) ||
         opt->contact_margin < 0.f || opt->mu_self < 0.f || opt->mu_rigid < 0.f || opt->restitution < 0.f)
         return DLO_ERR_INVALID_ARG;
+    // self-contact friction acts on the contact set of the first projection iteration
+    if (opt->self_contact && opt->n_iter_pbd < 1) return DLO_ERR_INVALID_ARG;
     if (scene && (scene->n_planes < 0 || scene->n_planes > kMaxPlanes || scene->n_boxes < 0 ||
                   scene->n_boxes > kMaxBoxes || (scene->n_planes && !scene->planes) ||
                   (scene->n_boxes && !scene->boxes)))

@@ -652,6 +652,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                 if (g.tid == 0)
                     for (int k = 0; k < 24; ++k) reinterpret_cast<float*>(e + 5 * NV)[k] = F.p[k];
                 g.sync();
+                if (f + 1 == f1) break;   // the segment's last frame only needs its start state
                 const float* act = P.actions + ((size_t)f * P.B + rod) * 12;
                 float ac[12];
 #pragma unroll

@@ -123,10 +123,26 @@ void runtime_release(dlo_ctx*) {}
 extern "C" dlo_status dlo_begin_rollout(dlo_ctx* c, int n_frames) {
     if (!c) return DLO_ERR_INVALID_ARG;
     if (n_frames <= 0) return set_err(c, DLO_ERR_INVALID_ARG, "n_frames must be positive");
-    int K = c->opt.checkpoint_every > 0 ? c->opt.checkpoint_every : std::min(n_frames, 50);
-    K = std::min(K, n_frames);
-    const int count = (n_frames + K - 1) / K;
     const size_t per = 16 * (3 * (size_t)c->V + 2 * (size_t)c->Et) + sizeof(float) * 24 * (size_t)c->B;
+    const size_t abytes = sizeof(float) * 12 * (size_t)c->B * n_frames;
+    int K = std::min(c->opt.checkpoint_every, n_frames);
+    if (K <= 0) {
+        // autotune: the shortest interval (the least recomputation in the backward) whose
+        // checkpoint ring, action record and backward workspace fit the HBM budget; the
+        // backward reruns at most K - 1 frames per segment to rebuild the frame-start states
+        const size_t budget = c->opt.hbm_budget ? c->opt.hbm_budget : ((size_t)80 << 30);
+        K = n_frames;
+        for (int k = 1; k <= n_frames; ++k) {
+            BwdPlan plan;
+            if (bwd_plan(c, 0, k, plan) != DLO_OK) return DLO_ERR_INVALID_ARG;
+            const size_t total = per * (size_t)((n_frames + k - 1) / k) + abytes + plan.bytes;
+            if (total <= budget) {
+                K = k;
+                break;
+            }
+        }
+    }
+    const int count = (n_frames + K - 1) / K;
     const size_t need = per * count + 256 * 8;
     if (need > c->ck_bytes) {
         dev_free(c, c->ck_mem);
@@ -146,7 +162,6 @@ extern "C" dlo_status dlo_begin_rollout(dlo_ctx* c, int n_frames) {
     c->ck.ED = reinterpret_cast<float4*>(take(16 * c->Et * count));
     c->ck.ET = reinterpret_cast<float4*>(take(16 * c->Et * count));
     c->ck.GP = reinterpret_cast<float*>(take(sizeof(float) * 24 * c->B * count));
-    const size_t abytes = sizeof(float) * 12 * (size_t)c->B * n_frames;
     if (abytes > c->rec_bytes) {
         dev_free(c, c->rec_actions);
         c->rec_actions = reinterpret_cast<float*>(dev_alloc(c, abytes));

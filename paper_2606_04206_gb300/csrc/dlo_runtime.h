@@ -67,6 +67,14 @@ struct dlo_ctx {
     size_t pl_bytes = 0;
 };
 
+// launch shape and workspace size of the backward for a checkpoint interval (dlo_adjoint.cu)
+struct BwdPlan {
+    std::vector<size_t> slot_b;
+    std::vector<int> warps, grid, nsmax;
+    size_t bytes = 0;
+};
+dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out);
+
 dlo_status set_err(dlo_ctx* c, dlo_status s, const std::string& msg);
 dlo_status cuda_err(dlo_ctx* c, cudaError_t e, const char* where);
 dlo_status check_status(dlo_ctx* c);
