@@ -150,7 +150,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         const int ne = nv - 1 + (closed ? 1 : 0);
         const double r = m.radius, rho = m.density, A = M_PI * r * r;
         std::vector<double> eb(ne);
-        double lmin = 1e300, lmax = 0.0;
+        double lmin = 1e300;
         for (int j = 0; j < ne; ++j) {
             int j1 = (j + 1 == nv) ? 0 : j + 1;
             double dx = (double)x_rest[3 * (v0 + j1)] - x_rest[3 * (v0 + j)];
@@ -162,7 +162,6 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
                 return DLO_ERR_INVALID_ARG;
             }
             lmin = std::min(lmin, eb[j]);
-            lmax = std::max(lmax, eb[j]);
             es[e0 + j] = make_float2((float)eb[j], (float)(1.0 / (0.5 * rho * A * eb[j] * r * r)));
         }
         const bool inext = m.inextensible != 0;
@@ -246,7 +245,6 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         R.radius = m.radius;
         R.slim = (!inext && m.strain_limit > 0.f) ? m.strain_limit : 0.f;
         R.contact_d = (float)(2.0 * r + opt->contact_margin * r);
-        R.cell = (float)(R.contact_d + 1.5 * lmax);
         R.eps = (float)(opt->eps_soft * r);
         R.pair_cap = kPairsPerVertex * nv_bucket(nv);
         R.pair_off = 0;

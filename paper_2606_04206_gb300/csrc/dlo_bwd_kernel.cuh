@@ -372,6 +372,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             vs[0] = f3(a.V1[i]);
             const V3<float> x = f3(x4);
             const float idt = 1.f / sc.dt;
+            unsigned onmask = 0;
             for (int k = 0; k < nprim; ++k) {
                 const int q = k - sc.n_planes - sc.n_boxes;
                 V3<float> gp = zf3(), gax = zf3(), vp = zf3(), w = zf3();
@@ -384,10 +385,12 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                 }
                 bool on;
                 V3<float> nxt = prim_respond<float>(k, sc, R, x, vs[k], gp, gax, vp, w, on);
+                if (on) onmask |= 1u << k;
                 if (k + 1 < kMaxPlanes + kMaxBoxes + 2) vs[k + 1] = nxt;
             }
             V3<float> lx_acc = zf3();
             for (int k = nprim - 1; k >= 0; --k) {
+                if (!((onmask >> k) & 1u)) continue;
                 const int q = k - sc.n_planes - sc.n_boxes;
                 V3<float> gp = zf3(), gax = zf3(), vp = zf3(), w = zf3();
                 if (q >= 0) {
@@ -397,9 +400,6 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                     vp = idt * f3(act[6 * q], act[6 * q + 1], act[6 * q + 2]);
                     w = idt * f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
                 }
-                bool on;
-                prim_respond<float>(k, sc, R, x, vs[k], gp, gax, vp, w, on);
-                if (!on) continue;
                 V3<float> ntmp;
                 if (q >= 0 && sdf_capsule(x, gp - sc.grip_hl * gax, gp + sc.grip_hl * gax, sc.grip_r, ntmp) > -sc.grip_r) {
                     // capsule gripper: closed-form reverse (the degenerate on-axis case keeps dual numbers)
@@ -601,6 +601,8 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
     const size_t E2 = 5 * NV + 6, E3 = (size_t)(7 + 2 * kPairsPerVertex) * NV + (size_t)4 * P.scene.n_iter * NV;
     float4* L3 = L2 + (size_t)P.K * E2;
     const SceneDev& sc = P.scene;
+    if (CONTACT)   // the contact accumulators start at zero; every sweep leaves them at zero
+        for (int i = g.tid; i < NV; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
     for (;;) {
         const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (item >= P.n_order) break;

@@ -33,6 +33,8 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
     const int slot = threadIdx.x / TPR;
     Smem<NV, CONTACT> s(dyn_smem + slot * (rod_smem_bytes(NV, CONTACT) / 16));
     const Grp<TPR> g{(int)(threadIdx.x % TPR), 1 + slot, s.red};
+    if (CONTACT)   // the contact accumulators start at zero; every sweep leaves them at zero
+        for (int i = g.tid; i < NV; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
     for (;;) {
         const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (item >= P.n_order) break;

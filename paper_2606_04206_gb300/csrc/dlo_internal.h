@@ -19,7 +19,7 @@ struct RodInfo {
     int nsub, flags, ngrip, excl;
     float h, kA, Bm, beta;     // substep, K A, E A r^2 / 4, G A r^2 / 2
     float sy, rc, cd, radius;  // yield curvature, creep rate, damping, radius
-    float slim, contact_d, cell, eps;   // strain limit, candidate distance, hash cell, eps_s
+    float slim, contact_d, rsv, eps;    // strain limit, candidate distance, (reserved), eps_s
     int pair_cap, pair_off, pad0, pad1;
 };
 

@@ -221,12 +221,19 @@ DLO_HD T sdf_capsule(V3<T> x, V3<T> a, V3<T> b, float rc, V3<T>& n) {
     return d - rc;
 }
 
+constexpr float kContactReach = 2.31f;   // -ln(0.1) = 2.3026 plus a margin
+
 // Soft coupling (Sec. 3.2): d = r - SDF, f = min(exp(d / eps_s), 1); if f > 0.1 the relative
 // velocity's normal part gets restitution and its tangential part Coulomb friction, and the
 // result is blended in with weight f.
 template <class T>
 DLO_HD V3<T> contact_respond(V3<T> v, T sdf, V3<T> n, V3<T> vrig, float r, float eps_s,
                              float mu, float rest, bool& act) {
+    // f < exp(-2.31) < 0.099 there: the contact is inactive (decided without the exponential)
+    if (vof(sdf) > r + kContactReach * eps_s) {
+        act = false;
+        return v;
+    }
     T f = dexp((r - sdf) / eps_s);
     if (vof(f) > 1.f) f = cst<T>(1.f);
     act = vof(f) > 0.1f;

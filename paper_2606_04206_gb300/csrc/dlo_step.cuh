@@ -121,10 +121,6 @@ __device__ __forceinline__ int to_fix(float v, float scale) {
     return __float2int_rn(q);
 }
 
-__device__ __forceinline__ unsigned cell_hash(int ix, int iy, int iz, int mask) {
-    return ((unsigned)ix * 73856093u ^ (unsigned)iy * 19349663u ^ (unsigned)iz * 83492791u) & (unsigned)mask;
-}
-
 // Rigid contact of one vertex against the scene and the rod's grippers (Sec. 3.2).
 __device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const RodInfo& R, V3<float> x,
                                                     V3<float> v, const float* gp0, const M3* gR0,
@@ -145,6 +141,7 @@ __device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const Rod
         V3<float> ax = col(gR0[g], 2);
         V3<float> a = p - sc.grip_hl * ax, b = p + sc.grip_hl * ax, n;
         float sdf = sdf_capsule(x, a, b, sc.grip_r, n);
+        if (sdf > R.radius + kContactReach * R.eps) continue;
         const float inv_dt = 1.f / sc.dt;
         V3<float> vp = f3(act[6 * g] * inv_dt, act[6 * g + 1] * inv_dt, act[6 * g + 2] * inv_dt);
         V3<float> w = f3(act[6 * g + 3] * inv_dt, act[6 * g + 4] * inv_dt, act[6 * g + 5] * inv_dt);
@@ -181,92 +178,72 @@ struct Smem {
 };
 
 // ------------------------------------------------------------------ broad phase
-// Per-rod spatial hash of edge midpoints (cells of R.cell >= candidate distance + longest
-// edge, so the 27 neighbouring cells hold every candidate); candidates are the edge pairs
-// outside the exclusion window whose segments are closer than R.contact_d.
+// Candidates of one rod: the edge pairs outside the exclusion window whose segments are
+// closer than R.contact_d.  A rod has at most 256 edges, so every pair is tested: the edge
+// midpoints and half lengths sit in shared memory, every thread of the group walks all
+// edges in the same order (each read is one broadcast), a bounding-sphere test
+// (|m_a - m_b| < contact_d + h_a + h_b, implied by a segment distance below contact_d)
+// rejects almost all pairs before the exact closest-point distance, and the found pairs are
+// appended with one shared-memory atomic per warp.  Groups are whole warps and both loops
+// are uniform across the group, so the warp-wide ballot sees all 32 lanes.
 template <int NV, bool CONTACT, int TPR>
 __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, bool closed, bool& overflow) {
-    constexpr int TBL = NV <= 32 ? 64 : (NV <= 64 ? 128 : (NV <= 128 ? 256 : 512));
-    int* keys = reinterpret_cast<int*>(s.HB0);
-    int* cnt = keys + NV;          // TBL bucket counters + 1 pair counter
-    int* sorted = cnt + TBL + 1;
+    static_assert(TPR % 32 == 0, "rod groups are whole warps");
+    float4* mid = s.HB0;                          // midpoint, half length of each edge
+    int* cnt = reinterpret_cast<int*>(s.HB1);     // pairs found
     const int ne = R.ne, nv = R.nv;
-    const V3<float> org = f3(s.X[0]);
-    const float inv_cell = 1.f / R.cell;
-    for (int k = g.tid; k <= TBL; k += TPR) cnt[k] = 0;
-    g.sync();
     for (int j = g.tid; j < ne; j += TPR) {
-        int j1 = (j + 1 == nv) ? 0 : j + 1;
-        V3<float> m = 0.5f * (f3(s.X[j]) + f3(s.X[j1])) - org;
-        int ix = min(max(__float2int_rd(m.x * inv_cell), -510), 510) + 512;
-        int iy = min(max(__float2int_rd(m.y * inv_cell), -510), 510) + 512;
-        int iz = min(max(__float2int_rd(m.z * inv_cell), -510), 510) + 512;
-        keys[j] = (ix << 20) | (iy << 10) | iz;
-        atomicAdd(&cnt[cell_hash(ix, iy, iz, TBL - 1)], 1);
+        const int j1 = (j + 1 == nv) ? 0 : j + 1;
+        const V3<float> p0 = f3(s.X[j]), p1 = f3(s.X[j1]);
+        const V3<float> e = p1 - p0;
+        mid[j] = f4(0.5f * (p0 + p1), 0.5f * sqrtf(dot(e, e)));
     }
+    if (g.tid == 0) *cnt = 0;
     g.sync();
-    {   // exclusive scan of the bucket counts (TBL/TPR consecutive buckets per thread)
-        constexpr int PER = TBL / TPR;
-        int loc[PER];
-        int sum = 0;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            loc[k] = cnt[g.tid * PER + k];
-            sum += loc[k];
-        }
-        int run = grp_excl_scan<TPR>(sum, g);
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            cnt[g.tid * PER + k] = run;
-            run += loc[k];
-        }
-    }
-    g.sync();
-    for (int j = g.tid; j < ne; j += TPR) {
-        int key = keys[j];
-        int pos = atomicAdd(&cnt[cell_hash(key >> 20, (key >> 10) & 1023, key & 1023, TBL - 1)], 1);
-        sorted[pos] = j;
-    }
-    g.sync();
-    // after the scatter cnt[h] is the end of bucket h (and the start of bucket h + 1)
-    const int cap = R.pair_cap;
+    const int cap = R.pair_cap, lane = threadIdx.x & 31;
+    const float cd = R.contact_d;
     bool ovf = false;
-    for (int a = g.tid; a < ne; a += TPR) {
-        int key = keys[a];
-        int ix = key >> 20, iy = (key >> 10) & 1023, iz = key & 1023;
-        int a1 = (a + 1 == nv) ? 0 : a + 1;
-        V3<float> pa0 = f3(s.X[a]), pa1 = f3(s.X[a1]);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int cx = ix + dx, cy = iy + dy, cz = iz + dz;
-                    int nk = (cx << 20) | (cy << 10) | cz;
-                    unsigned hh = cell_hash(cx, cy, cz, TBL - 1);
-                    int beg = hh ? cnt[hh - 1] : 0, end = cnt[hh];
-                    for (int q = beg; q < end; ++q) {
-                        int b = sorted[q];
-                        if (b <= a || keys[b] != nk) continue;
-                        int sep = b - a;
-                        if (closed) sep = min(sep, ne - sep);
-                        if (sep <= R.excl) continue;
-                        int b1 = (b + 1 == nv) ? 0 : b + 1;
-                        V3<float> pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
-                        float su, uu;
-                        closest_params(pa0, pa1, pb0, pb1, su, uu);
-                        V3<float> dd = (pa0 + su * (pa1 - pa0)) - (pb0 + uu * (pb1 - pb0));
-                        float dist = sqrtf(dot(dd, dd));
-                        if (!(dist < R.contact_d)) continue;
-                        int idx = atomicAdd(&cnt[TBL], 1);
-                        if (idx < cap)
-                            s.pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
-                        else
-                            ovf = true;
-                    }
+    for (int a0 = 0; a0 < ne; a0 += TPR) {
+        const int a = a0 + g.tid;
+        const bool va = a < ne;
+        const float4 ma = va ? mid[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int a1 = (a + 1 == nv) ? 0 : a + 1;
+        for (int b = 0; b < ne; ++b) {
+            const float4 mb = mid[b];
+            bool hit = false;
+            if (va && b > a) {
+                const float dx = ma.x - mb.x, dy = ma.y - mb.y, dz = ma.z - mb.z;
+                const float rr = (cd + ma.w + mb.w) * 1.00001f;
+                int sep = b - a;
+                if (closed) sep = min(sep, ne - sep);
+                if (dx * dx + dy * dy + dz * dz < rr * rr && sep > R.excl) {
+                    const int b1 = (b + 1 == nv) ? 0 : b + 1;
+                    const V3<float> pa0 = f3(s.X[a]), pa1 = f3(s.X[a1]), pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
+                    float su, uu;
+                    closest_params(pa0, pa1, pb0, pb1, su, uu);
+                    const V3<float> dd = (pa0 + su * (pa1 - pa0)) - (pb0 + uu * (pb1 - pb0));
+                    hit = sqrtf(dot(dd, dd)) < cd;
                 }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(cnt, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (hit) {
+                    const int idx = base + __popc(m & ((1u << lane) - 1u));
+                    if (idx < cap)
+                        s.pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
+                    else
+                        ovf = true;
+                }
+            }
+        }
     }
     g.sync();
     overflow = grp_any<TPR>(ovf, g);
-    int np = cnt[TBL];
+    const int np = *cnt;
     g.sync();
     return min(np, cap);
 }
@@ -329,9 +306,7 @@ __device__ __forceinline__ void inext_color(const RodInfo& R, Smem<NV, CONTACT>&
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int np,
                                               bool first) {
-    const int nv = R.nv;
-    for (int i = g.tid; i < nv; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
-    g.sync();
+    const int nv = R.nv;   // s.acc is zero on entry and is left zero
     const float rsum = 2.f * R.radius;
     for (int p = g.tid; p < np; p += TPR) {
         uint32_t pr = s.pairs[p];
@@ -366,6 +341,7 @@ __device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT
             float4 x = s.X[i];
             const float inv = 1.f / kFixPos;
             s.X[i] = make_float4(x.x + q.x * inv, x.y + q.y * inv, x.z + q.z * inv, x.w);
+            s.acc[i] = make_int4(0, 0, 0, 0);
         }
     }
     g.sync();
@@ -374,9 +350,7 @@ __device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int np,
                                               float h, float mu) {
-    const int nv = R.nv;
-    for (int i = g.tid; i < nv; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
-    g.sync();
+    const int nv = R.nv;   // s.acc is zero on entry and is left zero
     for (int p = g.tid; p < np; p += TPR) {
         float4 F1 = s.fr1[p];
         if (!(F1.w > 0.f)) continue;
@@ -408,6 +382,7 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
             float4 v = s.V[i];
             const float inv = 1.f / kFixVel;
             s.V[i] = make_float4(v.x + q.x * inv, v.y + q.y * inv, v.z + q.z * inv, v.w);
+            s.acc[i] = make_int4(0, 0, 0, 0);
         }
     }
     g.sync();
