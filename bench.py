@@ -35,8 +35,8 @@ METRIC = "rod-vertex-steps/s fwd and fwd+bwd at B=4096, vs plain GPU step at sta
 UNIT = "rod-vertex-steps/s"
 # algorithmic FP32 operations per vertex-substep (tests/flop_count.cu counts them from the
 # kernels' own element templates; tests/test_flop_count.py keeps these in step)
-FLOPS_FWD_PER_VS = 921.3
-FLOPS_BWD_PER_VS = 3668.0
+FLOPS_FWD_PER_VS = 912.3
+FLOPS_BWD_PER_VS = 3650.0
 # DRAM bytes (read + write) of bwd_kernel per rod-frame of the 128-vertex self-contact
 # workload, from one ncu capture of a 304-rod x 50-frame case of it (its recompute scratch
 # grows with rod-frames; profiles/fwd_bwd_kernels_trajopt_304x128x50.md)
