@@ -47,6 +47,39 @@ __device__ __forceinline__ V3<float> jl_t(V3<float> phi, V3<float> lam) {
     return lam - A * c + B * cross(phi, c);
 }
 
+// The value part of a hinge evaluated on dual numbers (the float evaluation, up to rounding).
+__device__ __forceinline__ EdgeF<float> edge_vals(const EdgeF<dualf>& E) {
+    EdgeF<float> o;
+    o.t = vals(E.t);
+    o.w0 = vals(E.w0);
+    o.d1r = vals(E.d1r);
+    o.d2r = vals(E.d2r);
+    o.d1 = vals(E.d1);
+    o.d2 = vals(E.d2);
+    o.ell = E.ell.v;
+    o.n1 = E.n1.v;
+    o.c = E.c.v;
+    o.s = E.s.v;
+    return o;
+}
+
+__device__ __forceinline__ HingeF<float> hinge_vals(const HingeF<dualf>& H) {
+    HingeF<float> o;
+    o.a = edge_vals(H.a);
+    o.b = edge_vals(H.b);
+    o.X = vals(H.X);
+    o.kb = vals(H.kb);
+    o.u = vals(H.u);
+    o.cc = H.cc.v;
+    o.y = H.y.v;
+    o.xq = H.xq.v;
+    o.mref = H.mref.v;
+    o.m = H.m.v;
+    o.k0 = H.k0.v;
+    o.k1 = H.k1.v;
+    return o;
+}
+
 // One rigid primitive acting on a vertex velocity (the k-th of planes, boxes, grippers).
 template <class T>
 __device__ __forceinline__ V3<T> prim_respond(int k, const SceneDev& sc, const RodInfo& R, V3<T> x, V3<T> v,
@@ -143,12 +176,27 @@ struct PoseAdj {
         for (int k = 0; k < 6; ++k) ps0[k] = phs0[k] = ps1[k] = phs1[k] = vp[k] = w[k] = 0.f;
     }
 };
+// gripper q in {0, 1}; both halves are addressed with constant indices so that the per-thread
+// arrays stay in registers
 __device__ __forceinline__ void add3(float* a, int q, V3<float> v) {
-    a[3 * q] += v.x;
-    a[3 * q + 1] += v.y;
-    a[3 * q + 2] += v.z;
+    if (q == 0) {
+        a[0] += v.x;
+        a[1] += v.y;
+        a[2] += v.z;
+    } else {
+        a[3] += v.x;
+        a[4] += v.y;
+        a[5] += v.z;
+    }
 }
-__device__ __forceinline__ V3<float> get3(const float* a, int q) { return f3(a[3 * q], a[3 * q + 1], a[3 * q + 2]); }
+__device__ __forceinline__ V3<float> get3(const float* a, int q) {
+    return q == 0 ? f3(a[0], a[1], a[2]) : f3(a[3], a[4], a[5]);
+}
+// row-major 3x3 at o times v
+__device__ __forceinline__ V3<float> mul_rm(const float* o, V3<float> v) {
+    return f3(o[0] * v.x + o[1] * v.y + o[2] * v.z, o[3] * v.x + o[4] * v.y + o[5] * v.z,
+              o[6] * v.x + o[7] * v.y + o[8] * v.z);
+}
 
 // ------------------------------------------------------------------ reverse of one substep
 // On entry the shared state holds S_n (the substep's start), the recorded intermediates and,
@@ -158,8 +206,8 @@ __device__ __forceinline__ V3<float> get3(const float* a, int q) { return f3(a[3
 // pose cotangents and ga the frame's action cotangents (all per g.tid).
 template <int NV, bool CONTACT, int TPR>
 __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, CONTACT>& s,
-                                AdjArrays<NV, CONTACT>& a, const float4* SN, const float4* CS, const Grp<TPR>& g, float h, const Pose& F0,
-                                const float* act, const M3* gR0, const M3* gR1, float c0, float c1, int np,
+                                AdjArrays<NV, CONTACT>& a, const float4* SN, const float4* CS, const Grp<TPR>& g, float h,
+                                float c0, float c1, int np,
                                 double* gm, float* lpf, float* lphif, float* ga) {
     const SceneDev& sc = P.scene;
     const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
@@ -178,7 +226,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         float4 lx = a.LX[i];
         if (kind >= 2) {
             const int q = kind - 2;
-            V3<float> y1 = mul(gR1[q], f3(kin));
+            V3<float> y1 = mul_rm(s.sp + 32 * q + 15, f3(kin));
             add3(pa.ps1, q, f3(lx));
             add3(pa.phs1, q, cross(y1, f3(lx)));
             a.LX[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -371,17 +419,16 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             V3<float> vs[kMaxPlanes + kMaxBoxes + 2];
             vs[0] = f3(a.V1[i]);
             const V3<float> x = f3(x4);
-            const float idt = 1.f / sc.dt;
             unsigned onmask = 0;
             for (int k = 0; k < nprim; ++k) {
                 const int q = k - sc.n_planes - sc.n_boxes;
                 V3<float> gp = zf3(), gax = zf3(), vp = zf3(), w = zf3();
                 if (q >= 0) {
-                    gp = f3(F0.p[12 * q] + c0 * act[6 * q], F0.p[12 * q + 1] + c0 * act[6 * q + 1],
-                            F0.p[12 * q + 2] + c0 * act[6 * q + 2]);
-                    gax = col(gR0[q], 2);
-                    vp = idt * f3(act[6 * q], act[6 * q + 1], act[6 * q + 2]);
-                    w = idt * f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
+                    const float* o = s.sp + 32 * q;
+                    gp = f3(o[0], o[1], o[2]);
+                    gax = f3(o[8], o[11], o[14]);
+                    vp = f3(o[24], o[25], o[26]);
+                    w = f3(o[27], o[28], o[29]);
                 }
                 bool on;
                 V3<float> nxt = prim_respond<float>(k, sc, R, x, vs[k], gp, gax, vp, w, on);
@@ -394,17 +441,17 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                 const int q = k - sc.n_planes - sc.n_boxes;
                 V3<float> gp = zf3(), gax = zf3(), vp = zf3(), w = zf3();
                 if (q >= 0) {
-                    gp = f3(F0.p[12 * q] + c0 * act[6 * q], F0.p[12 * q + 1] + c0 * act[6 * q + 1],
-                            F0.p[12 * q + 2] + c0 * act[6 * q + 2]);
-                    gax = col(gR0[q], 2);
-                    vp = idt * f3(act[6 * q], act[6 * q + 1], act[6 * q + 2]);
-                    w = idt * f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
+                    const float* o = s.sp + 32 * q;
+                    gp = f3(o[0], o[1], o[2]);
+                    gax = f3(o[8], o[11], o[14]);
+                    vp = f3(o[24], o[25], o[26]);
+                    w = f3(o[27], o[28], o[29]);
                 }
                 V3<float> ntmp;
                 if (q >= 0 && sdf_capsule(x, gp - sc.grip_hl * gax, gp + sc.grip_hl * gax, sc.grip_r, ntmp) > -sc.grip_r) {
                     // capsule gripper: closed-form reverse (the degenerate on-axis case keeps dual numbers)
                     V3<float> lxk, lvk, lpk, lphik, lvpk, lwk;
-                    capsule_contact_rev(x, vs[k], gp, col(gR0[q], 2), sc.grip_hl, sc.grip_r, vp, w, R.radius, R.eps,
+                    capsule_contact_rev(x, vs[k], gp, gax, sc.grip_hl, sc.grip_r, vp, w, R.radius, R.eps,
                                         sc.mu_rigid, sc.restitution, lam, lxk, lvk, lpk, lphik, lvpk, lwk);
                     lx_acc += lxk;
                     lam = lvk;
@@ -457,7 +504,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             // d = target(pose at the substep end) - x0
             const int q = kind - 2;
             add3(pa.ps1, q, ld0);
-            add3(pa.phs1, q, cross(mul(gR1[q], f3(kin)), ld0));
+            add3(pa.phs1, q, cross(mul_rm(s.sp + 32 * q + 15, f3(kin)), ld0));
             a.LX[i] = f4(f3(a.LX[i]) - ld0, 0.f);
         }
         const bool has_e = closed || i < nv - 1;
@@ -506,18 +553,16 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         const int im = (i == 0) ? nv - 1 : i - 1, ip = (i + 1 == nv) ? 0 : i + 1;
         const float4 EDa = s.ED[ea], EDb = s.ED[eb], ETa = s.ET[ea], ETb = s.ET[eb], hg = s.HG[i];
         const float lbar = 0.5f * (ETa.w + ETb.w), il = 1.f / lbar;
-        HingeF<float> Hf;
-        hinge_forward(Hf, f3(s.X0[im]), f3(s.X0[i]), f3(s.X0[ip]), f3(ETa), f3(EDa), f3(ETb), f3(EDb), EDa.w, EDb.w,
-                      hg.w);
-        float kb0 = hg.x, kb1 = hg.y;
-        const bool plastic = R.flags & ROD_PLASTIC;
-        const bool yielded = plastic && plastic_update(Hf.k0, Hf.k1, kb0, kb1, R.sy * lbar, R.rc);
         // second order of the elastic force: tangents = cotangents of the gradient
         HingeF<dualf> Hd;
         const float4 gm_ = a.LG[im], gi_ = a.LG[i], gp_ = a.LG[ip];
         hinge_forward(Hd, lift(f3(s.X0[im]), f3(gm_)), lift(f3(s.X0[i]), f3(gi_)), lift(f3(s.X0[ip]), f3(gp_)),
                       lift(f3(ETa)), lift(f3(EDa)), lift(f3(ETb)), lift(f3(EDb)), mkd(EDa.w, a.LG[ea].w),
                       mkd(EDb.w, a.LG[eb].w), mkd(hg.w));
+        const HingeF<float> Hf = hinge_vals(Hd);   // the hinge itself (for plasticity)
+        float kb0 = hg.x, kb1 = hg.y;
+        const bool plastic = R.flags & ROD_PLASTIC;
+        const bool yielded = plastic && plastic_update(Hf.k0, Hf.k1, kb0, kb1, R.sy * lbar, R.rc);
         dualf e0d = Hd.k0 - kb0, e1d = Hd.k1 - kb1, emd = Hd.m - hg.z;
         dualf gk0 = (R.Bm * il) * e0d, gk1 = (R.Bm * il) * e1d, gmt = (R.beta * il) * emd;
         V3<dualf> gxm, gxi, gxp, gtba, gd1ba, gtbb, gd1bb;
@@ -566,7 +611,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
     // ---- pose cotangents of this substep -> frame-start pose and the frame's actions
     const float idt = 1.f / sc.dt;
     for (int q = 0; q < R.ngrip; ++q) {
-        const V3<float> dphi = f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
+        const V3<float> dphi = f3(s.act[6 * q + 3], s.act[6 * q + 4], s.act[6 * q + 5]);
         const V3<float> ps = get3(pa.ps0, q) + get3(pa.ps1, q);
         add3(lpf, q, ps);
         const V3<float> gdp = c0 * get3(pa.ps0, q) + c1 * get3(pa.ps1, q) + idt * get3(pa.vp, q);
@@ -645,32 +690,31 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                 }
                 g.sync();
             }
-            Pose F;
-            F.load(P.ck.GP + seg * P.ck_strideB + 24LL * rod);
+            if (g.tid < 24) s.fp[g.tid] = P.ck.GP[seg * P.ck_strideB + 24LL * rod + g.tid];
+            g.sync();
             // level 2: frame-start states of the segment
             for (int f = f0; f < f1; ++f) {
                 float4* e = L2 + (size_t)(f - f0) * E2;
                 save_state<NV, CONTACT, TPR>(e, R, g, s);
-                if (g.tid == 0)
-                    for (int k = 0; k < 24; ++k) reinterpret_cast<float*>(e + 5 * NV)[k] = F.p[k];
+                if (g.tid < 24) reinterpret_cast<float*>(e + 5 * NV)[g.tid] = s.fp[g.tid];
                 g.sync();
                 if (f + 1 == f1) break;   // the segment's last frame only needs its start state
-                const float* act = P.actions + ((size_t)f * P.B + rod) * 12;
-                float ac[12];
-#pragma unroll
-                for (int k = 0; k < 12; ++k) ac[k] = act[k];
-                run_frame<NV, CONTACT, TPR, false>(sc, P.KIN, P.ES, R, s, g, nsub, h, F, ac, ovf,
+                if (g.tid < 12) s.act[g.tid] = P.actions[((size_t)f * P.B + rod) * 12 + g.tid];
+                g.sync();
+                run_frame<NV, CONTACT, TPR, false>(sc, P.KIN, P.ES, R, s, g, nsub, h, ovf,
                                             [](int) -> const Rec* { return nullptr; });
             }
             for (int f = f1 - 1; f >= f0; --f) {
-                float ac[12];
-#pragma unroll
-                for (int k = 0; k < 12; ++k) ac[k] = P.actions[((size_t)f * P.B + rod) * 12 + k];
+                g.sync();   // the previous frame's reverse has finished reading s.act
+                if (g.tid < 12) s.act[g.tid] = P.actions[((size_t)f * P.B + rod) * 12 + g.tid];
+                g.sync();
                 // carry the pose cotangent of frame f+1's start into this frame's actions
 #pragma unroll
                 for (int k = 0; k < 12; ++k) ga[k] = 0.f;
-                for (int q = 0; q < R.ngrip; ++q) {
-                    const V3<float> dphi = f3(ac[6 * q + 3], ac[6 * q + 4], ac[6 * q + 5]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    if (q >= R.ngrip) break;
+                    const V3<float> dphi = f3(s.act[6 * q + 3], s.act[6 * q + 4], s.act[6 * q + 5]);
                     const V3<float> lp = get3(lpf, q), lr = get3(lphif, q);
                     ga[6 * q] = lp.x;
                     ga[6 * q + 1] = lp.y;
@@ -687,12 +731,15 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                 // level 3: substep-start states of this frame
                 const float4* e = L2 + (size_t)(f - f0) * E2;
                 load_state<NV, CONTACT, TPR>(e, R, g, s);
-                Pose F0;
-                F0.load(reinterpret_cast<const float*>(e + 5 * NV));
-                Pose Fw = F0;
+                if (g.tid < 24) {   // the frame's start pose: s.f0 for the reverse, s.fp to step from
+                    const float pv = reinterpret_cast<const float*>(e + 5 * NV)[g.tid];
+                    s.f0[g.tid] = pv;
+                    s.fp[g.tid] = pv;
+                }
+                g.sync();
                 Rec recs;
                 const int np = run_frame<NV, CONTACT, TPR, false>(
-                    sc, P.KIN, P.ES, R, s, g, nsub, h, Fw, ac, ovf, [&](int sb) -> const Rec* {
+                    sc, P.KIN, P.ES, R, s, g, nsub, h, ovf, [&](int sb) -> const Rec* {
                         float4* e3 = L3 + (size_t)sb * E3;
                         save_state<NV, CONTACT, TPR>(e3, R, g, s);
                         float4* sn = e3 + (7 + 2 * kPairsPerVertex) * NV;
@@ -703,11 +750,8 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                 g.sync();
                 for (int sb = nsub - 1; sb >= 0; --sb) {
                     const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
-                    M3 gR0[2], gR1[2];
-                    gR0[0] = F0.R[0];
-                    gR0[1] = F0.R[1];
-                    if (sb > 0) substep_rot(F0, ac, R.ngrip, c0, gR0);
-                    substep_rot(F0, ac, R.ngrip, c1, gR1);
+                    // the substep's gripper block (read after the barrier below)
+                    if (g.tid < R.ngrip) substep_pose(s.f0, s.act, g.tid, c0, c1, sb == 0, 1.f / sc.dt, s.sp);
                     // the substep's start state and recorded intermediates
                     const float4* e3 = L3 + (size_t)sb * E3;
                     load_state<NV, CONTACT, TPR>(e3, R, g, s);
@@ -722,11 +766,13 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                         }
                     g.sync();
                     const float4* sn = e3 + (7 + 2 * kPairsPerVertex) * NV;
-                    reverse_substep<NV, CONTACT, TPR>(P, R, s, a, sn, sn + (size_t)sc.n_iter * NV, g, h, F0, ac,
-                                                      gR0, gR1, c0, c1, np, gm, lpf, lphif, ga);
+                    reverse_substep<NV, CONTACT, TPR>(P, R, s, a, sn, sn + (size_t)sc.n_iter * NV, g, h, c0, c1, np,
+                                                      gm, lpf, lphif, ga);
                 }
                 if (P.gact) {
-                    for (int k = 0; k < 6 * R.ngrip; ++k) {
+#pragma unroll
+                    for (int k = 0; k < 12; ++k) {
+                        if (k >= 6 * R.ngrip) break;
                         const float v = (float)grp_sum<TPR>((double)ga[k], g);
                         if (g.tid == 0) P.gact[((size_t)f * P.B + rod) * 12 + k] = v;
                     }

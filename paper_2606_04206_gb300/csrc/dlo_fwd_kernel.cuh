@@ -53,9 +53,8 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
             s.ED[j] = P.S.ED[R.e0 + j];
             s.ET[j] = P.S.ET[R.e0 + j];
         }
-        // gripper poses of the frame start (every thread holds a copy)
-        Pose F;
-        F.load(P.S.GP + 24LL * rod);
+        // gripper poses of the frame start
+        if (g.tid < 24) s.fp[g.tid] = P.S.GP[24LL * rod + g.tid];
         g.sync();
         unsigned bad = 0;
         int np_max = 0;
@@ -64,14 +63,12 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
             if (P.ck_every > 0 && gf % P.ck_every == 0 && gf / P.ck_every < P.ck_count) {
                 const long long c = gf / P.ck_every;
                 write_state<TPR>(P.ck, c * P.ck_strideV, c * P.ck_strideE, c * P.ck_strideB, R, rod, g, s.X, s.V,
-                                 s.ED, s.ET, s.HG, F.p);
+                                 s.ED, s.ET, s.HG, s.fp);
             }
-            float act[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k)
-                act[k] = P.actions ? P.actions[((long long)f * P.B + rod) * 12 + k] : 0.f;
+            if (g.tid < 12) s.act[g.tid] = P.actions ? P.actions[((long long)f * P.B + rod) * 12 + g.tid] : 0.f;
+            g.sync();
             bool ovf = false;
-            const int np = run_frame<NV, CONTACT, TPR, true>(P.scene, P.KIN, P.ES, R, s, g, nsub, h, F, act, ovf,
+            const int np = run_frame<NV, CONTACT, TPR, true>(P.scene, P.KIN, P.ES, R, s, g, nsub, h, ovf,
                                                        [](int) -> const Rec* { return nullptr; });
             if (ovf) bad |= 2u;
             np_max = max(np_max, np);
@@ -97,7 +94,7 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
                 if (g.tid == 0) P.npairs[rod] = np_max;
             }
         }
-        write_state<TPR>(P.S, 0, 0, 0, R, rod, g, s.X, s.V, s.ED, s.ET, s.HG, F.p);
+        write_state<TPR>(P.S, 0, 0, 0, R, rod, g, s.X, s.V, s.ED, s.ET, s.HG, s.fp);
         if (g.tid == 0 && bad) atomicOr(&P.status[rod], bad);
         g.sync();
     }

@@ -38,7 +38,8 @@ int backward_occ_nv256(bool c, int warps);
 cudaError_t launch_backward(const BwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
 int backward_blocks_per_sm(int nv_max, bool contact, int warps);
 // Shared memory of one rod: its arrays plus a 256-byte header for group reductions.
-__host__ __device__ constexpr size_t rod_smem_bytes(int NV, bool contact) { return warp_smem_bytes(NV, contact) + 256; }
+// per rod: the arrays above, 256 B of group-reduction scratch and the 512 B gripper block
+__host__ __device__ constexpr size_t rod_smem_bytes(int NV, bool contact) { return warp_smem_bytes(NV, contact) + 768; }
 
 // Threads that step one rod of size class NV (one vertex per thread up to 128 vertices).
 __host__ __device__ constexpr int threads_per_rod(int NV) { return NV < 128 ? NV : 128; }

@@ -33,48 +33,24 @@ struct PlainWs {
     float4* FR0;      // [P] first-iteration contact normal, depth
     float4* FR1;      // [P] closest parameters, weight sum, active flag
     int4* ACC;        // [V] fixed-point accumulators (kept at zero between uses)
-    float* POSE;      // [B][2][24]: p0 (3), R0 (9), p1 (3), R1 (9) of each gripper
+    float* POSE;      // [B][64]: the substep gripper block of each rod (layout of Smem::sp)
     float* ZACT;      // [B][12] zero actions (frames stepped without actions)
     long long P;      // pair slots
 };
 
 __device__ __forceinline__ int nsub_of(const RodInfo& R, int force) { return force > 0 ? force : R.nsub; }
 
-__device__ __forceinline__ M3 load_m3(const float* p) {
-    M3 m;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) m.m[k] = p[k];
-    return m;
-}
-
-__device__ __forceinline__ void store_m3(float* p, const M3& m) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) p[k] = m.m[k];
-}
-
-// gripper poses at the start and the end of substep s (interpolated over the frame, Sec. 3.2)
-__global__ void pl_pose(const RodInfo* rods, int B, const float* GP, const float* act, int s, int force,
+// gripper block of substep s (positions, rotations and rigid velocities, Sec. 3.2)
+__global__ void pl_pose(SceneDev sc, const RodInfo* rods, int B, const float* GP, const float* act, int s, int force,
                         float* POSE) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const RodInfo R = rods[b];
     const int n = nsub_of(R, force);
     if (s >= n) return;
-    const float c0 = (float)s / (float)n, c1 = (float)(s + 1) / (float)n;
-    for (int q = 0; q < R.ngrip; ++q) {
-        const float* g = GP + 24LL * b + 12 * q;
-        const float* a = act + 12LL * b + 6 * q;
-        const M3 RF = load_m3(g + 3);
-        const M3 R0 = s == 0 ? RF : matmul(expmap(f3(c0 * a[3], c0 * a[4], c0 * a[5])), RF);
-        const M3 R1 = matmul(expmap(f3(c1 * a[3], c1 * a[4], c1 * a[5])), RF);
-        float* o = POSE + 48LL * b + 24 * q;
-        for (int c = 0; c < 3; ++c) {
-            o[c] = g[c] + c0 * a[c];
-            o[12 + c] = g[c] + c1 * a[c];
-        }
-        store_m3(o + 3, R0);
-        store_m3(o + 15, R1);
-    }
+    for (int q = 0; q < R.ngrip; ++q)
+        substep_pose(GP + 24LL * b, act + 12LL * b, q, (float)s / (float)n, (float)(s + 1) / (float)n, s == 0,
+                     1.f / sc.dt, POSE + 64LL * b);
 }
 
 // frame end: p += dp, R = exp(dphi) R
@@ -82,12 +58,7 @@ __global__ void pl_pose_advance(const RodInfo* rods, int B, float* GP, const flo
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     const RodInfo R = rods[b];
-    for (int q = 0; q < R.ngrip; ++q) {
-        float* g = GP + 24LL * b + 12 * q;
-        const float* a = act + 12LL * b + 6 * q;
-        store_m3(g + 3, matmul(expmap(f3(a[3], a[4], a[5])), load_m3(g + 3)));
-        for (int c = 0; c < 3; ++c) g[c] += a[c];
-    }
+    for (int q = 0; q < R.ngrip; ++q) frame_advance(GP + 24LL * b, act + 12LL * b, q);
 }
 
 // candidates of one frame: every edge pair of a rod outside the exclusion window whose
@@ -213,26 +184,21 @@ __global__ void pl_vertex(SceneDev sc, const RodInfo* rods, const int* vrod, lon
     const float4 vi = Vl[gv];
     const float4 kin = KIN[gv];
     const int kind = (int)kin.w;
-    const float* pose = POSE + 48LL * rod;
-    const float* a = act + 12LL * rod;
+    const float* pose = POSE + 64LL * rod;
     V3<float> v2 = zf3(), d = zf3();
     float4 tgt4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (kind == 0) {
         const V3<float> grav = f3(0.f, 0.f, -sc.gravity);
         const V3<float> acc = (-xi4.w) * g + grav - R.cd * f3(vi);
         const V3<float> v1 = f3(vi) + h * acc;
-        float gp0[6];
-        M3 gR0[2];
-        for (int q = 0; q < R.ngrip; ++q) {
-            for (int c = 0; c < 3; ++c) gp0[3 * q + c] = pose[24 * q + c];
-            gR0[q] = load_m3(pose + 24 * q + 3);
-        }
-        v2 = rigid_contact(sc, R, xi, v1, gp0, gR0, a);
+        v2 = rigid_contact(sc, R, xi, v1, pose);
         d = h * v2;
     } else if (kind >= 2) {
-        const int q = kind - 2;
-        const V3<float> p1 = f3(pose[24 * q + 12], pose[24 * q + 13], pose[24 * q + 14]);
-        const V3<float> tgt = p1 + mul(load_m3(pose + 24 * q + 15), f3(kin));
+        const float* o = pose + 32 * (kind - 2);
+        const V3<float> off = f3(kin);
+        const V3<float> tgt = f3(o[3], o[4], o[5]) + f3(o[15] * off.x + o[16] * off.y + o[17] * off.z,
+                                                        o[18] * off.x + o[19] * off.y + o[20] * off.z,
+                                                        o[21] * off.x + o[22] * off.y + o[23] * off.z);
         tgt4 = f4(tgt, 1.f);
         d = tgt - xi;
         v2 = d / h;
@@ -443,7 +409,7 @@ dlo_status plain_workspace(dlo_ctx* c, PlainWs& w) {
     const size_t o_vrod = take(4 * V), o_erod = take(4 * Et), o_prod = take(4 * Pn), o_poff = take(4 * B),
                  o_npair = take(4 * B), o_pairs = take(4 * Pn), o_D = take(16 * V), o_TGT = take(16 * V),
                  o_NDR = take(16 * Et), o_HB0 = take(16 * V), o_HB1 = take(16 * V), o_HB2 = take(16 * V),
-                 o_FR0 = take(16 * Pn), o_FR1 = take(16 * Pn), o_ACC = take(16 * V), o_POSE = take(4 * 48 * B),
+                 o_FR0 = take(16 * Pn), o_FR1 = take(16 * Pn), o_ACC = take(16 * V), o_POSE = take(4 * 64 * B),
                  o_ZACT = take(4 * 12 * B);
     if (off > c->pl_bytes) {
         dev_free(c, c->pl_mem);
@@ -475,7 +441,7 @@ dlo_status plain_workspace(dlo_ctx* c, PlainWs& w) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.prod, prod.data(), 4 * prod.size(), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.poff, poff.data(), 4 * B, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.ACC, 0, 16 * V, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.POSE, 0, 4 * 48 * B, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.POSE, 0, 4 * 64 * B, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.ZACT, 0, 4 * 12 * B, c->stream);
     // the host vectors die at return: finish the copies first
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -511,7 +477,7 @@ extern "C" dlo_status dlo_step_plain(dlo_ctx* c, const float* actions, int frame
             c->launches++;
         }
         for (int s = 0; s < nsub_max; ++s) {
-            pl_pose<<<blocks(B, T), T, 0, sm>>>(c->d_rods, B, c->S.GP, act, s, substeps, w.POSE);
+            pl_pose<<<blocks(B, T), T, 0, sm>>>(c->scene, c->d_rods, B, c->S.GP, act, s, substeps, w.POSE);
             pl_hinge<<<blocks(V, T), T, 0, sm>>>(c->d_rods, w.vrod, V, c->S.X, c->S.ED, c->S.ET, c->S.HG, w.HB0, w.HB1,
                                                  w.HB2, w.NDR, s, substeps);
             pl_vertex<<<blocks(V, T), T, 0, sm>>>(c->scene, c->d_rods, w.vrod, V, c->d_kin, c->d_es, c->S.X, c->S.Vl,

@@ -122,9 +122,9 @@ __device__ __forceinline__ int to_fix(float v, float scale) {
 }
 
 // Rigid contact of one vertex against the scene and the rod's grippers (Sec. 3.2).
+// sp: the substep's gripper block (see Smem).
 __device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const RodInfo& R, V3<float> x,
-                                                    V3<float> v, const float* gp0, const M3* gR0,
-                                                    const float* act) {
+                                                    V3<float> v, const float* sp) {
     bool on;
     for (int k = 0; k < sc.n_planes; ++k) {
         V3<float> n = f3(sc.planes[k]);
@@ -137,14 +137,14 @@ __device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const Rod
         v = contact_respond(v, sdf, n, zf3(), R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
     }
     for (int g = 0; g < R.ngrip; ++g) {
-        V3<float> p = f3(gp0[3 * g], gp0[3 * g + 1], gp0[3 * g + 2]);
-        V3<float> ax = col(gR0[g], 2);
+        const float* o = sp + 32 * g;
+        V3<float> p = f3(o[0], o[1], o[2]);
+        V3<float> ax = f3(o[8], o[11], o[14]);   // column 2 of R0: the capsule axis
         V3<float> a = p - sc.grip_hl * ax, b = p + sc.grip_hl * ax, n;
         float sdf = sdf_capsule(x, a, b, sc.grip_r, n);
         if (sdf > R.radius + kContactReach * R.eps) continue;
-        const float inv_dt = 1.f / sc.dt;
-        V3<float> vp = f3(act[6 * g] * inv_dt, act[6 * g + 1] * inv_dt, act[6 * g + 2] * inv_dt);
-        V3<float> w = f3(act[6 * g + 3] * inv_dt, act[6 * g + 4] * inv_dt, act[6 * g + 5] * inv_dt);
+        V3<float> vp = f3(o[24], o[25], o[26]);
+        V3<float> w = f3(o[27], o[28], o[29]);
         V3<float> vrig = vp + cross(w, x - p);
         v = contact_respond(v, sdf, n, vrig, R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
     }
@@ -158,8 +158,18 @@ struct Smem {
     int4* acc;
     uint32_t* pairs;
     float* red;
+    // gripper block (read by every thread of the rod with broadcasts):
+    //   fp  [24] pose at the start of the frame being stepped, per gripper p (3), R (9) row major
+    //   f0  [24] a second frame-start pose (the frame the backward reverses)
+    //   sp  [64] the current substep, per gripper (32): p0 (3), p1 (3), R0 (9), R1 (9), vp (3), w (3)
+    //   act [12] the frame's actions
+    float *fp, *f0, *sp, *act;
     __device__ Smem(float4* base) {
         red = reinterpret_cast<float*>(base + warp_smem_bytes(NV, CONTACT) / 16);
+        fp = red + 64;
+        f0 = fp + 24;
+        sp = f0 + 24;
+        act = sp + 64;
         X = base;
         X0 = base + NV;
         V = base + 2 * NV;
@@ -391,8 +401,7 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
 // ------------------------------------------------------------------ one substep
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
-                        const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, float h, const float* gpF,
-                        const M3* gR0, const M3* gR1, float c0, float c1, const float* act, int np,
+                        const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, float h, int np,
                         const Rec* rec = nullptr) {
     const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
     const bool closed = R.flags & ROD_CLOSED;
@@ -476,18 +485,15 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
             V3<float> acc = (-xi4.w) * g + grav - R.cd * f3(vi);
             V3<float> v1 = f3(vi) + h * acc;
             if (rec) rec->v1[i] = f4(v1, 0.f);
-            // pose at the substep start for the rigid contact
-            float gp0[6];
-            for (int q = 0; q < R.ngrip; ++q)
-                for (int c = 0; c < 3; ++c) gp0[3 * q + c] = gpF[12 * q + c] + c0 * act[6 * q + c];
-            v2 = rigid_contact(sc, R, xi, v1, gp0, gR0, act);
+            v2 = rigid_contact(sc, R, xi, v1, s.sp);
             d = h * v2;
         } else if (kind >= 2) {
-            const int q = kind - 2;
+            const float* o = s.sp + 32 * (kind - 2);
             const V3<float> off = f3(kin);
-            V3<float> p1 = f3(gpF[12 * q] + c1 * act[6 * q], gpF[12 * q + 1] + c1 * act[6 * q + 1],
-                              gpF[12 * q + 2] + c1 * act[6 * q + 2]);
-            const V3<float> tgt = p1 + mul(gR1[q], off);
+            const V3<float> p1 = f3(o[3], o[4], o[5]);
+            const V3<float> tgt = p1 + f3(o[15] * off.x + o[16] * off.y + o[17] * off.z,
+                                          o[18] * off.x + o[19] * off.y + o[20] * off.z,
+                                          o[21] * off.x + o[22] * off.y + o[23] * off.z);
             nd_out = f4(tgt, 1.f);      // absolute target at the substep end
             d = tgt - xi;               // a grasped vertex sits at the gripper target
             v2 = d / h;
@@ -562,64 +568,76 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
 template <int NV, bool CONTACT, int TPR>
 __device__ __noinline__ void substep_call(const SceneDev& sc, const float4* __restrict__ KIN,
                                           const float2* __restrict__ ES, const RodInfo& R, Smem<NV, CONTACT>& s,
-                                          const Grp<TPR>& g, float h, const float* gpF, const M3* gR0,
-                                          const M3* gR1, float c0, float c1, const float* act, int np,
-                                          const Rec* rec) {
-    substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, gpF, gR0, gR1, c0, c1, act, np, rec);
+                                          const Grp<TPR>& g, float h, int np, const Rec* rec) {
+    substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec);
 }
 
-// Gripper poses of a rod at the start of a frame (positions and rotations of both grippers).
-struct Pose {
-    float p[24];   // per gripper: position (3), rotation row major (9)
-    M3 R[2];
-    __device__ void load(const float* g) {
+// Substep pose block of gripper q (32 floats at out + 32 q) from the frame-start pose F
+// (per gripper p (3), R (9) row major) and the frame's actions: positions and rotations at
+// the substep's start (c0) and end (c1) of the frame, p + c dp and exp(c dphi) R (the start
+// rotation of the first substep is the frame's own), and the rigid velocities dp/dt, dphi/dt.
+__device__ __forceinline__ void substep_pose(const float* F, const float* act, int q, float c0, float c1, bool first,
+                                             float inv_dt, float* out) {
+    const float* f = F + 12 * q;
+    const float* a = act + 6 * q;
+    M3 RF;
 #pragma unroll
-        for (int k = 0; k < 24; ++k) p[k] = g[k];
+    for (int k = 0; k < 9; ++k) RF.m[k] = f[3 + k];
+    const M3 R0 = first ? RF : matmul(expmap(f3(c0 * a[3], c0 * a[4], c0 * a[5])), RF);
+    const M3 R1 = matmul(expmap(f3(c1 * a[3], c1 * a[4], c1 * a[5])), RF);
+    float* o = out + 32 * q;
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int k = 0; k < 9; ++k) R[q].m[k] = p[12 * q + 3 + k];
+    for (int c = 0; c < 3; ++c) {
+        o[c] = f[c] + c0 * a[c];
+        o[3 + c] = f[c] + c1 * a[c];
+        o[24 + c] = a[c] * inv_dt;
+        o[27 + c] = a[3 + c] * inv_dt;
     }
-    // frame end: p += dp, R = exp(dphi) R
-    __device__ void advance(const float* act, int ngrip) {
-        for (int q = 0; q < ngrip; ++q) {
-            R[q] = matmul(expmap(f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5])), R[q]);
-            for (int c = 0; c < 3; ++c) p[12 * q + c] += act[6 * q + c];
-            for (int k = 0; k < 9; ++k) p[12 * q + 3 + k] = R[q].m[k];
-        }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        o[6 + k] = R0.m[k];
+        o[15 + k] = R1.m[k];
     }
-};
-
-// Rotations of the grippers after substep sb+1 of nsub: exp(c1 dphi) R_frame.
-__device__ __forceinline__ void substep_rot(const Pose& F, const float* act, int ngrip, float c1, M3* out) {
-    for (int q = 0; q < ngrip; ++q)
-        out[q] = matmul(expmap(f3(c1 * act[6 * q + 3], c1 * act[6 * q + 4], c1 * act[6 * q + 5])), F.R[q]);
 }
 
-// One frame of one rod: candidates (if self-contact), nsub substeps, pose update.
-// pre(sb) runs before substep sb (after a group barrier), e.g. to store the substep state, and
-// returns the substep's record (or nullptr).
+// Frame end for gripper q: p += dp, R = exp(dphi) R.
+__device__ __forceinline__ void frame_advance(float* F, const float* act, int q) {
+    float* f = F + 12 * q;
+    const float* a = act + 6 * q;
+    M3 RF;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) RF.m[k] = f[3 + k];
+    const M3 Rn = matmul(expmap(f3(a[3], a[4], a[5])), RF);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[c] += a[c];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[3 + k] = Rn.m[k];
+}
+
+// One frame of one rod: candidates (if self-contact), nsub substeps, pose update.  The frame's
+// start pose is s.fp and its actions s.act, both set (and synchronised) by the caller; s.fp
+// holds the end pose on return.  pre(sb) runs before substep sb (after a group barrier), e.g.
+// to store the substep state, and returns the substep's record (or nullptr).
 template <int NV, bool CONTACT, int TPR, bool INLINE, class PreSub>
 __device__ __forceinline__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
-                         const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int nsub, float h, Pose& F,
-                         const float* act, bool& ovf, PreSub pre) {
+                         const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int nsub, float h, bool& ovf,
+                         PreSub pre) {
     int np = 0;
     if (CONTACT && (R.flags & ROD_SELF)) np = broad_phase<NV, CONTACT, TPR>(R, s, g, (R.flags & ROD_CLOSED) != 0, ovf);
-    M3 gR0[2], gR1[2];
-    gR0[0] = F.R[0];
-    gR0[1] = F.R[1];
+    const float inv_dt = 1.f / sc.dt;
     for (int sb = 0; sb < nsub; ++sb) {
         const Rec* rec = pre(sb);
-        const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
-        substep_rot(F, act, R.ngrip, c1, gR1);
+        // the substep's gripper block: written here, read after the hinge phase's barrier
+        if (g.tid < R.ngrip)
+            substep_pose(s.fp, s.act, g.tid, (float)sb / (float)nsub, (float)(sb + 1) / (float)nsub, sb == 0, inv_dt,
+                         s.sp);
         if (INLINE)
-            substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, F.p, gR0, gR1, c0, c1, act, np, rec);
+            substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec);
         else
-            substep_call<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, F.p, gR0, gR1, c0, c1, act, np, rec);
-        gR0[0] = gR1[0];
-        gR0[1] = gR1[1];
+            substep_call<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec);
     }
-    F.advance(act, R.ngrip);
+    if (g.tid < R.ngrip) frame_advance(s.fp, s.act, g.tid);
+    g.sync();
     return np;
 }
 
