@@ -38,6 +38,73 @@ static void* alloc_zero(dlo_ctx* c, size_t bytes, dlo_status& st) {
     return d;
 }
 
+// Forward launch of one size class over `frames` frames without actions or recording.
+static cudaError_t launch_bucket(dlo_ctx* c, size_t k, int warps, int grid, int frames) {
+    const Bucket& bk = c->buckets[k];
+    FwdParams P{};
+    P.rods = c->d_rods;
+    P.order = bk.d_order;
+    P.n_order = bk.n;
+    P.counter = c->d_counters + k;
+    P.S = c->S;
+    P.KIN = c->d_kin;
+    P.ES = c->d_es;
+    P.frames = frames;
+    P.B = c->B;
+    P.nvert_total = c->V;
+    P.status = c->d_status;
+    P.residual = c->d_residual;
+    P.npairs = c->d_npairs;
+    P.scene = c->scene;
+    cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = launch_forward(P, bk.nv_max, bk.contact, grid, warps, c->stream);
+    c->launches++;
+    return e;
+}
+
+// Rods per CTA by measurement (the autotuner): every count whose occupancy keeps at least
+// half of the most resident rods is timed on two frames from the rest state, after one
+// warm-up launch, and the fastest is kept.  The caller resets the state afterwards.
+static dlo_status autotune_rods_per_cta(dlo_ctx* c) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_err(c, cudaGetLastError(), "event");
+    }
+    dlo_status st = DLO_OK;
+    for (size_t k = 0; k < c->buckets.size() && st == DLO_OK; ++k) {
+        Bucket& bk = c->buckets[k];
+        int most = 0;
+        for (int rpc = 1; rpc <= 16; ++rpc) most = std::max(most, rpc * forward_blocks_per_sm(bk.nv_max, bk.contact, rpc));
+        float best_ms = 1e30f;
+        int best_w = bk.warps, best_g = bk.grid;
+        cudaError_t e = launch_bucket(c, k, bk.warps, bk.grid, 1);   // warm-up (module load, clocks)
+        for (int rpc = 1; rpc <= 16 && e == cudaSuccess; ++rpc) {
+            const int nb = forward_blocks_per_sm(bk.nv_max, bk.contact, rpc);
+            if (nb < 1 || 2 * rpc * nb < most) continue;
+            const int grid = (int)std::min<long long>((long long)nb * c->sm_count, (bk.n + rpc - 1) / rpc);
+            e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess) e = launch_bucket(c, k, rpc, grid, 2);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best_w = rpc;
+                best_g = grid;
+            }
+        }
+        if (e != cudaSuccess) st = cuda_err(c, e, "autotune");
+        bk.warps = best_w;
+        bk.grid = best_g;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const std::vector<float4>& kin,
                             const std::vector<float2>& mass, const std::vector<float2>& es,
                             const std::vector<float4>& rest, const std::vector<float>& gp0,
@@ -78,7 +145,8 @@ dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const 
         bk.n = (int)ids.size();
         bk.d_order = alloc_up(c, ids, st);
         if (st != DLO_OK) return st;
-        // rods per CTA: the count (within the thread budget) that keeps the most rods resident
+        // rods per CTA: the count (within the thread budget) that keeps the most rods resident;
+        // the measured autotune below may pick another
         int best = 0, best_nb = 0;
         for (int rpc = 1; rpc <= 16; ++rpc) {
             if (c->opt.warps_per_cta > 0 && rpc != c->opt.warps_per_cta) continue;
@@ -112,6 +180,18 @@ dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const 
     P.rest_mode = 0;
     st = cuda_err(c, launch_init(P, c->stream), "state init");
     c->launches += 2;
+    if (st == DLO_OK && c->opt.warps_per_cta == 0) {
+        // measured autotune of rods per CTA; then the rest state is set again (positions
+        // re-uploaded, frames, velocities and poses re-initialised, status cleared)
+        st = autotune_rods_per_cta(c);
+        if (st == DLO_OK)
+            st = cuda_err(c, cudaMemcpyAsync(c->S.X, xr4.data(), sizeof(float4) * xr4.size(), cudaMemcpyHostToDevice,
+                                             c->stream), "rest positions");
+        if (st == DLO_OK)
+            st = cuda_err(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned) * c->B, c->stream), "status reset");
+        if (st == DLO_OK) st = cuda_err(c, launch_init(P, c->stream), "state init");
+        c->launches++;
+    }
     c->from_set_state = true;
     if (st == DLO_OK) st = cuda_err(c, cudaStreamSynchronize(c->stream), "create");
     return st;

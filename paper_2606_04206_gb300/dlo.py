@@ -338,3 +338,51 @@ class DloSim:
             return o.value
         a = np.ctypeslib.as_array(o).copy()
         return a.reshape(self.V, 4) if what == Q_MASS else a
+
+    def material_tensor(self):
+        """The context's per-rod material as a [B, 5] tensor (K_stretch, E_bend, G_twist,
+        yield_curv, damping): the input whose gradient DloRollout returns."""
+        p = self.p
+        m = np.stack([np.asarray(getattr(p, k), np.float32) for k in ("K", "E", "G", "yield_curv", "damping")], 1)
+        return self.torch.as_tensor(m, device=self.device)
+
+
+def _rollout_function():
+    import torch
+
+    class DloRollout(torch.autograd.Function):
+        """A recorded rollout as a differentiable torch operation (Sec. 3.3).
+
+        forward(sim, x0 [V,4], v0 [V,4], theta0 [E], actions [F,B,2,6], material [B,5])
+        sets the state, records and steps F frames, and returns the final (x, v, theta).
+        ``material`` must hold the values the context was created with (see
+        DloSim.material_tensor); it is an input only so that its gradient can flow.
+        backward runs dlo_backward on the recorded rollout."""
+
+        @staticmethod
+        def forward(ctx, sim, x0, v0, theta0, actions, material):
+            frames = actions.shape[0]
+            sim.set_state(x0.contiguous(), v0.contiguous(), theta0.contiguous())
+            sim.begin_rollout(frames)
+            sim.step(actions.contiguous(), frames)
+            x, v, th = sim.get_state()
+            ctx.sim = sim
+            return x, v, th
+
+        @staticmethod
+        def backward(ctx, gx, gv, gth):
+            need = ctx.needs_input_grad
+            want = [k for k, n in zip(("x0", "v0", "theta0", "actions", "material"), need[1:]) if n]
+            g = ctx.sim.backward(None if gx is None else gx.contiguous(), None if gv is None else gv.contiguous(),
+                                 None if gth is None else gth.contiguous(), want=tuple(want))
+            return (None, g.get("x0"), g.get("v0"), g.get("theta0"), g.get("actions"), g.get("material"))
+
+    return DloRollout
+
+
+def rollout(sim, x0, v0, theta0, actions, material=None):
+    """Differentiable rollout through the library: final (x, v, theta) after actions.shape[0]
+    frames, with gradients with respect to every tensor input (DloRollout)."""
+    if material is None:
+        material = sim.material_tensor()
+    return _rollout_function().apply(sim, x0, v0, theta0, actions, material)
