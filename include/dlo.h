@@ -111,14 +111,23 @@ typedef struct {
 /* Create a context.  n_verts[B] >= 2 and <= 256, mat[B], x_rest [V][3] host: the rest shape
  * (rest lengths, masses and grasped vertices are taken from it; open rods rest straight,
  * loops rest as a planar circle of the same length).  The state is set to the rest shape
- * at rest.  cuda_stream may be NULL (legacy default stream).  alloc may be NULL. */
+ * at rest.  cuda_stream may be NULL (legacy default stream).  alloc may be NULL.
+ * Defined by: the rod discretisation, masses and reference frames of App. A.1, the
+ * kinematic grasp of Sec. 3.2, frame time and substeps of App. B.1.  With
+ * opt->warps_per_cta == 0 the rods-per-CTA setting is measured here (a few frames run from
+ * the rest state, which is then set again).
+ * Errors: DLO_ERR_INVALID_ARG for sizes, options or scene out of range (self-contact needs
+ * n_iter_pbd >= 1) or a zero-length rest edge; DLO_ERR_OOM / DLO_ERR_CUDA; *out is NULL on
+ * any error. */
 dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, const dlo_material* mat,
                       const float* x_rest, const dlo_scene* scene, const dlo_options* opt,
                       const dlo_allocator* alloc, void* cuda_stream);
 
 /* Set a fresh state (device x [V][4], v [V][4], theta [Etot]).  Reference frames are rebuilt
  * from x by space-parallel transport (loops: holonomy spread over the edges, App. A.1), rest
- * curvatures and gripper poses are reset to their create-time values. */
+ * curvatures and gripper poses are reset to their create-time values.  Ends any armed
+ * recording.  Defined by: the state variables and frame initialisation of App. A.1.
+ * Errors: DLO_ERR_INVALID_ARG for a NULL x or a pointer that is not 16-byte aligned. */
 dlo_status dlo_set_state(dlo_ctx* ctx, const float* x, const float* v, const float* theta);
 
 /* Copy the state into caller-owned device buffers (any may be NULL).  Synchronises the
@@ -132,26 +141,49 @@ dlo_status dlo_get_state(dlo_ctx* ctx, float* x, float* v, float* theta);
 dlo_status dlo_get_internal(dlo_ctx* ctx, float* ref, float* tan, float* hinge, float* grip);
 
 /* Arm recording of the next n_frames frames: checkpoints every K frames into the HBM ring
- * and a copy of the actions, so that dlo_backward can differentiate the rollout. */
+ * and a copy of the actions, so that dlo_backward can differentiate the rollout.  K is
+ * opt.checkpoint_every, or when that is 0 the shortest interval whose ring, action record
+ * and backward workspace fit opt.hbm_budget (80 GiB by default).
+ * Defined by: the gradient checkpointing of Sec. 3.3 (checkpoints kept in HBM here).
+ * Errors: DLO_ERR_INVALID_ARG for n_frames <= 0; DLO_ERR_OOM when the ring cannot be
+ * allocated. */
 dlo_status dlo_begin_rollout(dlo_ctx* ctx, int n_frames);
 
 /* Advance every rod by `frames` frames of dt with actions (device, [frames][B][2][6]; may be
  * NULL = no gripper motion).  substeps > 0 forces that many substeps per frame for every rod;
  * 0 uses each rod's own count (max(substeps_min, ceil(dt * omega_max))).  x_frames (device,
- * [frames][V][4]) optionally receives the positions after every frame (may be NULL). */
+ * [frames][V][4]) optionally receives the positions after every frame (may be NULL).
+ * One persistent launch per rod size class; only stream-ordered work, no synchronisation,
+ * so the call can be captured in a CUDA graph on the context's stream.
+ * Defined by: symplectic-Euler time stepping of the energies of Sec. 3.1 / App. A.1
+ * (stretching, bending, twisting), bending plasticity, the inextensibility and self-collision
+ * projections with friction (App. A.1), soft coupling to rigid primitives and grippers
+ * (Sec. 3.2), frame time and substeps of App. B.1.
+ * Errors: DLO_ERR_INVALID_ARG for negative frames or substeps or an unaligned x_frames;
+ * DLO_ERR_STATE when a recorded rollout would run past its armed frames or change its
+ * substeps.  Non-finite states and pair-list overflow are reported by the next
+ * synchronising call. */
 dlo_status dlo_step(dlo_ctx* ctx, const float* actions, int frames, int substeps, float* x_frames);
 
 /* The same rollout computed by the plain per-phase kernels (one launch per phase per
- * substep, state in HBM, one thread per element): the speed comparator. Same arguments. */
+ * substep, state in HBM, one thread per element): the speed comparator.  Same arguments and
+ * errors as dlo_step (without x_frames); it does not record, and it ends any armed
+ * recording.  Defined by: the same passages as dlo_step. */
 dlo_status dlo_step_plain(dlo_ctx* ctx, const float* actions, int frames, int substeps);
 
-/* Differentiate the recorded rollout.  Inputs (device, may be NULL = zero): dL/dx_T [V][4]
+/* Differentiate the recorded rollout (the gradient through time of Sec. 3.3, computed by a
+ * hand-written adjoint that replays each frame from its checkpoint).  Inputs (device, may be
+ * NULL = zero): dL/dx_T [V][4]
  * (w ignored), dL/dv_T [V][4] (w = dL/d twist rate), dL/dtheta_T [Etot].  Outputs (device,
  * may be NULL = not wanted): dL/dactions [F][B][2][6], dL/dmaterial [B][5] for
  * (K_stretch, E_bend, G_twist, yield_curv, damping), dL/dx0 [V][4], dL/dv0 [V][4],
  * dL/dtheta0 [Etot].  Gradients are with respect to the state set by dlo_set_state when the
  * rollout started from it (reference frames rebuilt from x0), else with respect to the state
- * at dlo_begin_rollout holding its reference frames fixed.  Synchronises. */
+ * at dlo_begin_rollout holding its reference frames fixed.  Synchronises.
+ * Errors: DLO_ERR_STATE without a completed recorded rollout; DLO_ERR_INVALID_ARG for
+ * unaligned float4 arrays or self-contact with no projection iteration; DLO_ERR_OOM when
+ * the workspace cannot be allocated; DLO_ERR_NONFINITE / DLO_ERR_CAPACITY as recorded by the
+ * rollout. */
 dlo_status dlo_backward(dlo_ctx* ctx, const float* dL_dx_T, const float* dL_dv_T,
                         const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
                         float* dL_dx0, float* dL_dv0, float* dL_dtheta0);
