@@ -84,3 +84,13 @@ def grad_agreement(a, b):
     rel = np.linalg.norm(a - b) / nb
     cos = float(a @ b / (np.linalg.norm(a) * nb + 1e-300))
     return rel, cos
+
+
+def rod_state(st, prob, b):
+    """One rod's slice of a full device state (as returned by DloSim.full_state_numpy), in the
+    layout OracleSim.set_full_state expects for prob.subset([b])."""
+    vo, eo = prob.vert_off, prob.edge_off
+    v0, v1, e0, e1 = vo[b], vo[b + 1], eo[b], eo[b + 1]
+    return dict(x=st["x"][v0:v1], v=st["v"][v0:v1], theta=st["theta"][e0:e1], omega=st["omega"][e0:e1],
+                d1b=st["d1b"][e0:e1], tb=st["tb"][e0:e1], kbar=st["kbar"][v0:v1], mprev=st["mprev"][v0:v1],
+                mbar=st["mbar"][v0:v1], gp=st["gp"][b:b + 1], gR=st["gR"][b:b + 1])
