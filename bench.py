@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--frames", type=int, default=2000)
-    ap.add_argument("--rods", type=int, default=4096)
-    ap.add_argument("--verts", type=int, default=128)
+    ap.add_argument("--workload", default="trajopt", choices=["trajopt", "batching", "selfcontact", "diff"],
+                    help="trajopt is the headline line; the others measure the other configurations")
+    ap.add_argument("--frames", type=int, default=None)
+    ap.add_argument("--rods", type=int, default=None)
+    ap.add_argument("--verts", type=int, default=None)
     ap.add_argument("--no-self-contact", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -147,7 +149,7 @@ def oracle_rollout_rate(prob, frames, rods):
     sim.set_state(x0, torch.tensor(sub.v0), torch.tensor(sub.theta0), torch.tensor(sub.omega0))
     sim.step(act, frames, diff=True)
     x = sim.get_state(as_numpy=False)["x"]
-    L = ((x - torch.tensor(sub.target)) ** 2).sum(1).mean()
+    L = ((x - torch.tensor(sub.target)) ** 2).sum(1).mean() if sub.target is not None else x[:, 2].mean()
     torch.autograd.grad(L, [act, x0])
     dt = time.perf_counter() - t0
     units = float(np.sum(sub.n_verts)) * frames
@@ -157,9 +159,11 @@ def oracle_rollout_rate(prob, frames, rods):
 def run_reference(args, rank, ws):
     if rank != 0:
         return
+    import copy
     import torch
-    from paper_2606_04206_gb300 import inputs
-    prob = inputs.trajopt(n_rods=4, frames=4, n=args.verts, self_contact=not args.no_self_contact)
+    short = copy.copy(args)
+    short.frames = 4                       # the oracle samples two frames per step
+    prob, desc, R, _ = make_workload(short, 0)
     rates = []
     for i in range(args.warmup + args.steps):
         r, dt = oracle_rollout_rate(prob, 2, [0, 1])
@@ -168,18 +172,47 @@ def run_reference(args, rank, ws):
     value = sum(r for r, _ in rates) / len(rates)
     ms = 1e3 * sum(dt for _, dt in rates) / len(rates)
     cores = torch.get_num_threads()
-    sample = f"2 rods x {args.verts} vertices x 2 frames (5 substeps) per step, FP64 forward + autograd backward"
+    sample = (f"rods 0 and 1 ({int(prob.n_verts[0])} and {int(prob.n_verts[1])} vertices) x 2 frames per step, "
+              f"FP64 forward + autograd backward")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"trajopt {args.rods} rods x {args.verts} vertices (oracle sample)",
-                       "frames_per_step": 2},
+            "config": {"workload": desc + " (oracle sample)", "frames_per_step": 2},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- native arm
+# rods, vertices per rod, frames of each workload (the configurations' own sizes)
+WORKLOADS = {"trajopt": (4096, 128, 2000), "batching": (1024, None, 1000), "selfcontact": (4096, 200, 300),
+             "diff": (256, 64, 500)}
+
+
+def make_workload(args, rank):
+    from paper_2606_04206_gb300 import inputs
+    R0, N0, F0 = WORKLOADS[args.workload]
+    R = args.rods or R0
+    N = args.verts or N0
+    F = args.frames or F0
+    w = args.workload
+    if w == "trajopt":
+        prob = inputs.trajopt(n_rods=R, frames=F, seed=4000 + rank, n=N, self_contact=not args.no_self_contact)
+        desc = (f"trajopt: {R} rods x {N} vertices per GPU, {F} frames (dt 1e-3 s, 5 substeps), cable/rope/wire "
+                f"thirds, 2 grippers, ground, self-contact={'on' if not args.no_self_contact else 'off'}")
+    elif w == "batching":
+        prob = inputs.batching(n_rods=R, frames=F, seed=1000 + rank)
+        desc = (f"batching: {R} rods x 16..256 vertices, 0.3..2 m, E 1e4..1e8 Pa, plastic, 2 grippers, ground, "
+                f"{F} frames, per-rod substeps")
+    elif w == "selfcontact":
+        prob = inputs.selfcontact(n_rods=R, frames=F, seed=3000 + rank, n=N)
+        desc = f"selfcontact: {R} knotted closed bands x {N} vertices, ground + box, self-contact, {F} frames"
+    else:
+        prob = inputs.diff(n_rods=R, frames=F, seed=2000 + rank, n=N)
+        desc = f"diff: {R} rods x {N} vertices, rope/plastic wire halves, 2 grippers, ground, {F} frames"
+    return prob, desc, R, F
+
+
 def run_native(args, rank, ws):
     import numpy as np
     import torch
@@ -187,21 +220,30 @@ def run_native(args, rank, ws):
 
     build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
-    F, R, N = args.frames, args.rods, args.verts
-    prob = inputs.trajopt(n_rods=R, frames=F, seed=4000 + rank, n=N, self_contact=not args.no_self_contact)
+    prob, desc, R, F = make_workload(args, rank)
     sim = dlo.DloSim(prob)
     V = sim.V
-    units = float(R) * N * F
+    N = int(np.max(prob.n_verts))
+    units = float(np.sum(prob.n_verts)) * F
     acts = torch.as_tensor(np.ascontiguousarray(prob.actions, np.float32), device=dev)
     target = torch.zeros(V, 4, device=dev)
-    target[:, :3] = torch.as_tensor(prob.target, dtype=torch.float32, device=dev)
+    if prob.target is not None:
+        target[:, :3] = torch.as_tensor(prob.target, dtype=torch.float32, device=dev)
     x0, v0, th0 = sim.tensors_from_problem()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     stream = torch.cuda.current_stream()
+    mean_z = torch.zeros(V, 4, device=dev)
+    mean_z[:, 2] = 1.0 / V
+
+    def loss_grad(x):
+        """dL/dx_T: mean squared distance to the target curve, or the mean height without one."""
+        if prob.target is not None:
+            return (2.0 / V) * (x - target)
+        return mean_z
 
     def dL_dx():
         x, _, _ = sim.get_state()
-        return (2.0 / V) * (x - target)
+        return loss_grad(x)
 
     def one_step(record):
         flush.fill_(1.0)
@@ -262,8 +304,9 @@ def run_native(args, rank, ws):
         sim.begin_rollout(F)
         sim.step(d_acts, F)
         x, _, _ = sim.get_state()
-        loss = ((x - tg)[:, :3] ** 2).sum(1).mean()
-        g = sim.backward(dL_dx=(2.0 / V) * (x - tg), want=("actions", "material", "x0"))
+        loss = ((x - tg)[:, :3] ** 2).sum(1).mean() if prob.target is not None else x[:, 2].mean()
+        g = sim.backward(dL_dx=(2.0 / V) * (x - tg) if prob.target is not None else mean_z,
+                         want=("actions", "material", "x0"))
         h_gact.copy_(g["actions"], non_blocking=True)
         h_loss.copy_(loss.reshape(1), non_blocking=True)
         e1.record(stream)
@@ -277,13 +320,15 @@ def run_native(args, rank, ws):
     d2h = h_gact.numel() * 4 + 4
 
     # roofline of the dominant kernel (the backward): algorithmic FP32 operations per launch
-    nsub = int(np.max(sim.query(dlo.Q_SUBSTEPS)))
-    vs_units = float(R) * N * F * nsub
+    nsub_rod = np.asarray(sim.query(dlo.Q_SUBSTEPS), np.float64)
+    nsub = int(np.max(nsub_rod))
+    vs_units = float(F) * float(np.sum(np.asarray(prob.n_verts, np.float64) * nsub_rod))
     max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
     peak_tflops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
     bwd_tflops = FLOPS_BWD_PER_VS * vs_units / (ms_bwd / 1e3) / 1e12
     fwd_tflops = FLOPS_FWD_PER_VS * vs_units / (ms_fwd / 1e3) / 1e12
-    traffic = BWD_DRAM_BYTES_PER_ROD_FRAME * R * F if (N == 128 and not args.no_self_contact) else None
+    traffic = (BWD_DRAM_BYTES_PER_ROD_FRAME * R * F
+               if (args.workload == "trajopt" and N == 128 and not args.no_self_contact) else None)
     roofline = {"bound": "alu", "kernel": "bwd_kernel (dlo_backward)", "achieved": bwd_tflops,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": bwd_tflops / peak_tflops, "traffic": traffic,
                 "peak_basis": f"FP32 CUDA cores: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
@@ -304,7 +349,7 @@ def run_native(args, rank, ws):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_p = e0.elapsed_time(e1)
-        pv = float(R) * N * pf / (ms_p / 1e3)
+        pv = float(np.sum(prob.n_verts)) * pf / (ms_p / 1e3)
         plain = {"fwd_value": pv, "unit": UNIT, "frames": pf, "speedup_fwd": fwd_value / ws / pv}
     except Exception as exc:   # the comparator is optional for the line; say why it is missing
         plain = {"unavailable": str(exc)[:200]}
@@ -323,9 +368,7 @@ def run_native(args, rank, ws):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"trajopt: {R} rods x {N} vertices per GPU, {F} frames (dt 1e-3 s, "
-                                       f"{nsub} substeps), cable/rope/wire thirds, 2 grippers, ground, "
-                                       f"self-contact={'on' if not args.no_self_contact else 'off'}",
+                "config": {"workload": desc,
                            "rods_per_gpu": R, "verts_per_rod": N, "frames": F, "substeps": nsub,
                            "n_iter_pbd": 10, "checkpoint_every": int(sim.query(dlo.Q_CONFIG)[1]),
                            "l2": "256 MiB buffer written before every timed step"},
