@@ -122,6 +122,8 @@ cudaError_t launch_backward(const BwdParams& P, int nv, bool c, int grid, int wa
         case 32: return launch_backward_nv32(P, c, grid, warps, st);
         case 64: return launch_backward_nv64(P, c, grid, warps, st);
         case 128: return launch_backward_nv128(P, c, grid, warps, st);
+        case 192: return launch_backward_nv192(P, c, grid, warps, st);
+        case 224: return launch_backward_nv224(P, c, grid, warps, st);
         case 256: return launch_backward_nv256(P, c, grid, warps, st);
     }
     return cudaErrorInvalidValue;
@@ -138,6 +140,8 @@ int backward_blocks_per_sm(int nv, bool c, int warps) {
         case 32: return backward_occ_nv32(c, warps);
         case 64: return backward_occ_nv64(c, warps);
         case 128: return backward_occ_nv128(c, warps);
+        case 192: return backward_occ_nv192(c, warps);
+        case 224: return backward_occ_nv224(c, warps);
         case 256: return backward_occ_nv256(c, warps);
     }
     return 0;
@@ -154,6 +158,7 @@ using namespace dlo;
 dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out) {
     const size_t nb_ = c->buckets.size();
     out.slot_b.assign(nb_, 0);
+    out.offset.assign(nb_, 0);
     out.warps.assign(nb_, 0);
     out.grid.assign(nb_, 0);
     out.nsmax.assign(nb_, 0);
@@ -172,7 +177,7 @@ dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out) {
         int ns = force;
         if (!ns)
             for (int b = 0; b < c->B; ++b)
-                if (((c->rods_h[b].nv <= 32) ? 32 : (c->rods_h[b].nv <= 64) ? 64 : (c->rods_h[b].nv <= 128) ? 128 : 256) == bk.nv_max)
+                if (size_class(c->rods_h[b].nv) == bk.nv_max)
                     ns = std::max(ns, c->nsub[b]);
         out.nsmax[k] = ns;
         const size_t NV = bk.nv_max;
@@ -180,7 +185,9 @@ dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out) {
                               (size_t)ns * ((7 + 2 * kPairsPerVertex) * NV + (size_t)4 * c->opt.n_iter_pbd * NV));
         out.warps[k] = w;
         out.grid[k] = (int)std::min<long long>((long long)nb * c->sm_count, (bk.n + w - 1) / w);
-        need = std::max(need, out.slot_b[k] * (size_t)out.grid[k] * w);
+        // each class has its own region: the classes run concurrently on their streams
+        out.offset[k] = need;
+        need += (out.slot_b[k] * (size_t)out.grid[k] * w + 255) & ~(size_t)255;
     }
     out.bytes = need + 2 * 16 * (size_t)c->Et + 4 * sizeof(V3<double>) * (size_t)c->V + 1024;
     return DLO_OK;
@@ -203,6 +210,7 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
     const size_t need = plan.bytes;
     const std::vector<size_t>& slot_b = plan.slot_b;
     const std::vector<int>&warps = plan.warps, &grid = plan.grid, &nsmax = plan.nsmax;
+    const std::vector<size_t>& offset = plan.offset;
     if (need > c->bw_bytes) {
         dev_free(c, c->bw_mem);
         c->bw_mem = dev_alloc(c, need);
@@ -215,13 +223,17 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
     V3<double>* work = reinterpret_cast<V3<double>*>(gd1b0 + c->Et);
     char* scratch = reinterpret_cast<char*>(work + 4 * (size_t)c->V);
     scratch = reinterpret_cast<char*>(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+    {
+        cudaError_t fe = fork_classes(c);
+        if (fe != cudaSuccess) return cuda_err(c, fe, "fork");
+    }
     for (size_t k = 0; k < c->buckets.size(); ++k) {
         const Bucket& bk = c->buckets[k];
         BwdParams P{};
         P.rods = c->d_rods;
         P.order = bk.d_order;
         P.n_order = bk.n;
-        P.counter = c->d_counters + 4 + k;
+        P.counter = c->d_counters + kNumSizeClasses + k;
         P.ck = c->ck;
         P.ck_strideV = c->V;
         P.ck_strideE = c->Et;
@@ -244,15 +256,20 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
         P.gth0 = dL_dtheta0;
         P.gtb0 = gtb0;
         P.gd1b0 = gd1b0;
-        P.scratch = scratch;
+        P.scratch = scratch + offset[k];
         P.slot_bytes = slot_b[k];
         P.K = c->ck_every;
         P.nsub_max = nsmax[k];
         P.scene = c->scene;
-        cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), c->stream);
-        if (e == cudaSuccess) e = launch_backward(P, bk.nv_max, bk.contact, grid[k], warps[k], c->stream);
+        cudaStream_t sk = class_stream(c, k);
+        cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), sk);
+        if (e == cudaSuccess) e = launch_backward(P, bk.nv_max, bk.contact, grid[k], warps[k], sk);
         c->launches++;
         if (e != cudaSuccess) return cuda_err(c, e, "backward launch");
+    }
+    {
+        cudaError_t je = join_classes(c);
+        if (je != cudaSuccess) return cuda_err(c, je, "join");
     }
     if (c->rec_from_set && dL_dx0) {
         frames_adjoint_kernel<<<(c->B + 127) / 128, 128, 0, c->stream>>>(c->d_rods, c->B, c->ck.X, gtb0, gd1b0,

@@ -61,7 +61,6 @@ void dev_free(dlo_ctx* c, void* p) {
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-static int nv_bucket(int nv) { return nv <= 32 ? 32 : nv <= 64 ? 64 : nv <= 128 ? 128 : 256; }
 
 // Per-rod substep count: n = max(n_min, ceil(dt * omega_max)), omega_max the largest of the
 // stretching 2 sqrt(K/rho)/l, bending 2 r sqrt(E/rho)/l^2 and twisting 2 sqrt(G/rho)/l
@@ -246,7 +245,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         R.slim = (!inext && m.strain_limit > 0.f) ? m.strain_limit : 0.f;
         R.contact_d = (float)(2.0 * r + opt->contact_margin * r);
         R.eps = (float)(opt->eps_soft * r);
-        R.pair_cap = kPairsPerVertex * nv_bucket(nv);
+        R.pair_cap = kPairsPerVertex * size_class(nv);
         R.pair_off = 0;
     }
     c->rods_h = rods;
@@ -292,7 +291,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
 
 extern "C" void dlo_destroy(dlo_ctx* c) {
     if (!c) return;
-    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
     runtime_release(c);
     std::vector<void*> all = c->allocs;
     for (void* p : all) dev_free(c, p);

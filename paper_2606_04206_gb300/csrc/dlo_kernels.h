@@ -31,6 +31,14 @@ cudaError_t launch_forward_nv128(const FwdParams& P, bool c, int grid, int warps
 int forward_occ_nv128(bool c, int warps);
 cudaError_t launch_backward_nv128(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int backward_occ_nv128(bool c, int warps);
+cudaError_t launch_forward_nv192(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int forward_occ_nv192(bool c, int warps);
+cudaError_t launch_backward_nv192(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int backward_occ_nv192(bool c, int warps);
+cudaError_t launch_forward_nv224(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int forward_occ_nv224(bool c, int warps);
+cudaError_t launch_backward_nv224(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int backward_occ_nv224(bool c, int warps);
 cudaError_t launch_forward_nv256(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int forward_occ_nv256(bool c, int warps);
 cudaError_t launch_backward_nv256(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
@@ -40,6 +48,17 @@ int backward_blocks_per_sm(int nv_max, bool contact, int warps);
 // Shared memory of one rod: its arrays plus a 256-byte header for group reductions.
 // per rod: the arrays above, 256 B of group-reduction scratch and the 512 B gripper block
 __host__ __device__ constexpr size_t rod_smem_bytes(int NV, bool contact) { return warp_smem_bytes(NV, contact) + 768; }
+
+// Rod size classes: a rod of nv vertices runs in the kernels instantiated for the smallest
+// class that holds it (shared memory is sized per class; 192 and 224 let two rods of up to
+// 224 vertices share an SM in the backward, where a 256-vertex rod needs 124 KB).
+constexpr int kNumSizeClasses = 6;
+__host__ __device__ constexpr int size_class_at(int k) {
+    return k == 0 ? 32 : k == 1 ? 64 : k == 2 ? 128 : k == 3 ? 192 : k == 4 ? 224 : 256;
+}
+__host__ __device__ constexpr int size_class(int nv) {
+    return nv <= 32 ? 32 : nv <= 64 ? 64 : nv <= 128 ? 128 : nv <= 192 ? 192 : nv <= 224 ? 224 : 256;
+}
 
 // Threads that step one rod of size class NV (one vertex per thread up to 128 vertices).
 __host__ __device__ constexpr int threads_per_rod(int NV) { return NV < 128 ? NV : 128; }

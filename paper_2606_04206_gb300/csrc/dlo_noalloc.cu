@@ -69,7 +69,6 @@ static dlo_status check_status_noalloc(dlo_ctx* c) {
     return DLO_OK;
 }
 
-static int class_of(int nv) { return nv <= 32 ? 32 : nv <= 64 ? 64 : nv <= 128 ? 128 : 256; }
 
 extern "C" dlo_status dlo_backward_noalloc(dlo_ctx* c, const float* dL_dx_T, const float* dL_dv_T,
                                            const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
@@ -81,7 +80,7 @@ extern "C" dlo_status dlo_backward_noalloc(dlo_ctx* c, const float* dL_dx_T, con
         if (p && ((uintptr_t)p & 15u)) return set_err(c, DLO_ERR_INVALID_ARG, "float4 arrays must be 16-byte aligned");
     if (c->opt.self_contact && c->opt.n_iter_pbd < 1)
         return set_err(c, DLO_ERR_INVALID_ARG, "self-contact gradients need at least one projection iteration");
-    if (c->buckets.size() > 4) return set_err(c, DLO_ERR_INVALID_ARG, "more size classes than expected");
+    if (c->buckets.size() > (size_t)kNumSizeClasses) return set_err(c, DLO_ERR_INVALID_ARG, "more size classes than expected");
     char* base = nullptr;
     dlo_status st = scratch_address(c, &base);
     if (st != DLO_OK) return st;
@@ -92,8 +91,8 @@ extern "C" dlo_status dlo_backward_noalloc(dlo_ctx* c, const float* dL_dx_T, con
     const size_t fixed_raw = 2 * 16 * (size_t)c->Et + (frames_adj ? 4 * sizeof(V3<double>) * (size_t)c->V : 0);
     const size_t fixed = (fixed_raw + 255) & ~(size_t)255;
     const int force = c->rec_nsub > 0 ? c->rec_nsub : 0;
-    size_t slot_b[4];
-    int warps[4], grid[4], nsmax[4];
+    size_t slot_b[kNumSizeClasses];
+    int warps[kNumSizeClasses], grid[kNumSizeClasses], nsmax[kNumSizeClasses];
     for (size_t k = 0; k < c->buckets.size(); ++k) {
         const Bucket& bk = c->buckets[k];
         int w = 0, nb = 0;
@@ -108,7 +107,7 @@ extern "C" dlo_status dlo_backward_noalloc(dlo_ctx* c, const float* dL_dx_T, con
         int ns = force;
         if (!ns)
             for (int b = 0; b < c->B; ++b)
-                if (class_of(c->rods_h[b].nv) == bk.nv_max) ns = std::max(ns, c->nsub[b]);
+                if (size_class(c->rods_h[b].nv) == bk.nv_max) ns = std::max(ns, c->nsub[b]);
         nsmax[k] = ns;
         const size_t NV = bk.nv_max;
         slot_b[k] = 16 * ((size_t)c->ck_every * (5 * NV + 6) +
@@ -140,7 +139,7 @@ extern "C" dlo_status dlo_backward_noalloc(dlo_ctx* c, const float* dL_dx_T, con
         P.rods = c->d_rods;
         P.order = bk.d_order;
         P.n_order = bk.n;
-        P.counter = c->d_counters + 4 + k;
+        P.counter = c->d_counters + kNumSizeClasses + k;
         P.ck = c->ck;
         P.ck_strideV = c->V;
         P.ck_strideE = c->Et;

@@ -1,0 +1,16 @@
+// dlo_nv224.cu -- the forward and backward kernels for rods of at most 224 vertices.
+#include "dlo_bwd_kernel.cuh"
+#include "dlo_fwd_kernel.cuh"
+
+namespace dlo {
+
+cudaError_t launch_forward_nv224(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st) {
+    return c ? launch_fwd_t<224, true>(P, grid, warps, st) : launch_fwd_t<224, false>(P, grid, warps, st);
+}
+int forward_occ_nv224(bool c, int warps) { return c ? fwd_occ_t<224, true>(warps) : fwd_occ_t<224, false>(warps); }
+cudaError_t launch_backward_nv224(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st) {
+    return c ? launch_bwd_t<224, true>(P, grid, warps, st) : launch_bwd_t<224, false>(P, grid, warps, st);
+}
+int backward_occ_nv224(bool c, int warps) { return c ? bwd_occ_t<224, true>(warps) : bwd_occ_t<224, false>(warps); }
+
+}  // namespace dlo

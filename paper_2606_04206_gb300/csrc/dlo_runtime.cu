@@ -9,7 +9,6 @@
 
 using namespace dlo;
 
-static int nv_class(int nv) { return nv <= 32 ? 32 : nv <= 64 ? 64 : nv <= 128 ? 128 : 256; }
 
 template <class T>
 static T* alloc_up(dlo_ctx* c, const std::vector<T>& h, dlo_status& st) {
@@ -127,20 +126,18 @@ dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const 
     c->d_npairs = reinterpret_cast<int*>(alloc_zero(c, sizeof(int) * c->B, st));
     if (st != DLO_OK) return st;
     // size classes; rods of a class in decreasing cost so the persistent warps balance
-    std::vector<std::vector<int>> cls(4);
-    for (int b = 0; b < c->B; ++b) {
-        int k = nv_class(rods[b].nv);
-        cls[k == 32 ? 0 : k == 64 ? 1 : k == 128 ? 2 : 3].push_back(b);
-    }
-    const int classes[4] = {32, 64, 128, 256};
-    for (int k = 0; k < 4; ++k) {
+    std::vector<std::vector<int>> cls(kNumSizeClasses);
+    for (int b = 0; b < c->B; ++b)
+        for (int k = 0; k < kNumSizeClasses; ++k)
+            if (size_class_at(k) == size_class(rods[b].nv)) cls[k].push_back(b);
+    for (int k = 0; k < kNumSizeClasses; ++k) {
         if (cls[k].empty()) continue;
         std::vector<int>& ids = cls[k];
         std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) {
             return (long long)rods[a].nv * rods[a].nsub > (long long)rods[b].nv * rods[b].nsub;
         });
         Bucket bk;
-        bk.nv_max = classes[k];
+        bk.nv_max = size_class_at(k);
         bk.contact = c->opt.self_contact != 0;
         bk.n = (int)ids.size();
         bk.d_order = alloc_up(c, ids, st);
@@ -162,7 +159,18 @@ dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const 
         bk.grid = (int)std::min<long long>((long long)best_nb * c->sm_count, want);
         c->buckets.push_back(bk);
     }
-    c->d_counters = reinterpret_cast<int*>(alloc_zero(c, sizeof(int) * 8, st));
+    if (c->buckets.size() > 1) {   // one stream per size class (see dlo_ctx::side)
+        c->side.resize(c->buckets.size(), nullptr);
+        c->joins.resize(c->buckets.size(), nullptr);
+        cudaError_t e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+        for (size_t k = 0; k < c->buckets.size() && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->joins[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_err(c, e, "size-class streams");
+    }
+    // work-queue heads: one per size class for the forward, one per class for the backward
+    c->d_counters = reinterpret_cast<int*>(alloc_zero(c, sizeof(int) * 2 * kNumSizeClasses, st));
     if (st != DLO_OK) return st;
     // rest twist from the rest frames, then the rest state
     InitParams P{};
@@ -197,7 +205,32 @@ dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const 
     return st;
 }
 
-void runtime_release(dlo_ctx*) {}
+void runtime_release(dlo_ctx* c) {
+    for (cudaStream_t s : c->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : c->joins) cudaEventDestroy(e);
+    if (c->fork) cudaEventDestroy(c->fork);
+    c->side.clear();
+    c->joins.clear();
+    c->fork = nullptr;
+}
+
+cudaStream_t class_stream(dlo_ctx* c, size_t k) { return c->side.empty() ? c->stream : c->side[k]; }
+
+cudaError_t fork_classes(dlo_ctx* c) {
+    if (c->side.empty()) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(c->fork, c->stream);
+    for (size_t k = 0; k < c->side.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(c->side[k], c->fork, 0);
+    return e;
+}
+
+cudaError_t join_classes(dlo_ctx* c) {
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < c->side.size() && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(c->joins[k], c->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->joins[k], 0);
+    }
+    return e;
+}
 
 // ------------------------------------------------------------------ rollout recording
 extern "C" dlo_status dlo_begin_rollout(dlo_ctx* c, int n_frames) {
@@ -261,6 +294,8 @@ extern "C" dlo_status dlo_begin_rollout(dlo_ctx* c, int n_frames) {
 // ------------------------------------------------------------------ step
 dlo_status launch_step(dlo_ctx* c, const float* actions, int frames, int substeps, float* x_frames, int frame0,
                        bool record) {
+    cudaError_t fe = fork_classes(c);
+    if (fe != cudaSuccess) return cuda_err(c, fe, "fork");
     for (size_t k = 0; k < c->buckets.size(); ++k) {
         const Bucket& bk = c->buckets[k];
         FwdParams P{};
@@ -290,11 +325,14 @@ dlo_status launch_step(dlo_ctx* c, const float* actions, int frames, int substep
         P.residual = c->d_residual;
         P.npairs = c->d_npairs;
         P.scene = c->scene;
-        cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), c->stream);
-        if (e == cudaSuccess) e = launch_forward(P, bk.nv_max, bk.contact, bk.grid, bk.warps, c->stream);
+        cudaStream_t sk = class_stream(c, k);
+        cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), sk);
+        if (e == cudaSuccess) e = launch_forward(P, bk.nv_max, bk.contact, bk.grid, bk.warps, sk);
         c->launches++;
         if (e != cudaSuccess) return cuda_err(c, e, "forward launch");
     }
+    fe = join_classes(c);
+    if (fe != cudaSuccess) return cuda_err(c, fe, "join");
     return DLO_OK;
 }
 

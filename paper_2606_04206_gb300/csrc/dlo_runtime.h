@@ -47,6 +47,11 @@ struct dlo_ctx {
     int* d_npairs = nullptr;
     int* d_counters = nullptr;   // one work-queue head per bucket
     std::vector<dlo::Bucket> buckets;
+    // with several size classes, each class's kernels run on its own stream, forked from and
+    // joined back to `stream` with events, so that the classes' tails overlap
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
     long long launches = 0;
     bool from_set_state = false;
     // rollout recording for dlo_backward
@@ -69,10 +74,14 @@ struct dlo_ctx {
 
 // launch shape and workspace size of the backward for a checkpoint interval (dlo_adjoint.cu)
 struct BwdPlan {
-    std::vector<size_t> slot_b;
+    std::vector<size_t> slot_b, offset;   // per class: bytes per resident rod, scratch offset
     std::vector<int> warps, grid, nsmax;
     size_t bytes = 0;
 };
+// the stream of size class k, and the fork / join around work issued on those streams
+cudaStream_t class_stream(dlo_ctx* c, size_t k);
+cudaError_t fork_classes(dlo_ctx* c);
+cudaError_t join_classes(dlo_ctx* c);
 dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out);
 
 dlo_status set_err(dlo_ctx* c, dlo_status s, const std::string& msg);
