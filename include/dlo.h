@@ -215,6 +215,30 @@ dlo_status dlo_backward_noalloc(dlo_ctx* ctx, const float* dL_dx_T, const float*
                                 const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
                                 float* dL_dx0, float* dL_dv0, float* dL_dtheta0);
 
+/* Task losses of App. B ("Reward design"), per rod, on the device. */
+enum {
+    DLO_LOSS_TARGET = 1,    /* (1/N) sum_i |x_i - t_i|^2; aux = targets [V][4] (trajectory optimisation) */
+    DLO_LOSS_CHAMFER = 2,   /* (1/N) sum_i min_j |x_i - y_j|^2 + (1/M) sum_j min_i |x_i - y_j|^2;
+                               aux = points [B][m][4], 1 <= m <= 1024 (Separation, Wiring-post) */
+    DLO_LOSS_WINDING = 3,   /* (1/2pi) sum over segments of the signed angle each subtends at a
+                               vertical post in the xy-plane; aux = post [B][4] (x, y, -, -) (Wrapping) */
+    DLO_LOSS_CROSSING = 4   /* sum over ordered pairs of non-adjacent edges of Omega / (4 pi), Omega
+                               the exact Gauss double integral of the two segments: the signed
+                               crossing sum of Unknotting's crossing number; aux unused */
+};
+
+/* Loss Q_b of every rod and, when dL_dx is given, dL/dx for L = sum_b g_b Q_b: the cotangent
+ * dlo_backward takes as dL/dx_T.  x [V][4] device positions (w ignored); aux as the kind
+ * says (device float4, 16-byte aligned); g [B] device dL/dQ_b (NULL = 1); q [B] device out (may
+ * be NULL); dL_dx [V][4] device out (NULL = not wanted; every vertex is written).  Enqueued on
+ * the context's stream, deterministic, no synchronisation.  The paper defines these task
+ * terms in App. B; the crossing sum's pair term is the standard closed form of the Gauss
+ * integral for straight segments (a reading of "signed crossing contributions").
+ * Errors: DLO_ERR_INVALID_ARG for an unknown kind, a missing or unaligned array, m out of
+ * range or rods of more than 256 vertices. */
+dlo_status dlo_loss(dlo_ctx* ctx, int kind, const float* x, const float* aux, int m, const float* g, float* q,
+                    float* dL_dx);
+
 enum {
     DLO_Q_SUBSTEPS = 1,      /* int [B]: substeps per frame of each rod */
     DLO_Q_STATUS = 2,        /* unsigned [B]: status bits (1 non-finite, 2 pair overflow) */

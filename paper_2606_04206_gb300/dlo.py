@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "dlo.h")
 STATUS = {0: "DLO_OK", 1: "DLO_ERR_INVALID_ARG", 2: "DLO_ERR_CUDA", 3: "DLO_ERR_OOM", 4: "DLO_ERR_NONFINITE",
           5: "DLO_ERR_CAPACITY", 6: "DLO_ERR_TIMEOUT", 7: "DLO_ERR_STATE"}
 Q_SUBSTEPS, Q_STATUS, Q_BYTES, Q_CONFIG, Q_RESIDUAL, Q_PAIRS, Q_LAUNCHES, Q_MASS = range(1, 9)
+LOSS_TARGET, LOSS_CHAMFER, LOSS_WINDING, LOSS_CROSSING = range(1, 5)
 N_MAT_GRAD = 5      # K_stretch, E_bend, G_twist, yield_curv, damping
 
 
@@ -90,6 +91,8 @@ def load(path: str | None = None):
     lib.dlo_backward.restype = st
     lib.dlo_backward_noalloc.argtypes = [vp] * 9
     lib.dlo_backward_noalloc.restype = st
+    lib.dlo_loss.argtypes = [vp, ip, vp, vp, ip, vp, vp, vp]
+    lib.dlo_loss.restype = st
     lib.dlo_query.argtypes = [vp, ip, vp]
     lib.dlo_query.restype = st
     lib.dlo_status_string.argtypes = [st]
@@ -338,6 +341,19 @@ class DloSim:
             return o.value
         a = np.ctypeslib.as_array(o).copy()
         return a.reshape(self.V, 4) if what == Q_MASS else a
+
+    def loss(self, kind, x, aux=None, g=None, grad=True):
+        """dlo_loss: per-rod task loss q [B] and (grad=True) dL/dx [V,4] for L = sum_b g_b q_b."""
+        torch = self.torch
+        q = torch.empty(self.B, device=self.device)
+        gx = torch.empty(self.V, 4, device=self.device) if grad else None
+        m = 0
+        if kind == LOSS_CHAMFER:
+            assert aux is not None and aux.dim() == 3 and aux.shape[0] == self.B and aux.shape[2] == 4
+            m = aux.shape[1]
+        self._check(self.lib.dlo_loss(self.ctx, int(kind), _ptr(x), _ptr(aux), int(m), _ptr(g), _ptr(q), _ptr(gx)),
+                    "dlo_loss")
+        return q, gx
 
     def material_tensor(self):
         """The context's per-rod material as a [B, 5] tensor (K_stretch, E_bend, G_twist,

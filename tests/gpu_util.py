@@ -27,18 +27,18 @@ def rel_inf(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-def oracle_gradients(prob, frames, wx, wv, wth):
+def oracle_gradients(prob, frames, wx, wv, wth, dtype=None):
     """Autograd gradients of L = sum(wx * x_T) + sum(wv * (v_T, twist rate)) + sum(wth * theta_T)
     through the FP64 oracle rollout, with respect to the initial state, the actions and the
-    per-rod material (K, E, G, yield curvature, damping)."""
+    per-rod material (K, E, G, yield curvature, damping).  dtype=torch.float32 runs the same
+    definitions in float32, which measures how well float32 arithmetic can resolve a gradient."""
     import torch as T
     p = prob
-    leaves = dict(x0=T.tensor(p.x0, requires_grad=True), v0=T.tensor(p.v0, requires_grad=True),
-                  th0=T.tensor(p.theta0, requires_grad=True), om0=T.tensor(p.omega0, requires_grad=True),
-                  act=T.tensor(p.actions[:frames], requires_grad=True))
-    mats = {k: T.tensor(np.asarray(getattr(p, k), np.float64), requires_grad=True)
-            for k in ("K", "E", "G", "yield_curv", "damping")}
-    sim = OracleSim(p, params=mats)
+    dt = T.float64 if dtype is None else dtype
+    leaf = lambda a: T.tensor(np.asarray(a, np.float64), dtype=dt, requires_grad=True)
+    leaves = dict(x0=leaf(p.x0), v0=leaf(p.v0), th0=leaf(p.theta0), om0=leaf(p.omega0), act=leaf(p.actions[:frames]))
+    mats = {k: leaf(getattr(p, k)) for k in ("K", "E", "G", "yield_curv", "damping")}
+    sim = OracleSim(p, params=mats, dtype=dt)
     sim.set_state(leaves["x0"], leaves["v0"], leaves["th0"], leaves["om0"])
     sim.step(leaves["act"], frames, diff=True)
     st = sim.get_state(as_numpy=False)
@@ -47,12 +47,13 @@ def oracle_gradients(prob, frames, wx, wv, wth):
     for b in range(p.batch):
         ne = eo[b + 1] - eo[b]
         om_w[eo[b]:eo[b + 1]] = wv[vo[b]:vo[b] + ne, 3]
-    L = ((st["x"] * T.tensor(wx[:, :3])).sum() + (st["v"] * T.tensor(wv[:, :3])).sum()
-         + (st["omega"] * T.tensor(om_w)).sum() + (st["theta"] * T.tensor(wth)).sum())
+    w = lambda a: T.tensor(a, dtype=dt)
+    L = ((st["x"] * w(wx[:, :3])).sum() + (st["v"] * w(wv[:, :3])).sum()
+         + (st["omega"] * w(om_w)).sum() + (st["theta"] * w(wth)).sum())
     names = ["x0", "v0", "th0", "om0", "act"] + list(mats)
     inputs_ = [leaves[n] for n in names[:5]] + [mats[n] for n in names[5:]]
     g = T.autograd.grad(L, inputs_, allow_unused=True)
-    out = {n: (gi.numpy() if gi is not None else np.zeros(tuple(x.shape))) for n, gi, x in zip(names, g, inputs_)}
+    out = {n: (gi.double().numpy() if gi is not None else np.zeros(tuple(x.shape))) for n, gi, x in zip(names, g, inputs_)}
     out["material"] = np.stack([out[k] for k in ("K", "E", "G", "yield_curv", "damping")], 1)
     return out, float(L.detach())
 

@@ -37,9 +37,10 @@ def log_sens(prob, g):
     return g * pv
 
 
-def check(prob, frames, seed=0, **opt):
+def check(prob, frames, seed=0, tol=None, **opt):
     wx, wv, wth = weights(prob, seed)
     ref, _ = oracle_gradients(prob, frames, wx, wv, wth)
+    tol = TOL if tol is None else tol
     sim = sim_for(prob, **opt)
     got = device_gradients(sim, prob, frames, wx, wv, wth)
     got["material"], ref["material"] = log_sens(prob, got["material"]), log_sens(prob, ref["material"])
@@ -48,7 +49,7 @@ def check(prob, frames, seed=0, **opt):
         rel, cos = grad_agreement(got[k], ref[k])
         report[k] = (rel, cos)
     print("gradient agreement (rel L2, cosine):", {k: (f"{r:.2e}", f"{c:.6f}") for k, (r, c) in report.items()})
-    bad = {k: v for k, v in report.items() if not (v[0] <= TOL.get(k, 1e-3) and v[1] >= 0.999)}
+    bad = {k: v for k, v in report.items() if not (v[0] <= tol.get(k, 1e-3) and v[1] >= 0.999)}
     assert not bad, report
     return report
 
@@ -57,6 +58,26 @@ def check(prob, frames, seed=0, **opt):
 def test_backward_matches_oracle_autograd(kind):
     p = inputs.small_case(kind, n_rods=3, n=12, frames=3)
     check(p, 3)
+
+
+def test_backward_with_creep_below_full_return():
+    """Bending creep with r_c = 0.3 (App. A.1: the rest curvature moves toward the current one
+    by r_c of the excess over the yield surface): plastic wires bent past yield.
+
+    These rods are stiff (E up to 3e7 Pa, K = E), so their strains sit near float32's
+    resolution and the scale-free material sensitivities are poorly conditioned in float32:
+    the same definitions evaluated in float32 (the oracle at dtype float32) miss the FP64
+    values by ~1e-2.  The material bar is therefore max(1e-3, 2 x that float32 error),
+    measured here on the same inputs; every other gradient keeps the 1e-3 bar."""
+    p = inputs.small_case("batching", n_rods=3, n=24, frames=4)
+    p.creep_rate[:] = 0.3
+    p.yield_curv[:] = inputs.f32(np.full(3, 1.0))
+    wx, wv, wth = weights(p, 0)
+    ref, _ = oracle_gradients(p, 4, wx, wv, wth)
+    f32, _ = oracle_gradients(p, 4, wx, wv, wth, dtype=torch.float32)
+    floor, _ = grad_agreement(log_sens(p, f32["material"]), log_sens(p, ref["material"]))
+    print("float32 floor of the material sensitivities:", floor)
+    check(p, 4, tol={"material": max(1e-3, 2.0 * floor)})
 
 
 def test_backward_with_self_contact_and_loops():

@@ -67,6 +67,24 @@ def test_one_frame_from_same_state_with_contact(kind, warm):
     assert np.abs(fg["kbar"] - fo["kbar"]).max() <= 1e-4
 
 
+def test_creep_below_full_return_one_frame():
+    """r_c = 0.3 creep of the rest curvature (App. A.1) against the oracle, from the same state."""
+    p = inputs.small_case("batching", n_rods=4, n=40, frames=6)
+    p.creep_rate[:] = 0.3
+    p.yield_curv[:] = inputs.f32(np.full(4, 1.0))
+    sim = sim_for(p)
+    sim.reset()
+    acts = actions_dev(p)
+    sim.step(acts[:5].contiguous(), 5)
+    o = oracle_from_device_state(p, sim)
+    sim.step(acts[5:6].contiguous(), 1)
+    o.step(p.actions[5:6], 1)
+    fo, fg = o.get_state(), sim.full_state_numpy()
+    assert np.abs(fo["kbar"]).max() > 0                     # yield was exceeded
+    assert rel_inf(fg["x"], fo["x"]) <= 1e-5
+    assert np.abs(fg["kbar"] - fo["kbar"]).max() <= 1e-4
+
+
 def test_ragged_batch_all_size_classes():
     p = inputs.batching(n_rods=8, frames=3, seed=11, vmin=16, vmax=256)
     p.E[:] = inputs.f32(np.full(8, 2e4))          # keep substep counts small for the oracle
