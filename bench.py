@@ -16,6 +16,10 @@ roofline     the dominant kernel (the backward) against the FP32 CUDA-core peak,
 cpu_baseline the FP64 oracle on the host cores, on a bounded sample of the same workload
 plain        the plain per-phase GPU step (dlo_step_plain) on the same rods
 
+`--workload` selects the other configurations (batching, selfcontact, diff) or ``cmaes``: one
+CMA-ES generation of the Unknotting task per step (400 candidate rollouts of one knotted rope,
+forward only, each scored on the device by its crossing sum and self-repulsion penalty).
+
 `--impl reference` times the oracle instead (the reference arm of this benchmark).
 """
 import argparse
@@ -45,13 +49,19 @@ SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
 
+def metric_for(workload):
+    if workload == "cmaes":
+        return "rod-vertex-steps/s of one CMA-ES generation (forward rollouts + device scores)"
+    return METRIC
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="trajopt", choices=["trajopt", "batching", "selfcontact", "diff"],
+    ap.add_argument("--workload", default="trajopt", choices=["trajopt", "batching", "selfcontact", "diff", "cmaes"],
                     help="trajopt is the headline line; the others measure the other configurations")
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--rods", type=int, default=None)
@@ -135,6 +145,33 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------- reference arm
+def oracle_population_rate(prob, frames, rods):
+    """FP64 oracle forward rollout of `rods` candidates plus their Unknotting scores;
+    returns (rod-vertex-steps/s, seconds)."""
+    import numpy as np
+    import torch
+    from oracle import OracleSim, losses
+    sub = prob.subset(rods, frames=frames)
+    t0 = time.perf_counter()
+    sim = OracleSim(sub)
+    sim.set_state(sub.x0, sub.v0, sub.theta0, sub.omega0)
+    sim.step(sub.actions[:frames], frames)
+    x = torch.as_tensor(sim.get_state()["x"])
+    for b, (v0, v1) in enumerate(zip(sub.vert_off[:-1], sub.vert_off[1:])):
+        xb = x[v0:v1]
+        losses.crossing(xb)
+        losses.repulsion(xb, 2.0 * rest_edge(sub.x_rest[v0:v1]), 2)
+    dt = time.perf_counter() - t0
+    units = float(np.sum(sub.n_verts)) * frames
+    return units / dt, dt
+
+
+def rest_edge(x):
+    """Mean rest edge length of one open rod (its initial shape)."""
+    import numpy as np
+    return float(np.linalg.norm(np.diff(np.asarray(x, np.float64), axis=0), axis=1).mean())
+
+
 def oracle_rollout_rate(prob, frames, rods):
     """FP64 oracle forward + reverse-mode backward on `rods` rods of the workload; returns
     (rod-vertex-steps/s, seconds)."""
@@ -165,16 +202,18 @@ def run_reference(args, rank, ws):
     short.frames = 4                       # the oracle samples two frames per step
     prob, desc, R, _ = make_workload(short, 0)
     rates = []
+    rate_fn = oracle_population_rate if args.workload == "cmaes" else oracle_rollout_rate
     for i in range(args.warmup + args.steps):
-        r, dt = oracle_rollout_rate(prob, 2, [0, 1])
+        r, dt = rate_fn(prob, 2, [0, 1])
         if i >= args.warmup:
             rates.append((r, dt))
     value = sum(r for r, _ in rates) / len(rates)
     ms = 1e3 * sum(dt for _, dt in rates) / len(rates)
     cores = torch.get_num_threads()
     sample = (f"rods 0 and 1 ({int(prob.n_verts[0])} and {int(prob.n_verts[1])} vertices) x 2 frames per step, "
-              f"FP64 forward + autograd backward")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+              + ("FP64 forward + crossing sum and repulsion scores" if args.workload == "cmaes"
+                 else "FP64 forward + autograd backward"))
+    line = {"impl": "reference", "metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc + " (oracle sample)", "frames_per_step": 2},
@@ -186,7 +225,8 @@ def run_reference(args, rank, ws):
 # --------------------------------------------------------------------------- native arm
 # rods, vertices per rod, frames of each workload (the configurations' own sizes)
 WORKLOADS = {"trajopt": (4096, 128, 2000), "batching": (1024, None, 1000), "selfcontact": (4096, 200, 300),
-             "diff": (256, 64, 500)}
+             "diff": (256, 64, 500), "cmaes": (400, 128, 2000)}
+REPULSION_WEIGHT = 1e3     # the Unknotting penalty's weight against the crossing sum
 
 
 def make_workload(args, rank):
@@ -204,6 +244,10 @@ def make_workload(args, rank):
         prob = inputs.batching(n_rods=R, frames=F, seed=1000 + rank)
         desc = (f"batching: {R} rods x 16..256 vertices, 0.3..2 m, E 1e4..1e8 Pa, plastic, 2 grippers, ground, "
                 f"{F} frames, per-rod substeps")
+    elif w == "cmaes":
+        prob = inputs.cmaes(pop=R, frames=F, seed=5000 + rank, n=N)
+        desc = (f"cmaes: one CMA-ES generation of Unknotting, population {R} x {N} vertices (one knotted rope, "
+                f"sigma 5e-2), {F} frames forward, ground, self-contact, crossing-sum + repulsion scores")
     elif w == "selfcontact":
         prob = inputs.selfcontact(n_rods=R, frames=F, seed=3000 + rank, n=N)
         desc = f"selfcontact: {R} knotted closed bands x {N} vertices, ground + box, self-contact, {F} frames"
@@ -245,19 +289,38 @@ def run_native(args, rank, ws):
         x, _, _ = sim.get_state()
         return loss_grad(x)
 
+    pop = args.workload == "cmaes"          # forward-only rollouts scored on the device
+    if pop:
+        prm = torch.zeros(R, 4, device=dev)
+        prm[:, 0] = torch.as_tensor([2.0 * rest_edge(prob.x_rest[a:b]) for a, b in
+                                     zip(prob.vert_off[:-1], prob.vert_off[1:])], device=dev)
+        prm[:, 1] = 2.0
+
+    def scores():
+        x, _, _ = sim.get_state()
+        qc, _ = sim.loss(dlo.LOSS_CROSSING, x, grad=False)
+        qr, _ = sim.loss(dlo.LOSS_REPULSION, x, prm, grad=False)
+        return qc, qr
+
     def one_step(record):
         flush.fill_(1.0)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         l0 = sim.query(dlo.Q_LAUNCHES)
         ev[0].record(stream)
         sim.set_state(x0, v0, th0)
-        sim.begin_rollout(F)
-        sim.step(acts, F)
-        ev[1].record(stream)
-        g = dL_dx()
         gb = torch.cuda.Event(enable_timing=True)
-        gb.record(stream)
-        sim.backward(dL_dx=g, want=("actions", "material", "x0"))
+        if pop:
+            sim.step(acts, F)
+            ev[1].record(stream)
+            gb.record(stream)
+            scores()
+        else:
+            sim.begin_rollout(F)
+            sim.step(acts, F)
+            ev[1].record(stream)
+            g = dL_dx()
+            gb.record(stream)
+            sim.backward(dL_dx=g, want=("actions", "material", "x0"))
         ev[2].record(stream)
         torch.cuda.synchronize()
         l1 = sim.query(dlo.Q_LAUNCHES)
@@ -292,6 +355,7 @@ def run_native(args, rank, ws):
     h_target = target.cpu().pin_memory()
     h_gact = torch.empty(F, R, 2, 6).pin_memory()
     h_loss = torch.empty(1).pin_memory()
+    h_scores = torch.empty(2, R).pin_memory()
     def e2e_step():
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -301,6 +365,14 @@ def run_native(args, rank, ws):
         xs, vs, ts = (t.to(dev, non_blocking=True) for t in h_state)
         tg = h_target.to(dev, non_blocking=True)
         sim.set_state(xs, vs, ts)
+        if pop:
+            sim.step(d_acts, F)
+            qc, qr = scores()
+            h_scores[0].copy_(qc, non_blocking=True)
+            h_scores[1].copy_(qr, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
         sim.begin_rollout(F)
         sim.step(d_acts, F)
         x, _, _ = sim.get_state()
@@ -316,8 +388,12 @@ def run_native(args, rank, ws):
     e2e_step()   # warm-up: first use of the host buffers and of the device copies' allocations
     e2e = [e2e_step() for _ in range(args.e2e_steps)]
     ms_e2e = max_over_ranks(sum(e2e) / len(e2e), ws)
-    h2d = h_acts.numel() * 4 + sum(t.numel() * 4 for t in h_state) + h_target.numel() * 4
-    d2h = h_gact.numel() * 4 + 4
+    if pop:
+        h2d = h_acts.numel() * 4 + sum(t.numel() * 4 for t in h_state)
+        d2h = h_scores.numel() * 4
+    else:
+        h2d = h_acts.numel() * 4 + sum(t.numel() * 4 for t in h_state) + h_target.numel() * 4
+        d2h = h_gact.numel() * 4 + 4
 
     # roofline of the dominant kernel (the backward): algorithmic FP32 operations per launch
     nsub_rod = np.asarray(sim.query(dlo.Q_SUBSTEPS), np.float64)
@@ -329,11 +405,15 @@ def run_native(args, rank, ws):
     fwd_tflops = FLOPS_FWD_PER_VS * vs_units / (ms_fwd / 1e3) / 1e12
     traffic = (BWD_DRAM_BYTES_PER_ROD_FRAME * R * F
                if (args.workload == "trajopt" and N == 128 and not args.no_self_contact) else None)
-    roofline = {"bound": "alu", "kernel": "bwd_kernel (dlo_backward)", "achieved": bwd_tflops,
-                "peak": peak_tflops, "unit": "TFLOP/s", "frac": bwd_tflops / peak_tflops, "traffic": traffic,
-                "peak_basis": f"FP32 CUDA cores: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                              f"{max_mhz:.0f} MHz", "forward": {"achieved": fwd_tflops,
-                                                                "frac": fwd_tflops / peak_tflops}}
+    basis = f"FP32 CUDA cores: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz"
+    if pop:
+        roofline = {"bound": "alu", "kernel": "fwd_kernel (dlo_step)", "achieved": fwd_tflops,
+                    "peak": peak_tflops, "unit": "TFLOP/s", "frac": fwd_tflops / peak_tflops, "traffic": None,
+                    "peak_basis": basis}
+    else:
+        roofline = {"bound": "alu", "kernel": "bwd_kernel (dlo_backward)", "achieved": bwd_tflops,
+                    "peak": peak_tflops, "unit": "TFLOP/s", "frac": bwd_tflops / peak_tflops, "traffic": traffic,
+                    "peak_basis": basis, "forward": {"achieved": fwd_tflops, "frac": fwd_tflops / peak_tflops}}
 
     # plain per-phase GPU step on the same rods (short rollout, forward only)
     plain = None
@@ -357,22 +437,24 @@ def run_native(args, rank, ws):
     # CPU baseline: the FP64 oracle on a bounded sample of the same workload (rank 0 only)
     cpu = None
     if rank == 0:
-        rate, dt = oracle_rollout_rate(prob, 1, [0, 1])
+        rate_fn = oracle_population_rate if pop else oracle_rollout_rate
+        rate, dt = rate_fn(prob, 1, [0, 1])
         frames = max(1, min(20, int(args.cpu_seconds / max(dt, 1e-3))))
-        rate, dt = oracle_rollout_rate(prob, frames, [0, 1])
+        rate, dt = rate_fn(prob, frames, [0, 1])
+        what = "crossing sum and repulsion scores" if pop else "autograd backward"
         cpu = {"value": rate, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                "sample": f"2 rods x {N} vertices x {frames} frames of the same workload, FP64 forward + "
-                         f"autograd backward, {dt:.1f} s"}
+                         f"{what}, {dt:.1f} s"}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        line = {"metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": desc,
                            "rods_per_gpu": R, "verts_per_rod": N, "frames": F, "substeps": nsub,
                            "n_iter_pbd": 10, "checkpoint_every": int(sim.query(dlo.Q_CONFIG)[1]),
                            "l2": "256 MiB buffer written before every timed step"},
-                "fwd_value": fwd_value, "ms_fwd": ms_fwd, "ms_bwd": ms_bwd,
+                "fwd_value": fwd_value, "ms_fwd": ms_fwd, ("ms_score" if pop else "ms_bwd"): ms_bwd,
                 "e2e": {"value": units * ws / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(max(launches)), "roofline": roofline, "cpu_baseline": cpu, "plain": plain,

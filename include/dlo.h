@@ -222,9 +222,17 @@ enum {
                                aux = points [B][m][4], 1 <= m <= 1024 (Separation, Wiring-post) */
     DLO_LOSS_WINDING = 3,   /* (1/2pi) sum over segments of the signed angle each subtends at a
                                vertical post in the xy-plane; aux = post [B][4] (x, y, -, -) (Wrapping) */
-    DLO_LOSS_CROSSING = 4   /* sum over ordered pairs of non-adjacent edges of Omega / (4 pi), Omega
+    DLO_LOSS_CROSSING = 4,  /* sum over ordered pairs of non-adjacent edges of Omega / (4 pi), Omega
                                the exact Gauss double integral of the two segments: the signed
                                crossing sum of Unknotting's crossing number; aux unused */
+    DLO_LOSS_MINDIST = 5,   /* min_i |x_i - o|: distance from the rod to an object's centre (the
+                               rope-object contact terms of Gathering, Lifting, Wrapping);
+                               aux = o [B][4] (x, y, z, -); the gradient goes to the nearest
+                               vertex (the lowest index on an exact tie) */
+    DLO_LOSS_REPULSION = 6  /* sum over unordered edge pairs more than k apart along the rod
+                               (cyclically for loops) of max(0, delta - d_ab)^2, d_ab the distance
+                               between the closest points of the two segments (Unknotting's
+                               self-repulsion penalty); aux = [B][4] (delta, k, -, -), k >= 1 */
 };
 
 /* Loss Q_b of every rod and, when dL_dx is given, dL/dx for L = sum_b g_b Q_b: the cotangent
@@ -235,7 +243,8 @@ enum {
  * terms in App. B; the crossing sum's pair term is the standard closed form of the Gauss
  * integral for straight segments (a reading of "signed crossing contributions").
  * Errors: DLO_ERR_INVALID_ARG for an unknown kind, a missing or unaligned array, m out of
- * range or rods of more than 256 vertices. */
+ * range or rods of more than 256 vertices.  A repulsion window k < 1 (read on the device)
+ * is taken as 1. */
 dlo_status dlo_loss(dlo_ctx* ctx, int kind, const float* x, const float* aux, int m, const float* g, float* q,
                     float* dL_dx);
 

@@ -14,12 +14,20 @@ gradients are torch.autograd of these definitions.
                so the sum is the writhe of the polygon
 * linking      the same pair integral summed across two closed polygons (their linking
                number; used to pin the pair integral, which must give an integer)
+* mindist      the minimum distance from the rod's vertices to an object's centre (the
+               rope-object contact terms of Gathering, Lifting and Wrapping)
+* repulsion    Unknotting's self-repulsion penalty: sum over edge pairs more than k apart along
+               the rod of max(0, delta - d)^2, d the distance between the two segments;
+               reading: a quadratic hinge, with delta twice the rest edge length and k = 2 in the
+               task (the smallest window that leaves a straight rod unpenalised)
 """
 import math
 
 import torch
 
-__all__ = ["target_mse", "chamfer", "winding", "gauss_pair", "crossing", "linking"]
+from .dlo import closest_params
+
+__all__ = ["target_mse", "chamfer", "winding", "gauss_pair", "crossing", "linking", "mindist", "repulsion"]
 
 
 def target_mse(x, t):
@@ -95,3 +103,25 @@ def linking(xa, xb):
     a, b = a.reshape(-1), b.reshape(-1)
     om = gauss_pair(xa[ia0[a]], xa[ia1[a]], xb[ib0[b]], xb[ib1[b]])
     return om.sum() / (4.0 * math.pi)
+
+
+def mindist(x, o):
+    """min_i |x_i - o|."""
+    return (x - torch.as_tensor(o, dtype=x.dtype)[:3]).norm(dim=1).min()
+
+
+def repulsion(x, delta, k, closed=False):
+    """sum over edge pairs (a < b) whose index separation (cyclic for loops) exceeds k of
+    max(0, delta - |c_a - c_b|)^2, c_a and c_b the closest points of the two segments (the
+    clamped solve of closest_params, lower edge first)."""
+    i0, i1, ne = _edges(x, closed)
+    a, b = torch.triu_indices(ne, ne, 1)
+    sep = b - a
+    if closed:
+        sep = torch.minimum(sep, ne - sep)
+    keep = sep > k
+    a, b = a[keep], b[keep]
+    pa, qa, pb, qb = x[i0[a]], x[i1[a]], x[i0[b]], x[i1[b]]
+    s, u = closest_params(pa, qa, pb, qb)
+    d = ((pa + s[:, None] * (qa - pa)) - (pb + u[:, None] * (qb - pb))).norm(dim=1)
+    return ((delta - d).clamp(min=0.0) ** 2).sum()

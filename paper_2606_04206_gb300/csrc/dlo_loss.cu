@@ -6,6 +6,7 @@
 
 #include "dlo_runtime.h"
 #include "dlo_vec.cuh"
+#include "dlo_physics.cuh"
 
 namespace dlo {
 namespace {
@@ -195,6 +196,107 @@ __global__ void loss_crossing(const RodInfo* rods, const float4* X, const float*
     }
 }
 
+// min_i |x_i - o|; the subgradient at the nearest vertex (lowest index on a tie)
+__global__ void loss_mindist(const RodInfo* rods, const float4* X, const float4* obj, const float* g, float* q,
+                             float4* gx) {
+    __shared__ float bd[kLT];
+    __shared__ int bi[kLT];
+    const int rod = blockIdx.x;
+    const RodInfo R = rods[rod];
+    const V3<float> o = f3(obj[rod]);
+    float best = INFINITY;
+    int arg = 0;
+    for (int i = threadIdx.x; i < R.nv; i += kLT) {
+        const V3<float> d = f3(X[R.v0 + i]) - o;
+        const float d2 = dot(d, d);
+        if (d2 < best) {   // strict: a thread's own vertices come in increasing order
+            best = d2;
+            arg = i;
+        }
+    }
+    bd[threadIdx.x] = best;
+    bi[threadIdx.x] = arg;
+    __syncthreads();
+    for (int s = kLT / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            const float d2 = bd[threadIdx.x + s];
+            const int i2 = bi[threadIdx.x + s];
+            if (d2 < bd[threadIdx.x] || (d2 == bd[threadIdx.x] && i2 < bi[threadIdx.x])) {
+                bd[threadIdx.x] = d2;
+                bi[threadIdx.x] = i2;
+            }
+        }
+        __syncthreads();
+    }
+    const float dmin = sqrtf(bd[0]);
+    const int imin = bi[0];
+    if (q && threadIdx.x == 0) q[rod] = dmin;
+    if (!gx) return;
+    const float c = dmin > 0.f ? gscale(g, rod) / dmin : 0.f;
+    for (int i = threadIdx.x; i < R.nv; i += kLT)
+        gx[R.v0 + i] = i == imin ? f4(c * (f3(X[R.v0 + i]) - o), 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// sum over unordered pairs of edges more than k apart of max(0, delta - d)^2, d the distance of
+// the segments' closest points.  The closest-point parameters are each optimal for the other
+// (or fixed), so the gradient holds them fixed: dd/dx_a0 = (1 - s) n, dd/dx_a1 = s n.
+__global__ void loss_repulsion(const RodInfo* rods, const float4* X, const float4* prm, const float* g, float* q,
+                               float4* gx) {
+    __shared__ double sh[kLT];
+    __shared__ float4 xs[kMaxV];
+    __shared__ float4 ge0[kMaxV], ge1[kMaxV];
+    const int rod = blockIdx.x;
+    const RodInfo R = rods[rod];
+    const bool closed = R.flags & ROD_CLOSED;
+    const int n = R.nv, ne = closed ? n : n - 1;
+    const float delta = prm[rod].x;
+    const int k = max(1, (int)prm[rod].y);
+    for (int i = threadIdx.x; i < n; i += kLT) xs[i] = X[R.v0 + i];
+    __syncthreads();
+    double s = 0.0;
+    for (int a = threadIdx.x; a < ne; a += kLT) {
+        const int a1 = (a + 1 == n) ? 0 : a + 1;
+        const V3<float> pa = f3(xs[a]), pb = f3(xs[a1]);
+        V3<float> g0 = zf3(), g1 = zf3();
+        for (int b = 0; b < ne; ++b) {
+            int sep = abs(a - b);
+            if (closed) sep = min(sep, ne - sep);
+            if (sep <= k) continue;
+            const int b1 = (b + 1 == n) ? 0 : b + 1;
+            // every pair is solved with its lower edge first, as both of its threads must see
+            // the same closest points (the near-parallel rule is not symmetric)
+            const bool first = a < b;
+            const V3<float> qa = f3(xs[b]), qb = f3(xs[b1]);
+            const V3<float> p1 = first ? pa : qa, q1 = first ? pb : qb, p2 = first ? qa : pa, q2 = first ? qb : pb;
+            float ps, pu;
+            closest_params(p1, q1, p2, q2, ps, pu);
+            const V3<float> dv = (p1 + ps * (q1 - p1)) - (p2 + pu * (q2 - p2));
+            const float d = sqrtf(dot(dv, dv));
+            if (d >= delta) continue;
+            if (first) s += (double)((delta - d) * (delta - d));
+            if (d > 0.f) {
+                const V3<float> gd = (-2.f * (delta - d) / d) * dv;   // d(pen)/d(first closest point)
+                const float t = first ? ps : pu, sg = first ? 1.f : -1.f;
+                g0 += (sg * (1.f - t)) * gd;
+                g1 += (sg * t) * gd;
+            }
+        }
+        ge0[a] = f4(g0, 0.f);
+        ge1[a] = f4(g1, 0.f);
+    }
+    __syncthreads();
+    s = block_sum(s, sh);
+    if (q && threadIdx.x == 0) q[rod] = (float)s;
+    if (!gx) return;
+    const float c = gscale(g, rod);
+    for (int i = threadIdx.x; i < n; i += kLT) {
+        V3<float> d = zf3();
+        if (closed || i < ne) d += f3(ge0[i]);
+        if (closed || i > 0) d += f3(ge1[i == 0 ? ne - 1 : i - 1]);
+        gx[R.v0 + i] = f4(c * d, 0.f);
+    }
+}
+
 }  // namespace
 }  // namespace dlo
 
@@ -225,6 +327,15 @@ extern "C" dlo_status dlo_loss(dlo_ctx* c, int kind, const float* x, const float
             break;
         case DLO_LOSS_CROSSING:
             loss_crossing<<<c->B, kLT, 0, c->stream>>>(c->d_rods, X, g, q, GX);
+            break;
+        case DLO_LOSS_MINDIST:
+            if (!aux) return set_err(c, DLO_ERR_INVALID_ARG, "the minimum distance needs an object centre per rod");
+            loss_mindist<<<c->B, kLT, 0, c->stream>>>(c->d_rods, X, reinterpret_cast<const float4*>(aux), g, q, GX);
+            break;
+        case DLO_LOSS_REPULSION:
+            if (!aux) return set_err(c, DLO_ERR_INVALID_ARG, "the repulsion penalty needs (delta, k) per rod");
+            loss_repulsion<<<c->B, kLT, 0, c->stream>>>(c->d_rods, X, reinterpret_cast<const float4*>(aux), g, q,
+                                                        GX);
             break;
         default:
             return set_err(c, DLO_ERR_INVALID_ARG, "unknown loss kind");

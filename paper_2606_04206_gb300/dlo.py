@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "dlo.h")
 STATUS = {0: "DLO_OK", 1: "DLO_ERR_INVALID_ARG", 2: "DLO_ERR_CUDA", 3: "DLO_ERR_OOM", 4: "DLO_ERR_NONFINITE",
           5: "DLO_ERR_CAPACITY", 6: "DLO_ERR_TIMEOUT", 7: "DLO_ERR_STATE"}
 Q_SUBSTEPS, Q_STATUS, Q_BYTES, Q_CONFIG, Q_RESIDUAL, Q_PAIRS, Q_LAUNCHES, Q_MASS = range(1, 9)
-LOSS_TARGET, LOSS_CHAMFER, LOSS_WINDING, LOSS_CROSSING = range(1, 5)
+LOSS_TARGET, LOSS_CHAMFER, LOSS_WINDING, LOSS_CROSSING, LOSS_MINDIST, LOSS_REPULSION = range(1, 7)
 N_MAT_GRAD = 5      # K_stretch, E_bend, G_twist, yield_curv, damping
 
 

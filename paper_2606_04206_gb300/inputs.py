@@ -29,6 +29,11 @@ Workloads (seeds are ``numpy.random.default_rng(config_index*1000 + repeat)``):
                  elastic rope (Unknotting row), plastic wire (Letter-Art row),
                  grasped at 1/4 and 3/4 of their length by two grippers with
                  smooth random 6-DoF trajectories, 2000 frames.
+* ``cmaes``      one CMA-ES generation of Unknotting: 400 copies of one knotted
+                 rope (128 vertices, opened trefoil-family curve on the table,
+                 Unknotting row), mean gripper trajectory plus per-candidate
+                 smooth perturbations of 5e-2 m / rad, self-contact, 2000 frames,
+                 forward only, scored on the device.
 
 The open rods of batching, diff and trajopt are smooth curves whose unit tangent is a
 low-frequency random Fourier series (bending radius >= 2 cm), lying nearly horizontal
@@ -40,7 +45,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field, replace
 import numpy as np
 
-__all__ = ["Problem", "plain", "batching", "diff", "selfcontact", "trajopt",
+__all__ = ["Problem", "plain", "batching", "diff", "selfcontact", "trajopt", "cmaes",
            "small_case", "custom", "f32"]
 
 
@@ -388,6 +393,34 @@ def trajopt(n_rods: int = 4096, frames: int = 2000, seed: int = 4000, n: int = 1
                      self_contact=self_contact)
 
 
+def cmaes(pop: int = 400, frames: int = 2000, seed: int = 5000, n: int = 128, sigma: float = 5e-2) -> Problem:
+    """One CMA-ES generation of the Unknotting task: ``pop`` copies of one knotted rope (a
+    trefoil-family curve of 1 m, opened, resting on the ground; Unknotting row: K = 1e5,
+    E = 1e4, no twist stiffness), each with the population mean's gripper trajectory plus
+    its own smooth perturbation of amplitude ``sigma`` (m and rad)."""
+    rng = np.random.default_rng(seed)
+    for _ in range(200):
+        # a knot band of n + 3 vertices, opened by dropping three (the ends start four edges
+        # apart) and flattened onto the table; the crossings keep their over/under order
+        m = n + 3
+        x = _knot_band(rng, m, m / (n - 1), 0.002, z_min=0.005)[:n]
+        x[:, 2] *= 0.4
+        x = _resample(x, n)
+        x = (x - x.mean(0)) / _length(x)
+        x[:, 2] += 0.005 - x[:, 2].min()
+        if not _too_close(x, 4 * 0.002, 3, False):
+            break
+    else:
+        raise RuntimeError("could not draw a flat knotted rope")
+    rods = [x] * pop
+    gp, gr = _grippers_for(rods)
+    mean = _smooth_actions(rng, frames, 1, 1e-3)
+    acts = mean + _smooth_actions(rng, frames, pop, 1e-3, amp_pos=sigma, amp_rot=sigma)
+    return _assemble("cmaes", rods, np.zeros(pop, bool), dict(K=1e5, E=1e4, G=0.0),
+                     frames, acts, np.full(pop, 2), gp, gr,
+                     planes=np.array([[0.0, 0.0, 1.0, 0.0]]), self_contact=True)
+
+
 def custom(rods_x, closed=None, frames: int = 1, actions=None, n_grippers=None, grip_pos=None,
            grip_rot=None, pinned=None, **kw) -> Problem:
     """A hand-made workload: explicit rod shapes plus material / option overrides."""
@@ -418,6 +451,8 @@ def small_case(kind: str, n_rods: int = 4, n: int = 24, frames: int = 10, seed: 
         return diff(n_rods, frames, seed, n)
     if kind == "selfcontact":
         return selfcontact(n_rods, frames, seed, n)
+    if kind == "cmaes":
+        return cmaes(n_rods, frames, seed, n)
     if kind == "trajopt":
         return trajopt(n_rods, frames, seed, n, self_contact=True)
     raise ValueError(kind)
