@@ -52,7 +52,9 @@ FP32_LANES_PER_SM = 128
 def metric_for(workload):
     if workload == "cmaes":
         return "rod-vertex-steps/s of one CMA-ES generation (forward rollouts + device scores)"
-    return METRIC
+    if workload == "trajopt":
+        return METRIC
+    return f"rod-vertex-steps/s fwd+bwd ({workload} configuration), vs plain GPU step"
 
 
 def parse():
@@ -61,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="trajopt", choices=["trajopt", "batching", "selfcontact", "diff", "cmaes"],
+    ap.add_argument("--workload", default="trajopt", choices=["trajopt", "batching", "selfcontact", "diff", "cmaes", "sysid"],
                     help="trajopt is the headline line; the others measure the other configurations")
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--rods", type=int, default=None)
@@ -166,19 +168,42 @@ def oracle_population_rate(prob, frames, rods):
     return units / dt, dt
 
 
+def sysid_cameras():
+    """Two pinhole cameras over the table (rods within about 0.75 m of the origin): one looking
+    straight down from 1.6 m, one from the side at 50 degrees; 256 x 256 px."""
+    import math
+    import numpy as np
+    c = SIL_HW / 2
+    down = np.concatenate([[160.0, 160.0, c, c], np.diag([1.0, -1.0, -1.0]).reshape(9), [0.0, 0.0, 1.6]])
+    a = math.radians(50.0)
+    R = np.array([[1.0, 0.0, 0.0], [0.0, -math.sin(a), -math.cos(a)], [0.0, math.cos(a), -math.sin(a)]])
+    eye = np.array([0.0, -math.cos(a), math.sin(a)]) * 1.8
+    side = np.concatenate([[150.0, 150.0, c, c], R.reshape(9), -R @ eye])
+    return np.stack([down, side])
+
+
 def rest_edge(x):
     """Mean rest edge length of one open rod (its initial shape)."""
     import numpy as np
     return float(np.linalg.norm(np.diff(np.asarray(x, np.float64), axis=0), axis=1).mean())
 
 
-def oracle_rollout_rate(prob, frames, rods):
+def oracle_rollout_rate(prob, frames, rods, sil=False):
     """FP64 oracle forward + reverse-mode backward on `rods` rods of the workload; returns
-    (rod-vertex-steps/s, seconds)."""
+    (rod-vertex-steps/s, seconds).  sil: the loss is the silhouette loss against the oracle's
+    own masks of the target curves (rendered before the clock starts)."""
     import numpy as np
     import torch
     from oracle import OracleSim
+    from oracle import silhouette as S
     sub = prob.subset(rods, frames=frames)
+    if sil:
+        cams = sysid_cameras()
+        masks = []
+        for a, b in zip(sub.vert_off[:-1], sub.vert_off[1:]):
+            xt = torch.tensor(np.asarray(sub.target[a:b], np.float64))
+            masks.append(np.stack([(S.render(xt, c, SIL_HW, SIL_HW, SIL_TAU, float(sub.radius[0])) > 0.5).numpy()
+                                   for c in cams]).astype(np.float64))
     t0 = time.perf_counter()
     act = torch.tensor(sub.actions[:frames], requires_grad=True)
     x0 = torch.tensor(sub.x0, requires_grad=True)
@@ -186,7 +211,11 @@ def oracle_rollout_rate(prob, frames, rods):
     sim.set_state(x0, torch.tensor(sub.v0), torch.tensor(sub.theta0), torch.tensor(sub.omega0))
     sim.step(act, frames, diff=True)
     x = sim.get_state(as_numpy=False)["x"]
-    L = ((x - torch.tensor(sub.target)) ** 2).sum(1).mean() if sub.target is not None else x[:, 2].mean()
+    if sil:
+        L = sum(S.silhouette_loss(x[a:b], cams, masks[k], SIL_TAU, float(sub.radius[k]))
+                for k, (a, b) in enumerate(zip(sub.vert_off[:-1], sub.vert_off[1:])))
+    else:
+        L = ((x - torch.tensor(sub.target)) ** 2).sum(1).mean() if sub.target is not None else x[:, 2].mean()
     torch.autograd.grad(L, [act, x0])
     dt = time.perf_counter() - t0
     units = float(np.sum(sub.n_verts)) * frames
@@ -203,8 +232,9 @@ def run_reference(args, rank, ws):
     prob, desc, R, _ = make_workload(short, 0)
     rates = []
     rate_fn = oracle_population_rate if args.workload == "cmaes" else oracle_rollout_rate
+    kw = {"sil": True} if args.workload == "sysid" else {}
     for i in range(args.warmup + args.steps):
-        r, dt = rate_fn(prob, 2, [0, 1])
+        r, dt = rate_fn(prob, 2, [0, 1], **kw)
         if i >= args.warmup:
             rates.append((r, dt))
     value = sum(r for r, _ in rates) / len(rates)
@@ -212,6 +242,7 @@ def run_reference(args, rank, ws):
     cores = torch.get_num_threads()
     sample = (f"rods 0 and 1 ({int(prob.n_verts[0])} and {int(prob.n_verts[1])} vertices) x 2 frames per step, "
               + ("FP64 forward + crossing sum and repulsion scores" if args.workload == "cmaes"
+                 else "FP64 forward + silhouette loss + autograd backward" if args.workload == "sysid"
                  else "FP64 forward + autograd backward"))
     line = {"impl": "reference", "metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -225,7 +256,8 @@ def run_reference(args, rank, ws):
 # --------------------------------------------------------------------------- native arm
 # rods, vertices per rod, frames of each workload (the configurations' own sizes)
 WORKLOADS = {"trajopt": (4096, 128, 2000), "batching": (1024, None, 1000), "selfcontact": (4096, 200, 300),
-             "diff": (256, 64, 500), "cmaes": (400, 128, 2000)}
+             "diff": (256, 64, 500), "cmaes": (400, 128, 2000), "sysid": (256, 64, 500)}
+SIL_HW, SIL_TAU = 256, 0.5  # system identification: two 256 x 256 cameras, edge softness in pixels
 REPULSION_WEIGHT = 1e3     # the Unknotting penalty's weight against the crossing sum
 
 
@@ -244,6 +276,11 @@ def make_workload(args, rank):
         prob = inputs.batching(n_rods=R, frames=F, seed=1000 + rank)
         desc = (f"batching: {R} rods x 16..256 vertices, 0.3..2 m, E 1e4..1e8 Pa, plastic, 2 grippers, ground, "
                 f"{F} frames, per-rod substeps")
+    elif w == "sysid":
+        prob = inputs.diff(n_rods=R, frames=F, seed=2000 + rank, n=N)
+        desc = (f"sysid: {R} rods x {N} vertices, rope/plastic wire halves, 2 grippers, ground, {F} frames; "
+                f"silhouette loss of the final state from 2 cameras of {SIL_HW} x {SIL_HW} px against binary "
+                f"masks of the target curves, gradient to the material")
     elif w == "cmaes":
         prob = inputs.cmaes(pop=R, frames=F, seed=5000 + rank, n=N)
         desc = (f"cmaes: one CMA-ES generation of Unknotting, population {R} x {N} vertices (one knotted rope, "
@@ -279,8 +316,19 @@ def run_native(args, rank, ws):
     mean_z = torch.zeros(V, 4, device=dev)
     mean_z[:, 2] = 1.0 / V
 
+    sil = args.workload == "sysid"
+    if sil:
+        cams = torch.tensor(sysid_cameras(), dtype=torch.float32, device=dev)
+        blank = torch.zeros(R, 2, SIL_HW, SIL_HW, dtype=torch.uint8, device=dev)
+        _, _, img = sim.silhouette(target, cams, blank, SIL_TAU, grad=False, render=True)
+        masks = (img > 0.5).to(torch.uint8)
+        del img, blank
+
     def loss_grad(x):
-        """dL/dx_T: mean squared distance to the target curve, or the mean height without one."""
+        """dL/dx_T: the silhouette loss for system identification, else the mean squared
+        distance to the target curve, or the mean height without one."""
+        if sil:
+            return sim.silhouette(x, cams, masks, SIL_TAU)[1]
         if prob.target is not None:
             return (2.0 / V) * (x - target)
         return mean_z
@@ -356,6 +404,7 @@ def run_native(args, rank, ws):
     h_gact = torch.empty(F, R, 2, 6).pin_memory()
     h_loss = torch.empty(1).pin_memory()
     h_scores = torch.empty(2, R).pin_memory()
+    h_masks = masks.cpu().pin_memory() if sil else None
     def e2e_step():
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -376,9 +425,15 @@ def run_native(args, rank, ws):
         sim.begin_rollout(F)
         sim.step(d_acts, F)
         x, _, _ = sim.get_state()
-        loss = ((x - tg)[:, :3] ** 2).sum(1).mean() if prob.target is not None else x[:, 2].mean()
-        g = sim.backward(dL_dx=(2.0 / V) * (x - tg) if prob.target is not None else mean_z,
-                         want=("actions", "material", "x0"))
+        if sil:
+            d_masks = h_masks.to(dev, non_blocking=True)
+            qs, gs, _ = sim.silhouette(x, cams, d_masks, SIL_TAU)
+            loss = qs.sum()
+            g = sim.backward(dL_dx=gs, want=("actions", "material", "x0"))
+        else:
+            loss = ((x - tg)[:, :3] ** 2).sum(1).mean() if prob.target is not None else x[:, 2].mean()
+            g = sim.backward(dL_dx=(2.0 / V) * (x - tg) if prob.target is not None else mean_z,
+                             want=("actions", "material", "x0"))
         h_gact.copy_(g["actions"], non_blocking=True)
         h_loss.copy_(loss.reshape(1), non_blocking=True)
         e1.record(stream)
@@ -393,6 +448,8 @@ def run_native(args, rank, ws):
         d2h = h_scores.numel() * 4
     else:
         h2d = h_acts.numel() * 4 + sum(t.numel() * 4 for t in h_state) + h_target.numel() * 4
+        if sil:
+            h2d += h_masks.numel()
         d2h = h_gact.numel() * 4 + 4
 
     # roofline of the dominant kernel (the backward): algorithmic FP32 operations per launch
@@ -438,10 +495,12 @@ def run_native(args, rank, ws):
     cpu = None
     if rank == 0:
         rate_fn = oracle_population_rate if pop else oracle_rollout_rate
-        rate, dt = rate_fn(prob, 1, [0, 1])
+        kw = {"sil": True} if sil else {}
+        rate, dt = rate_fn(prob, 1, [0, 1], **kw)
         frames = max(1, min(20, int(args.cpu_seconds / max(dt, 1e-3))))
-        rate, dt = rate_fn(prob, frames, [0, 1])
-        what = "crossing sum and repulsion scores" if pop else "autograd backward"
+        rate, dt = rate_fn(prob, frames, [0, 1], **kw)
+        what = ("crossing sum and repulsion scores" if pop else
+                "silhouette loss + autograd backward" if sil else "autograd backward")
         cpu = {"value": rate, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
                "sample": f"2 rods x {N} vertices x {frames} frames of the same workload, FP64 forward + "
                          f"{what}, {dt:.1f} s"}

@@ -248,6 +248,31 @@ enum {
 dlo_status dlo_loss(dlo_ctx* ctx, int kind, const float* x, const float* aux, int m, const float* g, float* q,
                     float* dL_dx);
 
+/* System-identification loss (Sec. 5, "System Identification": the pixel-wise projection error
+ * between the simulated rope and a camera's binary mask, back-propagated to the material).
+ * Reading: a soft silhouette.  Each edge is a capsule of radius rho_e = (rho_a + rho_b) / 2,
+ * rho = fx r / Z the projected rod radius at an endpoint; a pixel centre p at signed distance
+ * s_e(p) = dist(p, projected segment) - rho_e from it is covered with sigma(-s_e / tau), and
+ * its occupancy is o(p) = 1 - prod_e (1 - sigma(-s_e(p) / tau)).  Q_b = mean over cameras and
+ * pixels of (o - mask)^2.  Edges with an endpoint at Z <= 1e-3 (at or behind the camera plane)
+ * are not drawn.
+ *   x       [V][4] device positions
+ *   cams    [n_cams][16] device floats per pinhole camera: fx, fy, cx, cy (pixels), then the
+ *           world-to-camera rotation R (row major) and translation t: X_cam = R x + t,
+ *           u = fx X/Z + cx, v = fy Y/Z + cy; pixel (i, j) is column i, row j, centre
+ *           (i + 0.5, j + 0.5)
+ *   masks   [B][n_cams][height][width] device bytes, nonzero = rope
+ *   tau     edge softness in pixels (> 0)
+ *   g, q, dL_dx as for dlo_loss (L = sum_b g_b Q_b)
+ *   render  [B][n_cams][height][width] device floats: the soft silhouettes o (NULL = not wanted)
+ * Grows a context workspace of B * height * width floats.  Enqueued on the context's stream,
+ * deterministic.  Errors: DLO_ERR_INVALID_ARG for a missing or unaligned array, no camera,
+ * more than 2^24 pixels, tau <= 0 or rods of more than 256 vertices; DLO_ERR_OOM when the
+ * workspace cannot grow. */
+dlo_status dlo_loss_silhouette(dlo_ctx* ctx, const float* x, const float* cams, int n_cams, int height, int width,
+                               const unsigned char* masks, float tau, const float* g, float* q, float* dL_dx,
+                               float* render);
+
 enum {
     DLO_Q_SUBSTEPS = 1,      /* int [B]: substeps per frame of each rod */
     DLO_Q_STATUS = 2,        /* unsigned [B]: status bits (1 non-finite, 2 pair overflow) */

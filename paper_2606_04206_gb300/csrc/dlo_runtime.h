@@ -70,6 +70,9 @@ struct dlo_ctx {
     // plain comparator workspace
     void* pl_mem = nullptr;
     size_t pl_bytes = 0;
+    // silhouette loss: per-pixel weights of one camera image per rod
+    void* sil_mem = nullptr;
+    size_t sil_bytes = 0;
 };
 
 // launch shape and workspace size of the backward for a checkpoint interval (dlo_adjoint.cu)

@@ -93,6 +93,8 @@ def load(path: str | None = None):
     lib.dlo_backward_noalloc.restype = st
     lib.dlo_loss.argtypes = [vp, ip, vp, vp, ip, vp, vp, vp]
     lib.dlo_loss.restype = st
+    lib.dlo_loss_silhouette.argtypes = [vp, vp, vp, ip, ip, ip, vp, C.c_float, vp, vp, vp, vp]
+    lib.dlo_loss_silhouette.restype = st
     lib.dlo_query.argtypes = [vp, ip, vp]
     lib.dlo_query.restype = st
     lib.dlo_status_string.argtypes = [st]
@@ -354,6 +356,24 @@ class DloSim:
         self._check(self.lib.dlo_loss(self.ctx, int(kind), _ptr(x), _ptr(aux), int(m), _ptr(g), _ptr(q), _ptr(gx)),
                     "dlo_loss")
         return q, gx
+
+    def silhouette(self, x, cams, masks, tau=1.0, g=None, grad=True, render=False):
+        """dlo_loss_silhouette: per-rod mean squared difference between the soft silhouettes of
+        the rods seen by pinhole cameras cams [C,16] and binary masks [B,C,H,W] (uint8); returns
+        (q [B], dL/dx [V,4] or None, soft silhouettes [B,C,H,W] or None)."""
+        torch = self.torch
+        assert cams.is_cuda and cams.dtype == torch.float32 and cams.dim() == 2 and cams.shape[1] == 16
+        assert masks.is_cuda and masks.dtype == torch.uint8 and masks.dim() == 4 and masks.shape[0] == self.B
+        C_, H, W = masks.shape[1], masks.shape[2], masks.shape[3]
+        assert cams.shape[0] == C_
+        q = torch.empty(self.B, device=self.device)
+        gx = torch.empty(self.V, 4, device=self.device) if grad else None
+        img = torch.empty(self.B, C_, H, W, device=self.device) if render else None
+        cams, masks = cams.contiguous(), masks.contiguous()
+        self._check(self.lib.dlo_loss_silhouette(self.ctx, _ptr(x), _ptr(cams), int(C_), int(H), int(W), _ptr(masks),
+                                                 float(tau), _ptr(g), _ptr(q), _ptr(gx), _ptr(img)),
+                    "dlo_loss_silhouette")
+        return q, gx, img
 
     def material_tensor(self):
         """The context's per-rod material as a [B, 5] tensor (K_stretch, E_bend, G_twist,
