@@ -100,6 +100,8 @@ typedef struct {
     int    checkpoint_every;/* frames between rollout checkpoints; 0 = chosen by the library */
     size_t hbm_budget;      /* bytes for checkpoints + backward buffers; 0 = 80 GiB */
     int    warps_per_cta;   /* rods per CTA of the persistent kernels; 0 = autotune */
+    int    reaction;        /* 1: dlo_step accumulates the impulse every rigid contact gives each
+                               vertex (read with dlo_reaction); 0: off, no cost */
 } dlo_options;
 
 typedef struct {
@@ -272,6 +274,20 @@ dlo_status dlo_loss(dlo_ctx* ctx, int kind, const float* x, const float* aux, in
 dlo_status dlo_loss_silhouette(dlo_ctx* ctx, const float* x, const float* cams, int n_cams, int height, int width,
                                const unsigned char* masks, float tau, const float* g, float* q, float* dL_dx,
                                float* render);
+
+/* Contact impulses of the rigid coupling (Sec. 3.2; the two-way coupling hands the rigid
+ * body the equal and opposite momentum): for every rod, the impulse sum_substeps m (v' - v)
+ * that each response of the soft rigid contact gave its vertices since the last reset, in
+ * four slots: all planes, all boxes, gripper 0, gripper 1 (N s, world frame).  The rigid
+ * bodies received the opposite impulses.  Only dlo_step accumulates (not dlo_step_plain, not
+ * the backward's recomputation); the context must be created with opt.reaction = 1.
+ *   per_rod    [B][4][4] device floats out (x, y, z, 0 per slot), or NULL; summed over the
+ *              rod's vertices in a fixed order
+ *   per_vertex [V][4][4] device floats out, or NULL: where along the rod the impulses acted
+ *   reset      1: zero the accumulators after reading
+ * Enqueued on the context's stream.  Errors: DLO_ERR_STATE if the context was created without
+ * opt.reaction; DLO_ERR_INVALID_ARG for unaligned outputs. */
+dlo_status dlo_reaction(dlo_ctx* ctx, float* per_rod, float* per_vertex, int reset);
 
 enum {
     DLO_Q_SUBSTEPS = 1,      /* int [B]: substeps per frame of each rod */

@@ -567,15 +567,24 @@ class OracleSim:
             vr2 = vn2[..., None] * nrm + sc[..., None] * vt
             return torch.where(act[..., None], v + f[..., None] * (vr2 - vr), v)
 
+        acc = G.get("react")
+
+        def track(slot, v_before, v_after):
+            # impulse m (v' - v) the response gave each vertex (Sec. 3.2: the rigid body gets
+            # the opposite); a diagnostic, kept out of any autograd graph
+            if acc is not None:
+                acc[:, :, slot] += (R["mass"][..., None] * (v_after - v_before)).detach()
+            return v_after
+
         zero = torch.zeros_like(v)
         allm = torch.ones_like(free)
         for pl in p.planes:
             n = torch.as_tensor(pl[:3], dtype=self.dtype)
             sdf, nrm = sdf_plane(x, n, float(pl[3]))
-            v = respond(v, sdf, nrm, zero, allm)
+            v = track(0, v, respond(v, sdf, nrm, zero, allm))
         for bx in p.boxes:
             sdf, nrm = sdf_box(x, torch.as_tensor(bx[:3], dtype=self.dtype), torch.as_tensor(bx[3:], dtype=self.dtype))
-            v = respond(v, sdf, nrm, zero, allm)
+            v = track(1, v, respond(v, sdf, nrm, zero, allm))
         for g in range(2):
             on = (G["ngrip"] > g)
             if not bool(on.any()):
@@ -585,7 +594,7 @@ class OracleSim:
             b = p0[:, g] + ax * p.grip_half_len
             sdf, nrm = sdf_capsule(x, a[:, None], b[:, None], p.grip_radius)
             vrig = vp[:, g, None] + cross(wv[:, g, None].expand(x.shape), x - p0[:, g, None])
-            v = respond(v, sdf, nrm, vrig, on[:, None].expand(free.shape))
+            v = track(2 + g, v, respond(v, sdf, nrm, vrig, on[:, None].expand(free.shape)))
         return v
 
     def inext_sweep(self, G, xs, col):
@@ -711,6 +720,22 @@ class OracleSim:
         return torch.stack(outs)
 
     # ------------------------------------------------------------------ diagnostics
+    def track_reaction(self):
+        """Start (or restart) accumulating the rigid-contact impulses per vertex in four slots:
+        planes, boxes, gripper 0, gripper 1."""
+        for G in self.groups:
+            G["react"] = torch.zeros(len(G["ids"]), G["N"], 4, 3, dtype=self.dtype)
+
+    def reaction(self):
+        """(per rod [B, 4, 3], per vertex [V, 4, 3]) impulses accumulated since track_reaction."""
+        B, V = self.p.batch, int(self.vo[-1])
+        per_v = np.zeros((V, 4, 3))
+        for G in self.groups:
+            for i, b in enumerate(G["ids"]):
+                per_v[self.vo[b]:self.vo[b + 1]] = G["react"][i].numpy()
+        per_rod = np.stack([per_v[self.vo[b]:self.vo[b + 1]].sum(0) for b in range(B)])
+        return per_rod, per_v
+
     def energies(self):
         """Per-rod (kinetic incl. twist, elastic, gravitational) energies of the current state."""
         out = np.zeros((self.p.batch, 3))

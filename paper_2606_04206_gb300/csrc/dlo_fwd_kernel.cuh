@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
             g.sync();
             bool ovf = false;
             const int np = run_frame<NV, CONTACT, TPR, true>(P.scene, P.KIN, P.ES, R, s, g, nsub, h, ovf,
-                                                       [](int) -> const Rec* { return nullptr; });
+                                                       [](int) -> const Rec* { return nullptr; },
+                                                       P.reaction ? P.reaction + 4LL * R.v0 : nullptr);
             if (ovf) bad |= 2u;
             np_max = max(np_max, np);
             bool nf = false;

@@ -65,6 +65,7 @@ struct FwdParams {
     double* residual;         // [B]
     int* npairs;              // [B]
     uint32_t* pairs_g;        // global spill of pair lists (unused when they fit in smem)
+    float4* reaction;         // [V][4] contact impulse slots (planes, boxes, gripper 0, 1) or null
     SceneDev scene;
 };
 

@@ -46,6 +46,7 @@ struct dlo_ctx {
     double* d_residual = nullptr;
     int* d_npairs = nullptr;
     int* d_counters = nullptr;   // one work-queue head per bucket
+    float4* d_reaction = nullptr;  // [V][4] contact impulse slots when opt.reaction
     std::vector<dlo::Bucket> buckets;
     // with several size classes, each class's kernels run on its own stream, forked from and
     // joined back to `stream` with events, so that the classes' tails overlap

@@ -121,20 +121,33 @@ __device__ __forceinline__ int to_fix(float v, float scale) {
     return __float2int_rn(q);
 }
 
+// Impulse m (v_after - v_before) that one contact response gave the vertex, added to its slot.
+__device__ __forceinline__ void add_impulse(float4* slot, float m, V3<float> vb, V3<float> va) {
+    float4 a = *slot;
+    *slot = make_float4(a.x + m * (va.x - vb.x), a.y + m * (va.y - vb.y), a.z + m * (va.z - vb.z), 0.f);
+}
+
 // Rigid contact of one vertex against the scene and the rod's grippers (Sec. 3.2).
-// sp: the substep's gripper block (see Smem).
+// sp: the substep's gripper block (see Smem).  imp (optional): the vertex's four impulse
+// slots (planes, boxes, gripper 0, gripper 1), to which each active response adds the
+// impulse it gave the vertex of mass m; the rigid body receives the opposite.
 __device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const RodInfo& R, V3<float> x,
-                                                    V3<float> v, const float* sp) {
+                                                    V3<float> v, const float* sp, float4* imp = nullptr,
+                                                    float m = 0.f) {
     bool on;
     for (int k = 0; k < sc.n_planes; ++k) {
         V3<float> n = f3(sc.planes[k]);
         float sdf = dot(x, n) - sc.planes[k].w;
+        const V3<float> vb = v;
         v = contact_respond(v, sdf, n, zf3(), R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
+        if (imp && on) add_impulse(imp, m, vb, v);
     }
     for (int k = 0; k < sc.n_boxes; ++k) {
         V3<float> n;
         float sdf = sdf_box(x, f3(sc.box_c[k]), f3(sc.box_h[k]), n);
+        const V3<float> vb = v;
         v = contact_respond(v, sdf, n, zf3(), R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
+        if (imp && on) add_impulse(imp + 1, m, vb, v);
     }
     for (int g = 0; g < R.ngrip; ++g) {
         const float* o = sp + 32 * g;
@@ -146,7 +159,9 @@ __device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const Rod
         V3<float> vp = f3(o[24], o[25], o[26]);
         V3<float> w = f3(o[27], o[28], o[29]);
         V3<float> vrig = vp + cross(w, x - p);
+        const V3<float> vb = v;
         v = contact_respond(v, sdf, n, vrig, R.radius, R.eps, sc.mu_rigid, sc.restitution, on);
+        if (imp && on) add_impulse(imp + 2 + g, m, vb, v);
     }
     return v;
 }
@@ -402,7 +417,7 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
                         const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, float h, int np,
-                        const Rec* rec = nullptr) {
+                        const Rec* rec = nullptr, float4* imp = nullptr) {
     const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
     const bool closed = R.flags & ROD_CLOSED;
     const int nh = closed ? nv : nv - 2;
@@ -485,7 +500,7 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
             V3<float> acc = (-xi4.w) * g + grav - R.cd * f3(vi);
             V3<float> v1 = f3(vi) + h * acc;
             if (rec) rec->v1[i] = f4(v1, 0.f);
-            v2 = rigid_contact(sc, R, xi, v1, s.sp);
+            v2 = rigid_contact(sc, R, xi, v1, s.sp, imp ? imp + 4 * i : nullptr, 1.f / xi4.w);
             d = h * v2;
         } else if (kind >= 2) {
             const float* o = s.sp + 32 * (kind - 2);
@@ -617,11 +632,13 @@ __device__ __forceinline__ void frame_advance(float* F, const float* act, int q)
 // One frame of one rod: candidates (if self-contact), nsub substeps, pose update.  The frame's
 // start pose is s.fp and its actions s.act, both set (and synchronised) by the caller; s.fp
 // holds the end pose on return.  pre(sb) runs before substep sb (after a group barrier), e.g.
-// to store the substep state, and returns the substep's record (or nullptr).
+// to store the substep state, and returns the substep's record (or nullptr).  imp: the rod's
+// impulse slots (4 per vertex) when the contact impulses are being accumulated (inlined
+// substeps only).
 template <int NV, bool CONTACT, int TPR, bool INLINE, class PreSub>
 __device__ __forceinline__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
                          const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int nsub, float h, bool& ovf,
-                         PreSub pre) {
+                         PreSub pre, float4* imp = nullptr) {
     int np = 0;
     if (CONTACT && (R.flags & ROD_SELF)) np = broad_phase<NV, CONTACT, TPR>(R, s, g, (R.flags & ROD_CLOSED) != 0, ovf);
     const float inv_dt = 1.f / sc.dt;
@@ -632,7 +649,7 @@ __device__ __forceinline__ int run_frame(const SceneDev& sc, const float4* __res
             substep_pose(s.fp, s.act, g.tid, (float)sb / (float)nsub, (float)(sb + 1) / (float)nsub, sb == 0, inv_dt,
                          s.sp);
         if (INLINE)
-            substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec);
+            substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec, imp);
         else
             substep_call<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec);
     }

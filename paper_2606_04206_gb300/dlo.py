@@ -48,7 +48,8 @@ class Options(C.Structure):
     _fields_ = [("dt", C.c_float), ("n_iter_pbd", C.c_int), ("substeps_min", C.c_int), ("gravity", C.c_float),
                 ("mu_self", C.c_float), ("mu_rigid", C.c_float), ("restitution", C.c_float),
                 ("eps_soft", C.c_float), ("contact_margin", C.c_float), ("self_contact", C.c_int),
-                ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t), ("warps_per_cta", C.c_int)]
+                ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t), ("warps_per_cta", C.c_int),
+                ("reaction", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -95,6 +96,8 @@ def load(path: str | None = None):
     lib.dlo_loss.restype = st
     lib.dlo_loss_silhouette.argtypes = [vp, vp, vp, ip, ip, ip, vp, C.c_float, vp, vp, vp, vp]
     lib.dlo_loss_silhouette.restype = st
+    lib.dlo_reaction.argtypes = [vp, vp, vp, ip]
+    lib.dlo_reaction.restype = st
     lib.dlo_query.argtypes = [vp, ip, vp]
     lib.dlo_query.restype = st
     lib.dlo_status_string.argtypes = [st]
@@ -126,7 +129,7 @@ def options_from(prob, **over) -> Options:
     o = Options(dt=prob.dt, n_iter_pbd=prob.n_iter, substeps_min=prob.substeps_min, gravity=prob.gravity,
                 mu_self=prob.mu_self, mu_rigid=prob.mu_rigid, restitution=prob.restitution,
                 eps_soft=prob.eps_soft, contact_margin=prob.contact_margin, self_contact=int(prob.self_contact),
-                checkpoint_every=0, hbm_budget=0, warps_per_cta=0)
+                checkpoint_every=0, hbm_budget=0, warps_per_cta=0, reaction=0)
     for k, v in over.items():
         setattr(o, k, v)
     return o
@@ -374,6 +377,16 @@ class DloSim:
                                                  float(tau), _ptr(g), _ptr(q), _ptr(gx), _ptr(img)),
                     "dlo_loss_silhouette")
         return q, gx, img
+
+    def reaction(self, per_vertex=False, reset=False):
+        """dlo_reaction: the contact impulses the rigid primitives gave each rod since the last
+        reset, [B, 4, 3] (planes, boxes, gripper 0, gripper 1), and per vertex [V, 4, 3] if asked.
+        The context must be created with reaction=1."""
+        torch = self.torch
+        pr = torch.empty(self.B, 4, 4, device=self.device)
+        pv = torch.empty(self.V, 4, 4, device=self.device) if per_vertex else None
+        self._check(self.lib.dlo_reaction(self.ctx, _ptr(pr), _ptr(pv), int(reset)), "dlo_reaction")
+        return pr[..., :3], (pv[..., :3] if per_vertex else None)
 
     def material_tensor(self):
         """The context's per-rod material as a [B, 5] tensor (K_stretch, E_bend, G_twist,
