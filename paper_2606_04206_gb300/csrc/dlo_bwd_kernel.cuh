@@ -21,7 +21,7 @@ namespace dlo {
 constexpr int kBwdMaxThreads = 256;   // per CTA (register budget of the backward kernel)
 
 __host__ __device__ constexpr size_t bwd_smem_bytes(int NV, bool contact) {
-    return rod_smem_bytes(NV, contact) + (size_t)(10 * NV) * 16;
+    return rod_smem_bytes(NV, contact) + (size_t)(10 * NV + 20) * 16;
 }
 
 // ------------------------------------------------------------------ small helpers
@@ -45,6 +45,42 @@ __device__ __forceinline__ V3<float> jl_t(V3<float> phi, V3<float> lam) {
     }
     V3<float> c = cross(phi, lam);
     return lam - A * c + B * cross(phi, c);
+}
+
+// The linear maps that carry gripper q's substep pose cotangents to the frame's actions and
+// start pose (see the pose block of reverse_substep), per gripper: M0 = exp(c0 dphi),
+// M1 = exp(c1 dphi), c0 J_l(c0 dphi)^T and c1 J_l(c1 dphi)^T (row major, 9 floats each).  Thread
+// t < 4 ngrip builds matrix t % 4 of gripper t / 4, so the eight run side by side.  With
+// phi = c dphi: J_l(phi)^T = I - A [phi]x + B [phi]x^2, the coefficients of jl_t above.
+__device__ __forceinline__ void pose_rev_mat(const float* act, int t, float c0, float c1, float* pm) {
+    const int q = t >> 2, m = t & 3;
+    const float c = (m & 1) ? c1 : c0;
+    const V3<float> phi = c * f3(act[6 * q + 3], act[6 * q + 4], act[6 * q + 5]);
+    float* o = pm + 36 * q + 9 * m;
+    if (m < 2) {
+        const M3 M = expmap(phi);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) o[k] = M.m[k];
+        return;
+    }
+    const float t2 = dot(phi, phi);
+    float A, B;
+    if (t2 < 1e-8f) {
+        A = 0.5f - t2 / 24.f;
+        B = 1.f / 6.f - t2 / 120.f;
+    } else {
+        const float th = sqrtf(t2), sh = sinf(0.5f * th);
+        A = 2.f * sh * sh / t2;
+        B = (th - sinf(th)) / (t2 * th);
+    }
+    const float p[3] = {phi.x, phi.y, phi.z};
+    const float d = 1.f - B * t2;
+    // [phi]x = [[0, -z, y], [z, 0, -x], [-y, x, 0]]
+    const float K[9] = {0.f, -phi.z, phi.y, phi.z, 0.f, -phi.x, -phi.y, phi.x, 0.f};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) o[3 * r + k] = c * ((r == k ? d : 0.f) - A * K[3 * r + k] + B * p[r] * p[k]);
 }
 
 // The value part of a hinge evaluated on dual numbers (the float evaluation, up to rounding).
@@ -125,6 +161,7 @@ __device__ __forceinline__ bool fric_pair(const V3<T>* P, const V3<T>* Vv, const
 template <int NV, bool CONTACT>
 struct AdjArrays {
     float4 *LX, *LD, *LV, *LE, *LT, *LK, *LP0, *LG, *V1, *DF;
+    float* PM;   // per gripper (36): the substep's M0, M1, c0 J_l(c0 dphi)^T, c1 J_l(c1 dphi)^T (row major)
     __device__ AdjArrays(float4* a) {
         LX = a;
         LD = a + NV;
@@ -136,6 +173,7 @@ struct AdjArrays {
         LG = a + 7 * NV;
         V1 = a + 8 * NV;
         DF = a + 9 * NV;
+        PM = reinterpret_cast<float*>(a + 10 * NV);
     }
 };
 
@@ -519,6 +557,36 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         a.LG[i] = lg;
     }
     g.sync();
+    // ---- pose cotangents of this substep -> frame-start pose and the frame's actions (pa is
+    // complete after B5; folding it here ends its registers' life before B8 and B7).  Only
+    // grasped vertices and vertices touching a gripper have any; the maps are a.PM's.
+    const float idt = 1.f / sc.dt;
+    for (int q = 0; q < R.ngrip; ++q) {
+        const V3<float> ps0 = get3(pa.ps0, q), ps1 = get3(pa.ps1, q), vp = get3(pa.vp, q);
+        const V3<float> ph0 = get3(pa.phs0, q), ph1 = get3(pa.phs1, q), w = get3(pa.w, q);
+        const bool nz = ps0.x != 0.f || ps0.y != 0.f || ps0.z != 0.f || ps1.x != 0.f || ps1.y != 0.f ||
+                        ps1.z != 0.f || vp.x != 0.f || vp.y != 0.f || vp.z != 0.f || ph0.x != 0.f ||
+                        ph0.y != 0.f || ph0.z != 0.f || ph1.x != 0.f || ph1.y != 0.f || ph1.z != 0.f ||
+                        w.x != 0.f || w.y != 0.f || w.z != 0.f;
+        if (!nz) continue;
+        const float* pm = a.PM + 36 * q;
+        add3(lpf, q, ps0 + ps1);
+        const V3<float> gdp = c0 * ps0 + c1 * ps1 + idt * vp;
+        const V3<float> gdr = mul_rm(pm + 18, ph0) + mul_rm(pm + 27, ph1) + idt * w;
+        ga[6 * q] += gdp.x;
+        ga[6 * q + 1] += gdp.y;
+        ga[6 * q + 2] += gdp.z;
+        ga[6 * q + 3] += gdr.x;
+        ga[6 * q + 4] += gdr.y;
+        ga[6 * q + 5] += gdr.z;
+        const V3<float> m0 = f3(pm[0] * ph0.x + pm[3] * ph0.y + pm[6] * ph0.z,
+                                pm[1] * ph0.x + pm[4] * ph0.y + pm[7] * ph0.z,
+                                pm[2] * ph0.x + pm[5] * ph0.y + pm[8] * ph0.z);
+        const V3<float> m1 = f3(pm[9] * ph1.x + pm[12] * ph1.y + pm[15] * ph1.z,
+                                pm[10] * ph1.x + pm[13] * ph1.y + pm[16] * ph1.z,
+                                pm[11] * ph1.x + pm[14] * ph1.y + pm[17] * ph1.z);
+        add3(lphif, q, m0 + m1);
+    }
     // ---- B8: per edge, reverse of the new reference-frame base and stretching second order
     for (int j = g.tid; j < ne; j += TPR) {
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
@@ -608,24 +676,6 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         a.LK[i] = make_float4(lk0, lk1, 0.f, 0.f);
     }
     g.sync();
-    // ---- pose cotangents of this substep -> frame-start pose and the frame's actions
-    const float idt = 1.f / sc.dt;
-    for (int q = 0; q < R.ngrip; ++q) {
-        const V3<float> dphi = f3(s.act[6 * q + 3], s.act[6 * q + 4], s.act[6 * q + 5]);
-        const V3<float> ps = get3(pa.ps0, q) + get3(pa.ps1, q);
-        add3(lpf, q, ps);
-        const V3<float> gdp = c0 * get3(pa.ps0, q) + c1 * get3(pa.ps1, q) + idt * get3(pa.vp, q);
-        const V3<float> gdr = c0 * jl_t(c0 * dphi, get3(pa.phs0, q)) + c1 * jl_t(c1 * dphi, get3(pa.phs1, q)) +
-                              idt * get3(pa.w, q);
-        ga[6 * q] += gdp.x;
-        ga[6 * q + 1] += gdp.y;
-        ga[6 * q + 2] += gdp.z;
-        ga[6 * q + 3] += gdr.x;
-        ga[6 * q + 4] += gdr.y;
-        ga[6 * q + 5] += gdr.z;
-        const M3 M0 = expmap(c0 * dphi), M1 = expmap(c1 * dphi);
-        add3(lphif, q, mulT(M0, get3(pa.phs0, q)) + mulT(M1, get3(pa.phs1, q)));
-    }
 }
 
 // ------------------------------------------------------------------ the backward kernel
@@ -738,7 +788,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                 }
                 g.sync();
                 Rec recs;
-                const int np = run_frame<NV, CONTACT, TPR, false>(
+                const int np = run_frame<NV, CONTACT, TPR, true>(
                     sc, P.KIN, P.ES, R, s, g, nsub, h, ovf, [&](int sb) -> const Rec* {
                         float4* e3 = L3 + (size_t)sb * E3;
                         save_state<NV, CONTACT, TPR>(e3, R, g, s);
@@ -752,6 +802,9 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
                     const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
                     // the substep's gripper block (read after the barrier below)
                     if (g.tid < R.ngrip) substep_pose(s.f0, s.act, g.tid, c0, c1, sb == 0, 1.f / sc.dt, s.sp);
+                    // the reverse's pose maps, on other threads (another warp where there is one)
+                    constexpr int PT = TPR > 32 ? 32 : 2;
+                    if (g.tid >= PT && g.tid < PT + 4 * R.ngrip) pose_rev_mat(s.act, g.tid - PT, c0, c1, a.PM);
                     // the substep's start state and recorded intermediates
                     const float4* e3 = L3 + (size_t)sb * E3;
                     load_state<NV, CONTACT, TPR>(e3, R, g, s);

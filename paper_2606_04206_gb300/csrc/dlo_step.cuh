@@ -578,8 +578,9 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
 }
 
 
-// The substep inlined (forward kernel) and as one shared out-of-line copy (the backward
-// kernel calls it from several places; one copy keeps its instruction footprint small).
+// The substep inlined (the forward kernel, and the backward's per-frame recompute with
+// records, where a call costs more than the larger code) and as one out-of-line copy (the
+// backward's replay of the frames between two checkpoints).
 template <int NV, bool CONTACT, int TPR>
 __device__ __noinline__ void substep_call(const SceneDev& sc, const float4* __restrict__ KIN,
                                           const float2* __restrict__ ES, const RodInfo& R, Smem<NV, CONTACT>& s,
