@@ -317,6 +317,74 @@ def test_momentum_conserved_through_self_contact(inclined):
     assert max(errs) < bound, errs
 
 
+# ---------------------------------------------------------------------- self-contact friction
+
+@pytest.mark.parametrize("seed", range(6))
+def test_self_contact_friction_obeys_coulomb(seed):
+    """Self-contact friction (App. A.1: Coulomb friction whose normal impulse is approximated
+    from the penetration depth d; reading O15 takes the normal velocity change as d/h).
+    Physical checks on one crossing pair with random inverse masses and velocities:
+    the impulse is tangential, so the normal relative velocity is unchanged; it opposes
+    sliding and never reverses it; its size is the Coulomb bound mu d/h while sliding
+    continues, and sliding stops exactly when that bound covers the tangential speed; it
+    conserves linear momentum and does not add kinetic energy."""
+    rng = np.random.default_rng(100 + seed)
+    # edge 1 along x at z = 0; edge 6 crosses above it along y at a height below 2r, at
+    # random points of both edges (so that the barycentric weights differ from 1/2)
+    zc = rng.uniform(0.4, 0.95) * 2 * R_
+    xc, ya = rng.uniform(0.003, 0.017), rng.uniform(0.003, 0.017)
+    x = np.array([[-0.02, 0, 0], [0, 0, 0], [0.02, 0, 0], [0.03, 0.01, 0.01], [0.02, 0.03, 0.01],
+                  [xc, ya + 0.01, zc], [xc, ya, zc], [xc + 0.001, ya - 0.02, zc], [xc + 0.001, ya - 0.04, zc]])
+    p = inputs.custom([x], K=1e5, E=1e4, self_contact=True)
+    sim = OracleSim(p)
+    G = dict(sim.groups[0])
+    R = dict(G["R"])
+    R["w"] = torch.as_tensor(rng.uniform(0.5, 2.0, size=(1, len(x))) * 1e3, dtype=F64)
+    G["R"] = R
+    xs = torch.as_tensor(x, dtype=F64)[None]
+    _, infos = sim.contact_sweep(G, xs, [torch.tensor([[1, 6]])])
+    I = infos[0]
+    assert bool(I["act"][0])
+    s_, u_, n_, d = float(I["s"][0]), float(I["u"][0]), I["n"][0].numpy(), float(I["d"][0])
+    h = 2e-4
+    mu = p.mu_self
+    idx = [1, 2, 6, 7]
+    bary = np.array([1 - s_, s_, -(1 - u_), -u_])
+    m = 1.0 / R["w"][0].numpy()
+
+    def rel(v):
+        return sum(b * v[i] for b, i in zip(bary, idx))
+
+    for trial in range(8):
+        v = rng.normal(size=(len(x), 3)) * 0.05
+        # relative tangential speed well above or well below the Coulomb bound mu d / h
+        vt_target = mu * d / h * (rng.uniform(1.5, 4.0) if trial % 2 == 0 else rng.uniform(0.1, 0.7))
+        vr = rel(v)
+        vt = vr - np.dot(vr, n_) * n_
+        # rescale the tangential part of the relative velocity by moving vertex 2 (weight s)
+        v[2] += (vt_target / np.linalg.norm(vt) - 1.0) * vt / s_
+        vr = rel(v)
+        vt = vr - np.dot(vr, n_) * n_
+        assert np.linalg.norm(vt) == pytest.approx(vt_target, rel=1e-9)
+        out = sim.self_friction(G, torch.as_tensor(v, dtype=F64)[None], infos, h)[0].numpy()
+        vr2 = rel(out)
+        vt2 = vr2 - np.dot(vr2, n_) * n_
+        # tangential impulse: normal relative velocity unchanged
+        assert np.dot(vr2, n_) == pytest.approx(np.dot(vr, n_), abs=1e-12)
+        # opposes sliding without reversing it: vt2 = c vt with 0 <= c <= 1
+        c = np.dot(vt2, vt) / np.dot(vt, vt)
+        assert np.linalg.norm(vt2 - c * vt) < 1e-12 * np.linalg.norm(vt)
+        assert -1e-12 <= c <= 1.0 + 1e-12
+        dvt = np.linalg.norm(vt - vt2)
+        if np.linalg.norm(vt) > mu * d / h:      # sliding: the Coulomb bound is reached
+            assert dvt == pytest.approx(mu * d / h, rel=1e-9)
+        else:                                     # sticking: the relative sliding stops
+            assert np.linalg.norm(vt2) < 1e-12
+        # momentum conserved, no kinetic energy added
+        np.testing.assert_allclose((m[:, None] * (out - v)).sum(0), 0.0, atol=1e-15)
+        assert (m * (out ** 2).sum(1)).sum() <= (m * (v ** 2).sum(1)).sum() * (1 + 1e-12)
+
+
 # ---------------------------------------------------------------------- P8 plasticity
 
 def test_plastic_return_reaches_yield_surface():
