@@ -44,7 +44,7 @@ FLOPS_BWD_PER_VS = 3650.0
 # DRAM bytes (read + write) of bwd_kernel per rod-frame of the 128-vertex self-contact
 # workload, from one ncu capture of a 304-rod x 50-frame case of it (its recompute scratch
 # grows with rod-frames; profiles/fwd_bwd_kernels_trajopt_304x128x50.md)
-BWD_DRAM_BYTES_PER_ROD_FRAME = (264.885760e6 + 1051.931e6) / (304 * 50)
+BWD_DRAM_BYTES_PER_ROD_FRAME = (209.585664e6 + 861.888e6) / (304 * 50)
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 

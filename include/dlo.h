@@ -110,7 +110,8 @@ typedef struct {
     void* user;
 } dlo_allocator;
 
-/* Create a context.  n_verts[B] >= 2 and <= 256, mat[B], x_rest [V][3] host: the rest shape
+/* Create a context for 1 <= B <= 2^24 rods (an empty batch is an argument error).
+ * n_verts[B] >= 2 and <= 256, mat[B], x_rest [V][3] host: the rest shape
  * (rest lengths, masses and grasped vertices are taken from it; open rods rest straight,
  * loops rest as a planar circle of the same length).  The state is set to the rest shape
  * at rest.  cuda_stream may be NULL (legacy default stream).  alloc may be NULL.

@@ -83,39 +83,6 @@ __device__ __forceinline__ void pose_rev_mat(const float* act, int t, float c0, 
         for (int k = 0; k < 3; ++k) o[3 * r + k] = c * ((r == k ? d : 0.f) - A * K[3 * r + k] + B * p[r] * p[k]);
 }
 
-// The value part of a hinge evaluated on dual numbers (the float evaluation, up to rounding).
-__device__ __forceinline__ EdgeF<float> edge_vals(const EdgeF<dualf>& E) {
-    EdgeF<float> o;
-    o.t = vals(E.t);
-    o.w0 = vals(E.w0);
-    o.d1r = vals(E.d1r);
-    o.d2r = vals(E.d2r);
-    o.d1 = vals(E.d1);
-    o.d2 = vals(E.d2);
-    o.ell = E.ell.v;
-    o.n1 = E.n1.v;
-    o.c = E.c.v;
-    o.s = E.s.v;
-    return o;
-}
-
-__device__ __forceinline__ HingeF<float> hinge_vals(const HingeF<dualf>& H) {
-    HingeF<float> o;
-    o.a = edge_vals(H.a);
-    o.b = edge_vals(H.b);
-    o.X = vals(H.X);
-    o.kb = vals(H.kb);
-    o.u = vals(H.u);
-    o.cc = H.cc.v;
-    o.y = H.y.v;
-    o.xq = H.xq.v;
-    o.mref = H.mref.v;
-    o.m = H.m.v;
-    o.k0 = H.k0.v;
-    o.k1 = H.k1.v;
-    return o;
-}
-
 // One rigid primitive acting on a vertex velocity (the k-th of planes, boxes, grippers).
 template <class T>
 __device__ __forceinline__ V3<T> prim_respond(int k, const SceneDev& sc, const RodInfo& R, V3<T> x, V3<T> v,
@@ -627,12 +594,31 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         hinge_forward(Hd, lift(f3(s.X0[im]), f3(gm_)), lift(f3(s.X0[i]), f3(gi_)), lift(f3(s.X0[ip]), f3(gp_)),
                       lift(f3(ETa)), lift(f3(EDa)), lift(f3(ETb)), lift(f3(EDb)), mkd(EDa.w, a.LG[ea].w),
                       mkd(EDb.w, a.LG[eb].w), mkd(hg.w));
-        const HingeF<float> Hf = hinge_vals(Hd);   // the hinge itself (for plasticity)
+        const float hk0 = Hd.k0.v, hk1 = Hd.k1.v;   // the hinge's material curvature (for plasticity)
         float kb0 = hg.x, kb1 = hg.y;
         const bool plastic = R.flags & ROD_PLASTIC;
-        const bool yielded = plastic && plastic_update(Hf.k0, Hf.k1, kb0, kb1, R.sy * lbar, R.rc);
+        const bool yielded = plastic && plastic_update(hk0, hk1, kb0, kb1, R.sy * lbar, R.rc);
         dualf e0d = Hd.k0 - kb0, e1d = Hd.k1 - kb1, emd = Hd.m - hg.z;
         dualf gk0 = (R.Bm * il) * e0d, gk1 = (R.Bm * il) * e1d, gmt = (R.beta * il) * emd;
+        gm[1] += (double)il * ((double)e0d.v * e0d.d + (double)e1d.v * e1d.d);
+        gm[2] += (double)il * (double)emd.v * (double)emd.d;
+        // rest curvature: cotangent of the one used (-d gk / d .) plus the carried one
+        float lk0 = a.LK[i].x - gk0.d, lk1 = a.LK[i].y - gk1.d;
+        if (yielded) {
+            const float el0 = hk0 - hg.x, el1 = hk1 - hg.y;
+            const float n = sqrtf(el0 * el0 + el1 * el1), thr = R.sy * lbar;
+            const float g = R.rc * (n - thr) / n;
+            const float kk = R.rc * thr / (n * n * n) * (el0 * lk0 + el1 * lk1);
+            const float le0 = g * lk0 + kk * el0, le1 = g * lk1 + kk * el1;     // cotangent of kappa_el
+            gm[3] += -(double)R.rc * lbar * ((double)el0 * lk0 + (double)el1 * lk1) / n;
+            // The first-order reverse of kappa from seeds (le0, le1) is needed too.  The hinge
+            // reverse is linear in its seeds, so adding them to the derivative part of the
+            // dual seeds makes the reverse below return J^T le on top of the Hessian term.
+            gk0.d += le0;
+            gk1.d += le1;
+            lk0 -= le0;
+            lk1 -= le1;
+        }
         V3<dualf> gxm, gxi, gxp, gtba, gd1ba, gtbb, gd1bb;
         dualf gta, gtb;
         hinge_reverse<dualf, true>(Hd, lift(f3(ETa)), lift(f3(EDa)), lift(f3(ETb)), lift(f3(EDb)), gk0, gk1, gmt,
@@ -646,33 +632,6 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         atomic_add3(&a.LE[ea], ders(gd1ba));
         atomic_add3(&a.LT[eb], ders(gtbb));
         atomic_add3(&a.LE[eb], ders(gd1bb));
-        gm[1] += (double)il * ((double)e0d.v * e0d.d + (double)e1d.v * e1d.d);
-        gm[2] += (double)il * (double)emd.v * (double)emd.d;
-        // rest curvature: cotangent of the one used (-d gk / d .) plus the carried one
-        float lk0 = a.LK[i].x - gk0.d, lk1 = a.LK[i].y - gk1.d;
-        if (yielded) {
-            const float el0 = Hf.k0 - hg.x, el1 = Hf.k1 - hg.y;
-            const float n = sqrtf(el0 * el0 + el1 * el1), thr = R.sy * lbar;
-            const float g = R.rc * (n - thr) / n;
-            const float kk = R.rc * thr / (n * n * n) * (el0 * lk0 + el1 * lk1);
-            const float le0 = g * lk0 + kk * el0, le1 = g * lk1 + kk * el1;     // cotangent of kappa_el
-            gm[3] += -(double)R.rc * lbar * ((double)el0 * lk0 + (double)el1 * lk1) / n;
-            V3<float> fxm, fxi, fxp, ftba, fd1ba, ftbb, fd1bb;
-            float fta, ftb;
-            hinge_reverse<float, true>(Hf, f3(ETa), f3(EDa), f3(ETb), f3(EDb), le0, le1, 0.f, 0.f, fxm, fxi, fxp,
-                                       fta, ftb, &ftba, &fd1ba, &ftbb, &fd1bb);
-            atomic_add3(&a.LX[im], fxm);
-            atomic_add3(&a.LX[i], fxi);
-            atomic_add3(&a.LX[ip], fxp);
-            atomicAdd(&a.LE[ea].w, fta);
-            atomicAdd(&a.LE[eb].w, ftb);
-            atomic_add3(&a.LT[ea], ftba);
-            atomic_add3(&a.LE[ea], fd1ba);
-            atomic_add3(&a.LT[eb], ftbb);
-            atomic_add3(&a.LE[eb], fd1bb);
-            lk0 -= le0;
-            lk1 -= le1;
-        }
         a.LK[i] = make_float4(lk0, lk1, 0.f, 0.f);
     }
     g.sync();

@@ -46,6 +46,7 @@ def _create(lib, nv, mat=None, opt=None, x=None):
 
 def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert _create(lib, [1])[0] == 1                     # too few vertices
+    assert _create(lib, [])[0] == 1                      # an empty batch
     assert _create(lib, [300])[0] == 1                   # above the 256-vertex limit
     bad = dlo.Material(-1, 0.002, 1e5, 1e4, 1e3, 0, 0, 0, 0, 1, 1, 0)
     assert _create(lib, [10], mat=bad)[0] == 1           # negative density
