@@ -2,10 +2,10 @@
 //
 // DLO-Lab (Sec. 3.3) differentiates whole trajectories by caching one state per segment and,
 // for each segment in reverse, re-running the forward simulation before back-propagating.
-// Here the checkpoints live in HBM (written by the forward kernel every K frames) and one warp
-// runs the whole backward of one rod:
+// Here the checkpoints live in HBM (written by the forward kernel every K frames) and one
+// thread group runs the whole backward of one rod:
 //   for each segment, last first: reload its checkpoint, recompute its frames storing the
-//   frame-start states (per-warp scratch); for each frame, last first: recompute it storing
+//   frame-start states (per-rod scratch); for each frame, last first: recompute it storing
 //   the substep-start states; for each substep, last first: recompute it once more recording
 //   its intermediates (velocity before contact, PBD iteration snapshots, displacement before
 //   friction), then apply the vector-Jacobian product of every phase in reverse order.
@@ -144,7 +144,7 @@ struct AdjArrays {
     }
 };
 
-// State snapshot layout in the per-warp scratch: X[NV], V[NV], HG[NV], ED[NV], ET[NV].
+// State snapshot layout in the per-rod scratch: X[NV], V[NV], HG[NV], ED[NV], ET[NV].
 template <int NV, bool C, int TPR>
 __device__ __forceinline__ void save_state(float4* dst, const RodInfo& R, const Grp<TPR>& g, const Smem<NV, C>& s) {
     for (int i = g.tid; i < R.nv; i += TPR) {

@@ -6,7 +6,7 @@
 
 namespace dlo {
 
-// Shared memory of one warp (one rod of at most NV vertices) in the persistent kernels:
+// Shared memory of one rod group (one rod of at most NV vertices) in the persistent kernels:
 // ten float4 arrays of NV (positions, start positions, velocities, base frames + twist,
 // base tangents + rest lengths, hinge state, three per-hinge gradient slots, new reference
 // frames) and, with self-contact, 4 NV pair slots (two float4 of projection data each,

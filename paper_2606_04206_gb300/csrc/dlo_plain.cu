@@ -4,7 +4,7 @@
 // whole state in HBM between phases; the element functions and the operation order are
 // those of the fused substep (dlo_step.cuh), so both follow the same trajectory up to
 // rounding.  Self-contact candidates are found once per frame by brute force over each
-// rod's edge pairs (the same set the fused kernel's spatial hash finds).  It does not record
+// rod's edge pairs (the same set the fused kernel's broad phase finds).  It does not record
 // a rollout for dlo_backward.
 #include <algorithm>
 #include <vector>

@@ -1,4 +1,4 @@
-// dlo_step.cuh -- one rod's frame and substep on one warp, state in shared memory.
+// dlo_step.cuh -- one rod's frame and substep on one thread group, state in shared memory.
 //
 // Shared by the forward kernel and the backward kernel's recomputations.  Per substep
 // (DLO-Lab Sec. 3.1 / 3.2 / App. A.1):
@@ -9,7 +9,8 @@
 //                 kinematic vertices, new reference-frame base
 //   PBD phase     N_C x (red-black inextensibility / strain limit, Jacobi self-collision)
 //   velocity      v = d/h, self-contact Coulomb friction, positions x + d
-// Per frame: self-contact candidates by a per-rod spatial hash, gripper pose update.
+// Per frame: self-contact candidates (every edge pair behind a bounding-sphere filter),
+// gripper pose update.
 #pragma once
 #include "dlo_internal.h"
 #include "dlo_kernels.h"

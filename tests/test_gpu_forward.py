@@ -119,7 +119,7 @@ def test_self_contact_candidates_and_projection_match_oracle():
     acts = actions_dev(p)
     o = oracle_from_device_state(p, sim)
     sim.step(acts[:1].contiguous(), 1)
-    got = sim.query(6)                            # pairs found by the hash at that frame start
+    got = sim.query(6)                            # pairs found by the broad phase at that frame start
     for G, S in zip(o.groups, o.state):
         cand = o.candidates(G, S["x"])
         for i, b in enumerate(G["ids"]):
