@@ -70,6 +70,46 @@ extern "C" void hinge_hvp_host(const float* in, const float* dir, float* out) {
     out[29] = (0.5f * il * em * em).d;              // dU/dbeta
 }
 
+// The backward reverses a yielded hinge in one dual pass: the plastic cotangent (le0, le1) of
+// the material curvature is added to the derivative part of the curvature seeds, which relies
+// on the hinge reverse being linear in its seeds.  in: the 24 hinge inputs of hinge_grad_host,
+// dir: their 24 tangents, seeds: gk0, gk1, gm (value, derivative) and le0, le1.
+// out[0..22]: derivative parts of the folded dual reverse (gxm gxi gxp gtba gd1ba gtbb gd1bb,
+// gta gtb); out[23..45]: the unfolded dual reverse plus the float reverse from (le0, le1).
+extern "C" void hinge_fold_host(const float* in, const float* dir, const float* seeds, float* out) {
+    auto D3 = [&](int k) { return V3<dualf>{mkd(in[k], dir[k]), mkd(in[k + 1], dir[k + 1]), mkd(in[k + 2], dir[k + 2])}; };
+    auto D1 = [&](int k) { return mkd(in[k], dir[k]); };
+    HingeF<dualf> Hd;
+    V3<dualf> tba = D3(9), d1ba = D3(12), tbb = D3(15), d1bb = D3(18);
+    hinge_forward(Hd, D3(0), D3(3), D3(6), tba, d1ba, tbb, d1bb, D1(21), D1(22), D1(23));
+    HingeF<float> Hf;
+    const V3<float> ftba = ld3(in + 9), fd1ba = ld3(in + 12), ftbb = ld3(in + 15), fd1bb = ld3(in + 18);
+    hinge_forward(Hf, ld3(in), ld3(in + 3), ld3(in + 6), ftba, fd1ba, ftbb, fd1bb, in[21], in[22], in[23]);
+    const dualf gk0 = mkd(seeds[0], seeds[1]), gk1 = mkd(seeds[2], seeds[3]), gm = mkd(seeds[4], seeds[5]);
+    const float le0 = seeds[6], le1 = seeds[7];
+    V3<dualf> A[7], B[7];
+    dualf a0, a1, b0, b1;
+    hinge_reverse<dualf, true>(Hd, tba, d1ba, tbb, d1bb, gk0, gk1, gm, mkd(0.f), A[0], A[1], A[2], a0, a1, &A[3], &A[4],
+                               &A[5], &A[6]);
+    dualf f0 = gk0, f1 = gk1;
+    f0.d += le0;
+    f1.d += le1;
+    hinge_reverse<dualf, true>(Hd, tba, d1ba, tbb, d1bb, f0, f1, gm, mkd(0.f), B[0], B[1], B[2], b0, b1, &B[3], &B[4],
+                               &B[5], &B[6]);
+    V3<float> C[7];
+    float c0, c1;
+    hinge_reverse<float, true>(Hf, ftba, fd1ba, ftbb, fd1bb, le0, le1, 0.f, 0.f, C[0], C[1], C[2], c0, c1, &C[3], &C[4],
+                               &C[5], &C[6]);
+    for (int k = 0; k < 7; ++k) {
+        st3(out + 3 * k, ders(B[k]));
+        st3(out + 23 + 3 * k, ders(A[k]) + C[k]);
+    }
+    out[21] = b0.d;
+    out[22] = b1.d;
+    out[44] = a0.d + c0;
+    out[45] = a1.d + c1;
+}
+
 // in: x(3) v(3) vrig(3) sdf_kind (0 plane, 1 box, 2 capsule) params(9) r eps mu rest  out: v'(3), active
 extern "C" void contact_host(const float* in, float* out) {
     V3<float> x = ld3(in), v = ld3(in + 3), vr = ld3(in + 6), n;

@@ -32,6 +32,7 @@ def H():
               "plane_rev_check"):
         getattr(lib, n).argtypes = [C.c_void_p, C.c_void_p]
     lib.hinge_hvp_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.hinge_fold_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     return lib
 
 
@@ -117,6 +118,35 @@ def test_hinge_second_derivatives_match_double_autograd(H):
         hv = torch.autograd.grad(g, z, torch.tensor(dirv))[0].numpy()
         scale = np.abs(hv).max()
         np.testing.assert_allclose(out, hv, atol=5e-4 * scale)
+
+
+def test_yielded_hinge_fold_equals_two_reverse_passes(H):
+    """The backward reverses a yielded hinge in one dual pass, with the plastic cotangent of
+    the curvature (App. A.1 rest-curvature update) added to the derivative part of the
+    curvature seeds.  That equals the dual reverse of the unyielded seeds plus a float
+    reverse from the plastic cotangent, because the hinge reverse is linear in its seeds."""
+    rng = np.random.default_rng(2)
+    for trial in range(50):
+        x, tb, d, th = rand_hinge(rng)
+        vals = np.concatenate([x.ravel(), tb[0], d[0], tb[1], d[1], th, [rng.normal() * 0.3]])
+        dirv = rng.normal(size=24)
+        dirv[9:21] = 0.0          # the bases are constants of the substep (no tangent)
+        dirv[23] = 0.0
+        seeds = rng.normal(size=8)
+        out = call(H.hinge_fold_host, fl(vals), fl(dirv), fl(seeds), n_out=46)
+        folded, two_pass = out[:23], out[23:]
+        scale = max(np.abs(two_pass).max(), 1e-30)
+        np.testing.assert_allclose(folded, two_pass, atol=2e-6 * scale)
+        # without a tangent only first-order terms remain, so the plastic part is of the same
+        # size as the rest: dropping it must change the result
+        zero = np.zeros(24)
+        f1 = call(H.hinge_fold_host, fl(vals), fl(zero), fl(seeds), n_out=46)
+        s1 = max(np.abs(f1[23:]).max(), 1e-30)
+        np.testing.assert_allclose(f1[:23], f1[23:], atol=2e-6 * s1)
+        seeds0 = seeds.copy()
+        seeds0[6:] = 0.0
+        base = call(H.hinge_fold_host, fl(vals), fl(zero), fl(seeds0), n_out=46)[:23]
+        assert np.abs(base - f1[:23]).max() > 1e-2 * s1
 
 
 def test_contact_response_matches_oracle(H):
