@@ -626,3 +626,164 @@ def test_rollout_gradient_matches_central_differences():
         fd = (float(loss(*ap).detach()) - float(loss(*am).detach())) / (2 * hh)
         g = float(grads[ai][idx])
         assert g == pytest.approx(fd, rel=2e-4, abs=1e-8 * max(1.0, abs(fd))), (ai, idx, g, fd)
+
+
+# ---------------------------------------------------------------------- self-contact projection
+
+def crossing_pair(rng):
+    """Nine vertices: edge 1 (vertices 1-2) along x at z = 0, edge 6 (vertices 6-7) crossing
+    it along y at a random height below the contact distance 2r, above random points of both
+    edges (so that the barycentric weights differ from 1/2)."""
+    zc = rng.uniform(0.2, 0.95) * 2 * R_
+    xc, ya = rng.uniform(0.003, 0.017), rng.uniform(0.003, 0.017)
+    return np.array([[-0.02, 0, 0], [0, 0, 0], [0.02, 0, 0], [0.03, 0.01, 0.01], [0.02, 0.03, 0.01],
+                     [xc, ya + 0.01, zc], [xc, ya, zc], [xc + 0.001, ya - 0.02, zc],
+                     [xc + 0.001, ya - 0.04, zc]])
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_self_contact_projection_single_pair(seed):
+    """One self-collision projection (App. A.1) of a single crossing pair with random inverse
+    masses.  With the closest-point parameters (t, u) held at their pre-projection values the
+    separation of the two segment points is linear in the correction, so after one projection
+    they sit exactly r_a + r_b = 2r apart, along the line they were on.  The correction is
+    also the smallest one, in the mass-weighted norm, that moves the two points apart to 2r
+    along that line: the minimum-norm solution of one linear equation, found here by a
+    library least-squares solve.  One vertex held fixed (w = 0) leaves the others to do all
+    of it; a pair already 2r apart does not move."""
+    rng = np.random.default_rng(300 + seed)
+    x = crossing_pair(rng)
+    p = inputs.custom([x], K=1e5, E=1e4, self_contact=True)
+    sim = OracleSim(p)
+    G = dict(sim.groups[0])
+    R = dict(G["R"])
+    w = rng.uniform(0.5, 2.0, size=len(x)) * 1e3
+    if seed % 3 == 2:
+        w[7] = 0.0                                  # a pinned vertex on the b side
+    R["w"] = torch.as_tensor(w[None], dtype=F64)
+    G["R"] = R
+    idx = [1, 2, 6, 7]
+    t_, u_ = (float(a) for a in closest_params(*(torch.as_tensor(x[i], dtype=F64) for i in idx)))
+    beta = np.array([1 - t_, t_, -(1 - u_), -u_])
+    sep0 = sum(b * x[i] for b, i in zip(beta, idx))
+    assert np.linalg.norm(sep0) < 2 * R_
+    out = sim.contact_sweep(G, torch.as_tensor(x, dtype=F64)[None], [torch.tensor([[1, 6]])])[0][0].numpy()
+    dx = out - x
+    # only the pair's four vertices move
+    others = [i for i in range(len(x)) if i not in idx]
+    assert np.abs(dx[others]).max() == 0.0
+    # the two points at the fixed (t, u) are exactly 2r apart, on the line they were on
+    sep1 = sum(b * out[i] for b, i in zip(beta, idx))
+    assert np.linalg.norm(sep1) == pytest.approx(2 * R_, rel=1e-12)
+    n0 = sep0 / np.linalg.norm(sep0)
+    np.testing.assert_allclose(sep1 / np.linalg.norm(sep1), n0, atol=1e-12)
+    # minimum mass-weighted correction: y = sqrt(m) dx minimises |y| subject to
+    # n0 . sum_i beta_i dx_i = 2r - |sep0|  (w = 0 vertices: fixed, left out of the solve)
+    free = [k for k, i in enumerate(idx) if w[i] > 0]
+    row = np.concatenate([beta[k] * n0 / math.sqrt(1.0 / w[idx[k]]) for k in free])[None]
+    y = np.linalg.lstsq(row, np.array([2 * R_ - np.linalg.norm(sep0)]), rcond=None)[0]
+    want = np.zeros((4, 3))
+    for j, k in enumerate(free):
+        want[k] = y[3 * j:3 * j + 3] / math.sqrt(1.0 / w[idx[k]])
+    np.testing.assert_allclose(dx[idx], want, rtol=1e-10, atol=1e-16)
+    # a pair that is already 2r apart stays where it is
+    x2 = x.copy()
+    x2[5:] += (2 * R_ - np.linalg.norm(sep0) + 1e-6) * n0 * np.sign(n0[2])
+    out2 = sim.contact_sweep(G, torch.as_tensor(x2, dtype=F64)[None], [torch.tensor([[1, 6]])])[0][0].numpy()
+    assert np.array_equal(out2, x2)
+
+
+# ---------------------------------------------------------------------- gripper kinematics
+
+def rotvec_matrix(phi):
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_rotvec(np.asarray(phi, np.float64)).as_matrix()
+
+
+@pytest.mark.parametrize("motion", ["translation", "rotation", "both"])
+def test_gripper_kinematics_closed_form(motion):
+    """Grasped vertices are kinematic and follow their gripper rigidly (Sec. 3.2).  Under a
+    constant per-frame action (dp, dphi) the gripper pose after f frames (and at the end of
+    substep s of frame f, c = f + (s + 1)/n) is p0 + c dp and exp(c dphi) R0: repeated
+    rotations about one axis add up.  A grasped vertex therefore sits at
+    p0 + c dp + Rot(c dphi) (x_rest - p0), with Rot from a library rotation-vector map.
+    R0 is a random rotation, so body and world frames differ."""
+    rng = np.random.default_rng({"translation": 1, "rotation": 2, "both": 3}[motion])
+    n = 8
+    x = straight(n, 0.35, z=0.3)                 # 5 cm edges: one vertex per gripper grasped
+    R0 = np.stack([rotvec_matrix(rng.normal(size=3)) for _ in range(2)])
+    # gripper centres 1 cm from the grasped vertices (inside the 1 cm capsule's reach), so the
+    # grasp offsets are not zero and the rotation moves the vertices
+    off = rng.normal(size=(2, 3))
+    gp = np.stack([x[2], x[5]]) + 0.01 * off / np.linalg.norm(off, axis=1, keepdims=True)
+    dp = rng.normal(scale=0.002, size=(2, 3)) * (motion != "rotation")
+    dphi = rng.normal(scale=0.02, size=(2, 3)) * (motion != "translation")
+    frames = 4
+    acts = np.zeros((frames, 1, 2, 6))
+    acts[:, 0, :, :3] = dp
+    acts[:, 0, :, 3:] = dphi
+    p = inputs.custom([x], frames=frames, actions=acts, n_grippers=[2], grip_pos=gp[None], grip_rot=R0[None],
+                      K=1e5, E=1e4, G=1e3, gravity=0.0)
+    # inputs are rounded to float32: take the rounded values as the closed form's data
+    # (the rounded R0 is orthogonal only to ~1e-7, so the offset R0^T (x - p0) maps back with
+    # R0 R0^T, which the closed form carries explicitly)
+    dp, dphi, gp, R0, x = p.actions[0, 0, :, :3], p.actions[0, 0, :, 3:], p.grip_pos[0], p.grip_rot[0], p.x_rest
+    RRt = R0 @ np.transpose(R0, (0, 2, 1))
+    sim = OracleSim(p)
+    sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    G, S = sim.groups[0], sim.state[0]
+    kind = G["kind"][0].numpy()
+    assert [int(i) for i in np.nonzero(kind)[0]] == [2, 5] and kind[2] == 2 and kind[5] == 3
+    n_sub = G["nsub"]
+    act = torch.as_tensor(p.actions[0], dtype=F64)[None]
+    for f in range(frames):
+        for s in range(n_sub):
+            S = sim.substep(G, S, act[0], s)
+            c = f + (s + 1) / n_sub
+            for g, vi in enumerate((2, 5)):
+                want = gp[g] + c * dp[g] + rotvec_matrix(c * dphi[g]) @ RRt[g] @ (x[vi] - gp[g])
+                np.testing.assert_allclose(S["x"][0, vi].numpy(), want, rtol=0, atol=1e-13)
+        S = dict(S)
+        S["gp"] = S["gp"] + act[0, ..., :3]
+        from oracle.dlo import expmap
+        S["gR"] = expmap(act[0, ..., 3:]) @ S["gR"]
+    # the frame-level pose update (OracleSim.frame) gives the same closed form
+    sim2 = OracleSim(p)
+    sim2.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    sim2.step(p.actions, frames)
+    st = sim2.get_state()
+    for g, vi in enumerate((2, 5)):
+        np.testing.assert_allclose(st["gp"][0, g], gp[g] + frames * dp[g], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(st["gR"][0, g], rotvec_matrix(frames * dphi[g]) @ R0[g], rtol=0, atol=1e-13)
+        want = gp[g] + frames * dp[g] + rotvec_matrix(frames * dphi[g]) @ RRt[g] @ (x[vi] - gp[g])
+        np.testing.assert_allclose(st["x"][vi], want, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------------- damping
+
+def test_damping_decays_velocity_and_twist_rate_geometrically():
+    """Mass-proportional damping (reading O8: force -c_d m v, torque -c_d I omega) under
+    symplectic Euler.  A straight free rod with no gravity and no contact, moving as a rigid
+    translation with a uniform twist rate, feels no elastic force or torque, so each substep
+    multiplies v and omega by exactly (1 - h c_d): after n substeps they are
+    (1 - h c_d)^n times their start values, and the positions have moved by the geometric sum
+    h v0 sum_{k=1..n} (1 - h c_d)^k."""
+    n = 12
+    x = straight(n, 0.4, z=0.5)
+    cd = 7.0
+    p = inputs.custom([x], frames=6, K=1e5, E=1e4, G=1e3, damping=cd, gravity=0.0)
+    v0 = np.array([0.12, -0.05, 0.08])
+    p.v0 = np.tile(v0, (n, 1))
+    p.omega0 = np.full(n - 1, 3.0)
+    sim = OracleSim(p)
+    sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+    h = p.dt / sim.nsub[0]
+    q = 1.0 - h * float(p.damping[0])
+    for f in range(1, 7):
+        sim.step(p.actions[f - 1:f], 1)
+        k = f * sim.nsub[0]
+        st = sim.get_state()
+        np.testing.assert_allclose(st["v"], np.tile(q ** k * v0, (n, 1)), rtol=1e-9)
+        np.testing.assert_allclose(st["omega"], np.full(n - 1, q ** k * 3.0), rtol=1e-12)
+        moved = h * v0 * q * (1.0 - q ** k) / (1.0 - q)
+        np.testing.assert_allclose(st["x"] - p.x0, np.tile(moved, (n, 1)), rtol=1e-9, atol=1e-15)
