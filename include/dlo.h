@@ -133,6 +133,18 @@ dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, const dlo_ma
  * Errors: DLO_ERR_INVALID_ARG for a NULL x or a pointer that is not 16-byte aligned. */
 dlo_status dlo_set_state(dlo_ctx* ctx, const float* x, const float* v, const float* theta);
 
+/* Replace the per-rod material (host mat[B]) after create: the moduli K_stretch, E_bend and
+ * G_twist, the yield curvature, the creep rate and the damping, with which the next dlo_step
+ * runs.  Each rod's substep count is recomputed from the new moduli (as at dlo_create).
+ * Density, radius, inextensibility, strain limit, plasticity and topology are fixed at
+ * create (they set masses, inertias and the rod's constraints) and must be unchanged.  Ends
+ * any armed recording (a recorded rollout ran with the previous material).  Synchronises.
+ * Defined by: the material parameters of the energies and the plasticity rule of App. A.1
+ * (the quantities the system identification of Sec. 5 fits).
+ * Errors: DLO_ERR_INVALID_ARG for a NULL mat, a value out of range or a change of a
+ * create-time quantity (dlo_last_error names the rod); the context is unchanged then. */
+dlo_status dlo_set_material(dlo_ctx* ctx, const dlo_material* mat);
+
 /* Copy the state into caller-owned device buffers (any may be NULL).  Synchronises the
  * stream and reports device-side errors. */
 dlo_status dlo_get_state(dlo_ctx* ctx, float* x, float* v, float* theta);
@@ -292,7 +304,11 @@ dlo_status dlo_reaction(dlo_ctx* ctx, float* per_rod, float* per_vertex, int res
 
 enum {
     DLO_Q_SUBSTEPS = 1,      /* int [B]: substeps per frame of each rod */
-    DLO_Q_STATUS = 2,        /* unsigned [B]: status bits (1 non-finite, 2 pair overflow) */
+    DLO_Q_STATUS = 2,        /* unsigned [B]: status bits since the last dlo_set_state: 1 non-finite
+                                state, 2 pair-list overflow (both errors), 4 a warning: some vertex
+                                moved, within one frame, at least half of the candidate margin
+                                (contact_margin x radius), so the candidates found at the frame's
+                                start may miss a pair that came into contact during it */
     DLO_Q_BYTES = 3,         /* size_t: device bytes held by the context */
     DLO_Q_CONFIG = 4,        /* int [4]: warps per CTA, checkpoint interval, CTAs, smem/CTA */
     DLO_Q_RESIDUAL = 5,      /* double [B]: sum |C_j| of the inextensibility constraints
@@ -300,8 +316,13 @@ enum {
     DLO_Q_PAIRS = 6,         /* int [B]: largest self-contact candidate count of any frame of the
                                 last dlo_step (capacity: 4 per vertex of the rod's size class) */
     DLO_Q_LAUNCHES = 7,      /* long long: kernels launched by this context so far */
-    DLO_Q_MASS = 8           /* float [V][4]: (mass, inverse mass, kind, 0); kind 0 free,
+    DLO_Q_MASS = 8,          /* float [V][4]: (mass, inverse mass, kind, 0); kind 0 free,
                                 1 pinned, 2/3 grasped by gripper 0/1 (host out) */
+    DLO_Q_PAIR_LIST = 9      /* unsigned [B][1 + 1024]: per rod, the number n of self-contact
+                                candidates found at the start of the last frame of the last
+                                dlo_step, then n entries (a | b << 16), edge a < edge b, in no
+                                particular order; the rest of the row is 0xffffffff.  All counts
+                                are 0 when self-contact is off */
 };
 
 /* Query (host `out`).  Synchronises. */

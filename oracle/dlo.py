@@ -198,6 +198,34 @@ def elastic_energy(x, theta, tb, d1b, mprev, kbar, R, closed: bool):
     return Us.sum(1) + Ub.sum(1) + Ut.sum(1)
 
 
+class ElasticGradient(torch.autograd.Function):
+    """(dU/dx, dU/dtheta) of ``elastic_energy`` as one differentiable operation, for rollouts
+    that are differentiated.
+
+    The values are the autograd gradient of the written-out energy, as everywhere else.  The
+    evaluation runs on detached copies of its inputs, so each substep's autograd call walks
+    only the energy's own graph; called on inputs that carry the rollout's history it would
+    walk all of that history first, and a rollout's cost would grow with the square of its
+    length.  The backward applies the energy's second derivatives to the incoming cotangents
+    (a double backward through the same graph), with respect to every input: positions, twist
+    angles, reference frames, reference twist, rest curvature and the moduli k_s, B, beta."""
+
+    @staticmethod
+    def forward(ctx, x, th, tb, d1b, mprev, kbar, kA, Bm, beta, R, closed):
+        leaves = [a.detach().requires_grad_(True) for a in (x, th, tb, d1b, mprev, kbar, kA, Bm, beta)]
+        with torch.enable_grad():
+            R2 = dict(R, kA=leaves[6], Bm=leaves[7], beta=leaves[8])
+            U = elastic_energy(*leaves[:6], R2, closed)
+            gx, gth = torch.autograd.grad(U.sum(), leaves[:2], create_graph=True)
+        ctx.leaves, ctx.outs = leaves, (gx, gth)
+        return gx.detach(), gth.detach()
+
+    @staticmethod
+    def backward(ctx, ggx, ggth):
+        g = torch.autograd.grad(ctx.outs, ctx.leaves, (ggx, ggth), allow_unused=True)
+        return (*g, None, None)
+
+
 # --------------------------------------------------------------------------- contact geometry
 
 def sdf_plane(x, n, off):
@@ -304,6 +332,10 @@ class OracleSim:
             keys.setdefault((int(prob.n_verts[b]), bool(prob.closed[b]), self.nsub[b]), []).append(b)
         self.groups = [self._group(np.array(ids), *k) for k, ids in sorted(keys.items())]
         self.state = None
+        # branch trace: when set to a list, every branch decision of the step (rigid contact
+        # active, yield, strain-limit projection active, candidate pair set) is appended to it
+        # in order, so that two runs can be checked for taking the same branches
+        self.trace = None
 
     # ------------------------------------------------------------------ static per-group data
     def _group(self, ids, N, closed, nsub):
@@ -484,11 +516,15 @@ class OracleSim:
         kappa, mref, _ = hinge_strains(t, d1r, d1, d2, th, S["mprev"], closed)
         kbar = self.plastic_update(G, kappa, S["kbar"])
         # A2: F = -dU/dx, tau = -dU/dtheta (autograd of the energy at the updated kbar)
-        dx = torch.zeros_like(x, requires_grad=True)
-        dth = torch.zeros_like(th, requires_grad=True)
-        with torch.enable_grad():
-            U = elastic_energy(x + dx, th + dth, S["tb"], S["d1b"], S["mprev"], kbar, R, closed)
-            gx, gth = torch.autograd.grad(U.sum(), [dx, dth], create_graph=diff)
+        if diff:
+            gx, gth = ElasticGradient.apply(x, th, S["tb"], S["d1b"], S["mprev"], kbar, R["kA"], R["Bm"],
+                                            R["beta"], R, closed)
+        else:
+            dx = torch.zeros_like(x, requires_grad=True)
+            dth = torch.zeros_like(th, requires_grad=True)
+            with torch.enable_grad():
+                U = elastic_energy(x + dx, th + dth, S["tb"], S["d1b"], S["mprev"], kbar, R, closed)
+                gx, gth = torch.autograd.grad(U.sum(), [dx, dth])
         # A4/A5: gravity, damping, symplectic Euler velocity update
         grav = torch.tensor([0.0, 0.0, -p.gravity], dtype=self.dtype)
         w = R["w"][..., None]
@@ -535,6 +571,7 @@ class OracleSim:
         nk = safe_norm(kel)
         thr = R["sy"][:, None] * R["lbar"]
         y = R["plastic"][:, None] & (nk > thr)
+        self._note("yield", y)
         nks = torch.where(y, nk, torch.ones_like(nk))
         upd = kbar + (R["rc"][:, None] * (nk - thr) / nks)[..., None] * kel
         return torch.where(y[..., None], upd, kbar)
@@ -554,6 +591,7 @@ class OracleSim:
             d = r - sdf
             f = torch.exp(d / (p.eps_soft * r)).clamp(max=1.0)
             act = (f > 0.1) & free & mask
+            self._note("rigid", act)
             nrm = torch.where(act[..., None], nrm, torch.zeros_like(nrm))
             vr = v - vrig
             vn = dot(vr, nrm)
@@ -620,6 +658,7 @@ class OracleSim:
         wa, wb = R["w"][:, j0], R["w"][:, j1]
         ws = wa + wb
         active = active & (ws > 0)
+        self._note("length", active)
         lam = torch.where(active, (ell - target) / torch.where(active, ws, torch.ones_like(ws)), torch.zeros_like(ws))
         da = (lam * wa)[..., None] * t
         db = -(lam * wb)[..., None] * t
@@ -648,6 +687,7 @@ class OracleSim:
             rr = float(self.p.radius[b])
             near = norm(ca - cb) < 2 * rr + self.p.contact_margin * rr
             out.append(torch.stack([a[near], c[near]], 1))
+            self._note("pairs", out[-1])
         return out
 
     def contact_sweep(self, G, xs, pairs):
@@ -720,6 +760,10 @@ class OracleSim:
         return torch.stack(outs)
 
     # ------------------------------------------------------------------ diagnostics
+    def _note(self, kind, mask):
+        if self.trace is not None:
+            self.trace.append((kind, mask.detach().numpy().copy()))
+
     def track_reaction(self):
         """Start (or restart) accumulating the rigid-contact impulses per vertex in four slots:
         planes, boxes, gripper 0, gripper 1."""

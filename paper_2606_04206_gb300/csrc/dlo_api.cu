@@ -74,6 +74,26 @@ static int substeps_for(double dt, int nmin, double rho, double r, double K, dou
     return std::max(nmin, (int)std::ceil(dt * w));
 }
 
+// The material-dependent constants of a rod (App. A.1: k_s = K A, B = E A r^2 / 4,
+// beta = G A r^2 / 2; yield curvature, creep rate, damping) and its substep.
+static void set_moduli(RodInfo& R, const dlo_material& m, int ns, double dt) {
+    const double r = m.radius, A = M_PI * r * r;
+    R.nsub = ns;
+    R.h = (float)(dt / ns);
+    R.kA = m.inextensible ? 0.f : (float)(m.K_stretch * A);
+    R.Bm = (float)(m.E_bend * A * r * r / 4.0);
+    R.beta = (float)(m.G_twist * A * r * r / 2.0);
+    R.sy = m.yield_curv;
+    R.rc = m.creep_rate;
+    R.cd = m.damping;
+}
+
+static bool material_ok(const dlo_material& m) {
+    return m.density > 0.f && m.radius > 0.f && m.K_stretch >= 0.f && m.E_bend >= 0.f && m.G_twist >= 0.f &&
+           m.strain_limit >= 0.f && m.strain_limit < 1.f && m.yield_curv >= 0.f && m.creep_rate >= 0.f &&
+           m.creep_rate <= 1.f && m.damping >= 0.f;
+}
+
 // ------------------------------------------------------------------ create / destroy
 extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, const dlo_material* mat,
                                  const float* x_rest, const dlo_scene* scene, const dlo_options* opt,
@@ -108,9 +128,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
             return DLO_ERR_INVALID_ARG;
         }
         const dlo_material& m = mat[b];
-        if (!(m.density > 0.f) || !(m.radius > 0.f) || m.K_stretch < 0.f || m.E_bend < 0.f || m.G_twist < 0.f ||
-            m.strain_limit < 0.f || m.strain_limit >= 1.f || m.yield_curv < 0.f || m.creep_rate < 0.f ||
-            m.creep_rate > 1.f || m.damping < 0.f) {
+        if (!material_ok(m)) {
             delete c;
             return DLO_ERR_INVALID_ARG;
         }
@@ -142,6 +160,8 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
     std::vector<float2> massv(V), es(Et);
     std::vector<float> gp0((size_t)batch * 24, 0.f);
     c->nsub.resize(batch);
+    c->lmin_h.resize(batch);
+    c->mat_h.assign(mat, mat + batch);
     for (int b = 0; b < batch; ++b) {
         const dlo_material& m = mat[b];
         const int nv = n_verts[b], v0 = vo[b], e0 = eo[b];
@@ -166,6 +186,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         const bool inext = m.inextensible != 0;
         const int ns = substeps_for(opt->dt, opt->substeps_min, rho, r, m.K_stretch, m.E_bend, m.G_twist, inext, lmin);
         c->nsub[b] = ns;
+        c->lmin_h[b] = lmin;
         // kinematic kinds: pinned, grasped (every vertex touching the capsule, at least the nearest)
         std::vector<int> kind(nv, 0);
         std::vector<double> off(3 * nv, 0.0);
@@ -234,13 +255,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
                   (closed ? ROD_CLOSED : 0);
         R.ngrip = ng;
         R.excl = std::max(1, (int)std::ceil(2.0 * r / lmin));
-        R.h = (float)(opt->dt / ns);
-        R.kA = inext ? 0.f : (float)(m.K_stretch * A);
-        R.Bm = (float)(m.E_bend * A * r * r / 4.0);
-        R.beta = (float)(m.G_twist * A * r * r / 2.0);
-        R.sy = m.yield_curv;
-        R.rc = m.creep_rate;
-        R.cd = m.damping;
+        set_moduli(R, m, ns, opt->dt);
         R.radius = m.radius;
         R.slim = (!inext && m.strain_limit > 0.f) ? m.strain_limit : 0.f;
         R.contact_d = (float)(2.0 * r + opt->contact_margin * r);
@@ -331,6 +346,36 @@ extern "C" dlo_status dlo_set_state(dlo_ctx* c, const float* x, const float* v, 
     return st;
 }
 
+// ------------------------------------------------------------------ material
+extern "C" dlo_status dlo_set_material(dlo_ctx* c, const dlo_material* mat) {
+    if (!c) return DLO_ERR_INVALID_ARG;
+    if (!mat) return set_err(c, DLO_ERR_INVALID_ARG, "mat is NULL");
+    std::vector<RodInfo> rods = c->rods_h;
+    std::vector<int> nsub = c->nsub;
+    for (int b = 0; b < c->B; ++b) {
+        const dlo_material& m = mat[b], &m0 = c->mat_h[b];
+        if (!material_ok(m))
+            return set_err(c, DLO_ERR_INVALID_ARG, "rod " + std::to_string(b) + ": material value out of range");
+        if (m.density != m0.density || m.radius != m0.radius || m.inextensible != m0.inextensible ||
+            m.strain_limit != m0.strain_limit || m.plastic != m0.plastic || m.closed != m0.closed)
+            return set_err(c, DLO_ERR_INVALID_ARG,
+                           "rod " + std::to_string(b) +
+                               ": density, radius, inextensibility, strain limit, plasticity and topology are fixed "
+                               "at dlo_create");
+        nsub[b] = substeps_for(c->opt.dt, c->opt.substeps_min, m.density, m.radius, m.K_stretch, m.E_bend,
+                               m.G_twist, m.inextensible != 0, c->lmin_h[b]);
+        set_moduli(rods[b], m, nsub[b], c->opt.dt);
+    }
+    cudaError_t e = cudaMemcpyAsync(c->d_rods, rods.data(), sizeof(RodInfo) * c->B, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // the host vector is released on return
+    if (e != cudaSuccess) return cuda_err(c, e, "material upload");
+    c->rods_h = rods;
+    c->nsub = nsub;
+    c->mat_h.assign(mat, mat + c->B);
+    c->rec_active = false;   // a recorded rollout ran with the previous material
+    return DLO_OK;
+}
+
 dlo_status check_status(dlo_ctx* c) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_err(c, e, "stream");
@@ -402,6 +447,21 @@ extern "C" dlo_status dlo_query(dlo_ctx* c, int what, void* out) {
             cudaError_t e = cudaStreamSynchronize(c->stream);
             if (e == cudaSuccess) e = cudaMemcpy(out, c->d_npairs, sizeof(int) * c->B, cudaMemcpyDeviceToHost);
             return cuda_err(c, e, "query pairs");
+        }
+        case DLO_Q_PAIR_LIST: {
+            const size_t stride = 1 + (size_t)kPairListStride;
+            uint32_t* o = reinterpret_cast<uint32_t*>(out);
+            cudaError_t e = cudaStreamSynchronize(c->stream);
+            if (e == cudaSuccess && c->d_pair_list)
+                e = cudaMemcpy(o, c->d_pair_list, sizeof(uint32_t) * stride * c->B, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_err(c, e, "query pair list");
+            for (int b = 0; b < c->B; ++b) {
+                uint32_t* r = o + stride * b;
+                if (!c->d_pair_list) r[0] = 0;
+                const uint32_t n = std::min<uint32_t>(r[0], (uint32_t)kPairListStride);
+                for (size_t k = 1 + n; k < stride; ++k) r[k] = 0xffffffffu;
+            }
+            return DLO_OK;
         }
         case DLO_Q_LAUNCHES:
             *reinterpret_cast<long long*>(out) = c->launches;

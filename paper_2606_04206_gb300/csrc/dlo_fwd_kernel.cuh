@@ -68,31 +68,44 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
             if (g.tid < 12) s.act[g.tid] = P.actions ? P.actions[((long long)f * P.B + rod) * 12 + g.tid] : 0.f;
             g.sync();
             bool ovf = false;
+            float mv = 0.f;
             const int np = run_frame<NV, CONTACT, TPR, true>(P.scene, P.KIN, P.ES, R, s, g, nsub, h, ovf,
                                                        [](int) -> const Rec* { return nullptr; },
-                                                       P.reaction ? P.reaction + 4LL * R.v0 : nullptr);
+                                                       P.reaction ? P.reaction + 4LL * R.v0 : nullptr, &mv);
             if (ovf) bad |= 2u;
             np_max = max(np_max, np);
-            bool nf = false;
+            unsigned fl = 0u;
             for (int i = g.tid; i < R.nv; i += TPR) {
                 float4 x = s.X[i], v = s.V[i];
-                nf |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) && isfinite(v.y) &&
-                        isfinite(v.z) && isfinite(v.w));
+                if (!(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(v.x) && isfinite(v.y) &&
+                      isfinite(v.z) && isfinite(v.w)))
+                    fl |= 1u;
                 if (P.xframes) reinterpret_cast<float4*>(P.xframes)[(long long)f * P.nvert_total + R.v0 + i] = x;
             }
-            if (grp_any<TPR>(nf, g)) bad |= 1u;
+            // candidates are found once per frame at its start, with a margin of contact_d - 2r:
+            // two vertices that each moved less than half of it cannot have closed it
+            if ((R.flags & ROD_SELF) && !(mv < 0.5f * (R.contact_d - 2.f * R.radius))) fl |= 4u;
+            bad |= grp_or<TPR>(fl, g);
             if (f + 1 == P.frames) {
                 if (R.flags & ROD_INEXT) {
+                    // sum |C_j| in FP64, each edge length from the float32 positions in FP64
                     double r = 0.0;
                     for (int j = g.tid; j < R.ne; j += TPR) {
                         int j1 = (j + 1 == R.nv) ? 0 : j + 1;
-                        V3<float> e = f3(s.X[j1]) - f3(s.X[j]);
-                        r += fabs((double)sqrtf(dot(e, e)) - (double)s.ET[j].w);
+                        const double ex = (double)s.X[j1].x - (double)s.X[j].x;
+                        const double ey = (double)s.X[j1].y - (double)s.X[j].y;
+                        const double ez = (double)s.X[j1].z - (double)s.X[j].z;
+                        r += fabs(sqrt(ex * ex + ey * ey + ez * ez) - (double)s.ET[j].w);
                     }
                     r = grp_sum<TPR>(r, g);
                     if (g.tid == 0) P.residual[rod] = r;
                 }
                 if (g.tid == 0) P.npairs[rod] = np_max;
+                if (CONTACT && P.pair_list) {   // the last frame's candidates
+                    uint32_t* dst = P.pair_list + (size_t)rod * (1 + kPairListStride);
+                    for (int k = g.tid; k < np; k += TPR) dst[1 + k] = s.pairs[k];
+                    if (g.tid == 0) dst[0] = (uint32_t)np;
+                }
             }
         }
         write_state<TPR>(P.S, 0, 0, 0, R, rod, g, s.X, s.V, s.ED, s.ET, s.HG, s.fp);

@@ -23,6 +23,10 @@ struct RodInfo {
     int pair_cap, pair_off, pad0, pad1;
 };
 
+// Stride of the per-rod candidate list read back by DLO_Q_PAIR_LIST: 4 pairs per vertex of
+// the largest size class (256 vertices).
+constexpr int kPairListStride = 1024;
+
 constexpr int kMaxPlanes = 4;
 constexpr int kMaxBoxes = 4;
 
@@ -61,10 +65,10 @@ struct FwdParams {
     StateRef ck;
     long long ck_strideV, ck_strideE, ck_strideB;
     int ck_every, ck_count;
-    unsigned* status;         // [B] bit 1 non-finite, bit 2 pair overflow
+    unsigned* status;         // [B] bit 1 non-finite, bit 2 pair overflow, bit 4 moved past the margin
     double* residual;         // [B]
     int* npairs;              // [B]
-    uint32_t* pairs_g;        // global spill of pair lists (unused when they fit in smem)
+    uint32_t* pair_list;      // [B][1 + kPairListStride]: the last frame's candidates (count, pairs) or null
     float4* reaction;         // [V][4] contact impulse slots (planes, boxes, gripper 0, 1) or null
     SceneDev scene;
 };

@@ -125,6 +125,9 @@ dlo_status runtime_allocate(dlo_ctx* c, const std::vector<RodInfo>& rods, const 
     c->d_residual = reinterpret_cast<double*>(alloc_zero(c, sizeof(double) * c->B, st));
     c->d_npairs = reinterpret_cast<int*>(alloc_zero(c, sizeof(int) * c->B, st));
     if (c->opt.reaction) c->d_reaction = reinterpret_cast<float4*>(alloc_zero(c, 64 * c->V, st));
+    if (c->opt.self_contact)
+        c->d_pair_list = reinterpret_cast<uint32_t*>(
+            alloc_zero(c, sizeof(uint32_t) * (1 + (size_t)kPairListStride) * c->B, st));
     if (st != DLO_OK) return st;
     // size classes; rods of a class in decreasing cost so the persistent warps balance
     std::vector<std::vector<int>> cls(kNumSizeClasses);
@@ -326,6 +329,7 @@ dlo_status launch_step(dlo_ctx* c, const float* actions, int frames, int substep
         P.residual = c->d_residual;
         P.npairs = c->d_npairs;
         P.reaction = c->d_reaction;
+        P.pair_list = c->d_pair_list;
         P.scene = c->scene;
         cudaStream_t sk = class_stream(c, k);
         cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), sk);

@@ -47,6 +47,9 @@ struct dlo_ctx {
     int* d_npairs = nullptr;
     int* d_counters = nullptr;   // one work-queue head per bucket
     float4* d_reaction = nullptr;  // [V][4] contact impulse slots when opt.reaction
+    uint32_t* d_pair_list = nullptr;  // [B][1 + kPairListStride] last frame's candidates (self-contact)
+    std::vector<dlo_material> mat_h;  // per-rod material as created (or last set)
+    std::vector<double> lmin_h;       // per-rod shortest rest edge
     std::vector<dlo::Bucket> buckets;
     // with several size classes, each class's kernels run on its own stream, forked from and
     // joined back to `stream` with events, so that the classes' tails overlap

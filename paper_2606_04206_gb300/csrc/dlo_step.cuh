@@ -69,6 +69,21 @@ __device__ __forceinline__ bool grp_any(bool p, const Grp<TPR>& g) {
     return s;
 }
 
+// Bitwise OR over the group.
+template <int TPR>
+__device__ __forceinline__ unsigned grp_or(unsigned v, const Grp<TPR>& g) {
+    const unsigned w = __reduce_or_sync(0xffffffffu, v);
+    if (TPR == 32) return w;
+    unsigned* r = reinterpret_cast<unsigned*>(g.red) + 56;
+    if ((g.tid & 31) == 0) r[g.tid >> 5] = w;
+    g.sync();
+    unsigned s = 0u;
+#pragma unroll
+    for (int k = 0; k < TPR / 32; ++k) s |= r[k];
+    g.sync();
+    return s;
+}
+
 // Value held by thread 0 of the group.
 template <int TPR>
 __device__ __forceinline__ int grp_bcast0(int v, const Grp<TPR>& g) {
@@ -418,7 +433,7 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
                         const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, float h, int np,
-                        const Rec* rec = nullptr, float4* imp = nullptr) {
+                        const Rec* rec = nullptr, float4* imp = nullptr, float* mv = nullptr) {
     const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
     const bool closed = R.flags & ROD_CLOSED;
     const int nh = closed ? nv : nv - 2;
@@ -568,13 +583,19 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
             rec->fr1[p] = s.fr1[p];
         }
     if (CONTACT && np > 0) self_friction<NV, CONTACT, TPR>(R, s, g, np, h, sc.mu_self);
+    float dm2 = 0.f;   // the largest squared displacement of this thread's vertices
     for (int i = g.tid; i < nv; i += TPR) {
         float4 x0 = s.X0[i], d = s.X[i], nd = s.ND[i];
         float4 x = nd.w > 0.5f ? make_float4(nd.x, nd.y, nd.z, x0.w)
                                : make_float4(x0.x + d.x, x0.y + d.y, x0.z + d.z, x0.w);
+        if (mv) {
+            const float dx = x.x - x0.x, dy = x.y - x0.y, dz = x.z - x0.z;
+            dm2 = fmaxf(dm2, dx * dx + dy * dy + dz * dz);
+        }
         s.X0[i] = x;
         s.X[i] = x;
     }
+    if (mv) *mv += sqrtf(dm2);
     g.sync();
 }
 
@@ -636,11 +657,13 @@ __device__ __forceinline__ void frame_advance(float* F, const float* act, int q)
 // holds the end pose on return.  pre(sb) runs before substep sb (after a group barrier), e.g.
 // to store the substep state, and returns the substep's record (or nullptr).  imp: the rod's
 // impulse slots (4 per vertex) when the contact impulses are being accumulated (inlined
-// substeps only).
+// substeps only).  mv (inlined substeps only): adds, per thread, the sum over the frame's
+// substeps of the largest displacement of the thread's vertices, a bound on how far any of
+// them moved during the frame.
 template <int NV, bool CONTACT, int TPR, bool INLINE, class PreSub>
 __device__ __forceinline__ int run_frame(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
                          const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int nsub, float h, bool& ovf,
-                         PreSub pre, float4* imp = nullptr) {
+                         PreSub pre, float4* imp = nullptr, float* mv = nullptr) {
     int np = 0;
     if (CONTACT && (R.flags & ROD_SELF)) np = broad_phase<NV, CONTACT, TPR>(R, s, g, (R.flags & ROD_CLOSED) != 0, ovf);
     const float inv_dt = 1.f / sc.dt;
@@ -651,7 +674,7 @@ __device__ __forceinline__ int run_frame(const SceneDev& sc, const float4* __res
             substep_pose(s.fp, s.act, g.tid, (float)sb / (float)nsub, (float)(sb + 1) / (float)nsub, sb == 0, inv_dt,
                          s.sp);
         if (INLINE)
-            substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec, imp);
+            substep_body<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec, imp, mv);
         else
             substep_call<NV, CONTACT, TPR>(sc, KIN, ES, R, s, g, h, np, rec);
     }

@@ -19,7 +19,10 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "dlo.h")
 
 STATUS = {0: "DLO_OK", 1: "DLO_ERR_INVALID_ARG", 2: "DLO_ERR_CUDA", 3: "DLO_ERR_OOM", 4: "DLO_ERR_NONFINITE",
           5: "DLO_ERR_CAPACITY", 6: "DLO_ERR_TIMEOUT", 7: "DLO_ERR_STATE"}
-Q_SUBSTEPS, Q_STATUS, Q_BYTES, Q_CONFIG, Q_RESIDUAL, Q_PAIRS, Q_LAUNCHES, Q_MASS = range(1, 9)
+Q_SUBSTEPS, Q_STATUS, Q_BYTES, Q_CONFIG, Q_RESIDUAL, Q_PAIRS, Q_LAUNCHES, Q_MASS, Q_PAIR_LIST = range(1, 10)
+PAIR_LIST_STRIDE = 1024   # candidates per rod row of Q_PAIR_LIST (4 per vertex of 256 vertices)
+STATUS_NONFINITE, STATUS_PAIR_OVERFLOW, STATUS_MOVED_PAST_MARGIN = 1, 2, 4
+MATERIAL_KEYS = ("K", "E", "G", "yield_curv", "damping")
 LOSS_TARGET, LOSS_CHAMFER, LOSS_WINDING, LOSS_CROSSING, LOSS_MINDIST, LOSS_REPULSION = range(1, 7)
 N_MAT_GRAD = 5      # K_stretch, E_bend, G_twist, yield_curv, damping
 
@@ -76,6 +79,8 @@ def load(path: str | None = None):
     lib.dlo_create.argtypes = [C.POINTER(vp), ip, C.POINTER(C.c_int), C.POINTER(Material), fp, C.POINTER(Scene),
                                C.POINTER(Options), C.POINTER(Allocator), vp]
     lib.dlo_create.restype = st
+    lib.dlo_set_material.argtypes = [vp, C.POINTER(Material)]
+    lib.dlo_set_material.restype = st
     lib.dlo_set_state.argtypes = [vp, vp, vp, vp]
     lib.dlo_set_state.restype = st
     lib.dlo_get_state.argtypes = [vp, vp, vp, vp]
@@ -136,9 +141,13 @@ def options_from(prob, **over) -> Options:
 
 
 class DloSim:
-    """One library context over the rods of a workload (``inputs.Problem``)."""
+    """One library context over the rods of a workload (``inputs.Problem``).
 
-    def __init__(self, prob, torch_alloc: bool = True, **opt):
+    Device memory comes from torch's caching allocator, or from ``allocator``: a pair of
+    callables (alloc(nbytes) -> device address or None, free(address)) handed to the
+    library as its dlo_allocator."""
+
+    def __init__(self, prob, torch_alloc: bool = True, allocator=None, **opt):
         import torch
         self.torch = torch
         self.lib = load()
@@ -150,11 +159,9 @@ class DloSim:
         self.stream = torch.cuda.current_stream()
         B = self.B
         self._keep = []
-        mats = (Material * B)()
-        for b in range(B):
-            mats[b] = Material(prob.density[b], prob.radius[b], prob.K[b], prob.E[b], prob.G[b],
-                               int(prob.inextensible[b]), prob.strain_limit[b], int(prob.plastic[b]),
-                               prob.yield_curv[b], prob.creep_rate[b], prob.damping[b], int(prob.closed[b]))
+        self._mat = np.stack([np.asarray(getattr(prob, k), np.float32) for k in MATERIAL_KEYS], 1)
+        mats = self._materials(self._mat)
+        self.rollout_id = 0   # advanced by every call that replaces or ends the recorded rollout
         nv = np.ascontiguousarray(prob.n_verts, np.int32)
         xr = np.ascontiguousarray(prob.x_rest, np.float32)
         planes = np.ascontiguousarray(prob.planes, np.float32).reshape(-1)
@@ -171,7 +178,21 @@ class DloSim:
                       pinned.ctypes.data_as(C.POINTER(C.c_ubyte)))
         self.options = options_from(prob, **opt)
         alloc = None
-        if torch_alloc:
+        if allocator is not None:
+            ua, uf = allocator
+
+            def _alloc(n, user):
+                try:
+                    return ua(int(n))
+                except Exception:
+                    return None
+
+            def _free(p, user):
+                uf(p)
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            alloc = Allocator(self._cb[0], self._cb[1], None)
+        elif torch_alloc:
             dev = self.device.index
             stream = self.stream
 
@@ -195,6 +216,16 @@ class DloSim:
         self.ctx = ctx
 
     # ------------------------------------------------------------------ helpers
+    def _materials(self, vals):
+        """dlo_material[B] from the workload with (K, E, G, yield_curv, damping) = vals [B, 5]."""
+        p = self.p
+        mats = (Material * self.B)()
+        for b in range(self.B):
+            K, E, G, sy, cd = (float(v) for v in vals[b])
+            mats[b] = Material(p.density[b], p.radius[b], K, E, G, int(p.inextensible[b]), p.strain_limit[b],
+                               int(p.plastic[b]), sy, p.creep_rate[b], cd, int(p.closed[b]))
+        return mats
+
     def _check(self, st, what):
         if st != 0:
             raise DloError(st, f"{what}: {self.lib.dlo_last_error(self.ctx).decode()}")
@@ -231,7 +262,17 @@ class DloSim:
 
     # ------------------------------------------------------------------ API
     def set_state(self, x, v, theta):
+        self.rollout_id += 1
         self._check(self.lib.dlo_set_state(self.ctx, _ptr(x), _ptr(v), _ptr(theta)), "dlo_set_state")
+
+    def set_material(self, values):
+        """dlo_set_material: per-rod (K_stretch, E_bend, G_twist, yield_curv, damping) = values
+        [B, 5] (array or tensor) for the next steps; ends any recorded rollout."""
+        vals = np.asarray(values.detach().cpu().numpy() if hasattr(values, "detach") else values, np.float32)
+        assert vals.shape == (self.B, N_MAT_GRAD), vals.shape
+        self.rollout_id += 1
+        self._check(self.lib.dlo_set_material(self.ctx, self._materials(vals)), "dlo_set_material")
+        self._mat = vals.copy()
 
     def reset(self):
         self.set_state(*self.tensors_from_problem())
@@ -270,7 +311,10 @@ class DloSim:
                     gR=grip[..., 3:].reshape(self.B, 2, 3, 3))
 
     def begin_rollout(self, n_frames):
+        self.rollout_id += 1
+        self._rec_left = 0
         self._check(self.lib.dlo_begin_rollout(self.ctx, int(n_frames)), "dlo_begin_rollout")
+        self._rec_left = int(n_frames)
         self._rollout_frames = int(n_frames)
 
     def step(self, actions=None, frames=None, substeps=0, x_frames=None):
@@ -281,8 +325,15 @@ class DloSim:
             assert actions.numel() >= frames * self.B * 12
         self._check(self.lib.dlo_step(self.ctx, _ptr(actions), int(frames), int(substeps), _ptr(x_frames)),
                     "dlo_step")
+        if frames > 0:
+            if getattr(self, "_rec_left", 0) >= frames:
+                self._rec_left -= frames     # part of the armed recording
+            else:
+                self.rollout_id += 1         # a step past the recording ends it
+                self._rec_left = 0
 
     def step_plain(self, actions=None, frames=None, substeps=0):
+        self.rollout_id += 1
         if frames is None:
             frames = actions.shape[0]
         self._check(self.lib.dlo_step_plain(self.ctx, _ptr(actions), int(frames), int(substeps)), "dlo_step_plain")
@@ -339,13 +390,25 @@ class DloSim:
             o = C.c_longlong()
         elif what == Q_MASS:
             o = (C.c_float * (4 * self.V))()
+        elif what == Q_PAIR_LIST:
+            o = (C.c_uint * ((1 + PAIR_LIST_STRIDE) * self.B))()
         else:
             raise ValueError(what)
         self._check(self.lib.dlo_query(self.ctx, what, C.byref(o)), "dlo_query")
         if hasattr(o, "value"):
             return o.value
         a = np.ctypeslib.as_array(o).copy()
-        return a.reshape(self.V, 4) if what == Q_MASS else a
+        if what == Q_MASS:
+            return a.reshape(self.V, 4)
+        if what == Q_PAIR_LIST:
+            return a.reshape(self.B, 1 + PAIR_LIST_STRIDE)
+        return a
+
+    def pair_sets(self):
+        """Self-contact candidates of the last frame of the last dlo_step, per rod: a set of
+        (edge a, edge b) with a < b (DLO_Q_PAIR_LIST)."""
+        rows = self.query(Q_PAIR_LIST)
+        return [{(int(e & 0xffff), int(e >> 16)) for e in r[1:1 + int(r[0])]} for r in rows]
 
     def loss(self, kind, x, aux=None, g=None, grad=True):
         """dlo_loss: per-rod task loss q [B] and (grad=True) dL/dx [V,4] for L = sum_b g_b q_b."""
@@ -389,11 +452,9 @@ class DloSim:
         return pr[..., :3], (pv[..., :3] if per_vertex else None)
 
     def material_tensor(self):
-        """The context's per-rod material as a [B, 5] tensor (K_stretch, E_bend, G_twist,
+        """The context's current per-rod material as a [B, 5] tensor (K_stretch, E_bend, G_twist,
         yield_curv, damping): the input whose gradient DloRollout returns."""
-        p = self.p
-        m = np.stack([np.asarray(getattr(p, k), np.float32) for k in ("K", "E", "G", "yield_curv", "damping")], 1)
-        return self.torch.as_tensor(m, device=self.device)
+        return self.torch.as_tensor(self._mat.copy(), device=self.device)
 
 
 def _rollout_function():
@@ -403,23 +464,33 @@ def _rollout_function():
         """A recorded rollout as a differentiable torch operation (Sec. 3.3).
 
         forward(sim, x0 [V,4], v0 [V,4], theta0 [E], actions [F,B,2,6], material [B,5])
-        sets the state, records and steps F frames, and returns the final (x, v, theta).
-        ``material`` must hold the values the context was created with (see
-        DloSim.material_tensor); it is an input only so that its gradient can flow.
-        backward runs dlo_backward on the recorded rollout."""
+        sets the material (dlo_set_material, when it differs from the context's) and the
+        state, records and steps F frames, and returns the final (x, v, theta).
+        backward runs dlo_backward on the recorded rollout; it raises if the context has
+        recorded or reset anything since this forward (its record would belong to another
+        rollout)."""
 
         @staticmethod
         def forward(ctx, sim, x0, v0, theta0, actions, material):
             frames = actions.shape[0]
+            mat = material.detach().float().cpu().numpy()
+            if mat.shape != sim._mat.shape:
+                raise ValueError(f"material must be [B, {N_MAT_GRAD}], got {tuple(mat.shape)}")
+            if not np.array_equal(mat, sim._mat):
+                sim.set_material(mat)
             sim.set_state(x0.contiguous(), v0.contiguous(), theta0.contiguous())
             sim.begin_rollout(frames)
             sim.step(actions.contiguous(), frames)
             x, v, th = sim.get_state()
             ctx.sim = sim
+            ctx.rollout_id = sim.rollout_id
             return x, v, th
 
         @staticmethod
         def backward(ctx, gx, gv, gth):
+            if ctx.sim.rollout_id != ctx.rollout_id:
+                raise RuntimeError("DloRollout.backward: the context has recorded or reset another rollout since "
+                                   "this one ran; run its backward before the next rollout on the same DloSim")
             need = ctx.needs_input_grad
             want = [k for k, n in zip(("x0", "v0", "theta0", "actions", "material"), need[1:]) if n]
             g = ctx.sim.backward(None if gx is None else gx.contiguous(), None if gv is None else gv.contiguous(),

@@ -112,6 +112,11 @@ def coils(n_rods=3, frames=3, n=48):
                          planes=np.array([[0, 0, 1.0, 0.0]]))
 
 
+def pair_set(cand):
+    """The oracle's candidates of one rod ([n, 2] edge pairs, a < b) as a set."""
+    return {(int(a), int(b)) for a, b in cand.tolist()}
+
+
 def test_self_contact_candidates_and_projection_match_oracle():
     p = coils()
     sim = sim_for(p)
@@ -119,12 +124,13 @@ def test_self_contact_candidates_and_projection_match_oracle():
     acts = actions_dev(p)
     o = oracle_from_device_state(p, sim)
     sim.step(acts[:1].contiguous(), 1)
-    got = sim.query(6)                            # pairs found by the broad phase at that frame start
+    got = sim.pair_sets()                         # pairs found by the broad phase at that frame start
     for G, S in zip(o.groups, o.state):
         cand = o.candidates(G, S["x"])
         for i, b in enumerate(G["ids"]):
-            assert got[b] == cand[i].shape[0], (b, got[b], cand[i].shape[0])
-    assert got.min() > 0
+            assert got[b] == pair_set(cand[i]), (b, got[b] ^ pair_set(cand[i]))
+    assert min(len(s) for s in got) > 0
+    assert np.array_equal(sim.query(6), [len(s) for s in got])
     o.step(p.actions[:1], 1)
     fg, fo = sim.full_state_numpy(), o.get_state()
     assert rel_inf(fg["x"], fo["x"]) <= 1e-5
@@ -139,11 +145,14 @@ def test_self_contact_candidates_match_brute_force_on_knots():
     sim.step(acts[:2].contiguous(), 2)
     o = oracle_from_device_state(p, sim)
     sim.step(acts[2:3].contiguous(), 1)
-    got = sim.query(6)
+    got = sim.pair_sets()
+    n = 0
     for G, S in zip(o.groups, o.state):
         cand = o.candidates(G, S["x"])
         for i, b in enumerate(G["ids"]):
-            assert got[b] == cand[i].shape[0], (b, got[b], cand[i].shape[0])
+            assert got[b] == pair_set(cand[i]), (b, got[b] ^ pair_set(cand[i]))
+            n += len(got[b])
+    assert n > 0
 
 
 def test_bitwise_deterministic():
@@ -187,3 +196,56 @@ def test_zero_frames_and_nonfinite_detection():
     with pytest.raises(DloError) as ei:
         sim.get_state()
     assert ei.value.status == 4 and "rod 0" in str(ei.value)
+
+
+def test_fp64_inextensibility_residual():
+    """The inextensibility residual sum_j |C_j| = sum_j | |x_{j+1} - x_j| - |ebar_j| | after the
+    last frame (App. A.1), accumulated on the device in FP64 (DLO_Q_RESIDUAL).  It equals the
+    FP64 sum over the device's own float32 positions and float32 rest lengths to rounding of the
+    sum, and it differs from the oracle's residual after the same frame from the same state by
+    no more than the positions allow: each |C_j| moves by at most twice the largest position
+    difference, plus the float32 rounding of the rest length."""
+    from paper_2606_04206_gb300.dlo import Q_RESIDUAL
+    p = inputs.small_case("trajopt", n_rods=6, n=64, frames=4)
+    assert p.inextensible.any() and not p.inextensible.all()
+    sim = sim_for(p)
+    sim.reset()
+    acts = actions_dev(p)
+    sim.step(acts[:3].contiguous(), 3)
+    o = oracle_from_device_state(p, sim)
+    sim.step(acts[3:4].contiguous(), 1)
+    o.step(p.actions[3:4], 1)
+    res = sim.query(Q_RESIDUAL)
+    x = sim.get_state()[0][:, :3].double().cpu().numpy()
+    xo = o.get_state()["x"]
+    vo = p.vert_off
+    for b in range(p.batch):
+        if not p.inextensible[b]:
+            assert res[b] == 0.0
+            continue
+        eb = o.ebar[b]
+        eb32 = eb.astype(np.float32).astype(np.float64)
+        xb, xob = x[vo[b]:vo[b + 1]], xo[vo[b]:vo[b + 1]]
+        own = np.abs(np.linalg.norm(np.diff(xb, axis=0), axis=1) - eb32).sum()
+        assert res[b] == pytest.approx(own, rel=1e-12), (b, res[b], own)
+        ora = np.abs(np.linalg.norm(np.diff(xob, axis=0), axis=1) - eb).sum()
+        ne = len(eb)
+        bound = 2 * ne * np.abs(xb - xob).max() + ne * 2.0 ** -24 * eb.max()
+        assert abs(res[b] - ora) <= bound, (b, res[b], ora, bound)
+        assert res[b] > 0.0
+
+
+def test_status_flags_motion_past_the_candidate_margin():
+    """Candidates are found once per frame with a margin of contact_margin x r beyond the contact
+    distance 2r.  A rod whose vertices move half of that margin or more within one frame gets the
+    warning bit 4 in DLO_Q_STATUS; a slow rod does not, and neither is an error."""
+    from paper_2606_04206_gb300.dlo import Q_STATUS, STATUS_MOVED_PAST_MARGIN
+    xs = [np.stack([np.linspace(0.0, 0.3, 20), np.full(20, y), np.full(20, 0.5)], 1) for y in (0.0, 0.5)]
+    p = inputs.custom(xs, frames=2, K=1e5, E=1e4, G=1e3, gravity=0.0, damping=0.0, self_contact=True)
+    p.v0 = np.concatenate([np.tile([0.1, 0.0, 0.0], (20, 1)), np.tile([4.0, 0.0, 0.0], (20, 1))])
+    sim = sim_for(p)
+    sim.reset()
+    sim.step(None, 2)
+    sim.get_state()                               # a warning, not an error
+    st = sim.query(Q_STATUS)
+    assert not (st[0] & STATUS_MOVED_PAST_MARGIN) and (st[1] & STATUS_MOVED_PAST_MARGIN), st
