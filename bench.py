@@ -11,7 +11,8 @@ pass for dL/d(actions, material, initial state) of L = mean |x_T - target|^2.
 value        rod-vertex-steps/s of forward + backward (rods x vertices x frames / time)
 fwd_value    the same for the forward rollout alone
 e2e          the same through the public API from pinned host buffers (copies included)
-roofline     the dominant kernel (the backward) against the FP32 CUDA-core peak, with
+roofline     the dominant kernel (the backward) against the FP32 CUDA-core peak measured on
+             the device by a register-only FMA kernel (dlo_measure_fp32_peak), with
              algorithmic operation counts per vertex-substep from tests/flop_count.cu
 cpu_baseline the FP64 oracle on the host cores, on a bounded sample of the same workload
 plain        the plain per-phase GPU step (dlo_step_plain) on the same rods
@@ -45,8 +46,7 @@ FLOPS_BWD_PER_VS = 3650.0
 # workload, from one ncu capture of a 304-rod x 50-frame case of it (its recompute scratch
 # grows with rod-frames; profiles/fwd_bwd_kernels_trajopt_304x128x50.md)
 BWD_DRAM_BYTES_PER_ROD_FRAME = (209.585664e6 + 861.888e6) / (304 * 50)
-SM_COUNT_GB300 = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128     # for the nominal figure printed beside the measured peak
 
 
 def metric_for(workload):
@@ -457,12 +457,16 @@ def run_native(args, rank, ws):
     nsub = int(np.max(nsub_rod))
     vs_units = float(F) * float(np.sum(np.asarray(prob.n_verts, np.float64) * nsub_rod))
     max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak_tflops = SM_COUNT_GB300 * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nominal = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    peak_tflops = dlo.measure_fp32_peak(2.0)
     bwd_tflops = FLOPS_BWD_PER_VS * vs_units / (ms_bwd / 1e3) / 1e12
     fwd_tflops = FLOPS_FWD_PER_VS * vs_units / (ms_fwd / 1e3) / 1e12
     traffic = (BWD_DRAM_BYTES_PER_ROD_FRAME * R * F
                if (args.workload == "trajopt" and N == 128 and not args.no_self_contact) else None)
-    basis = f"FP32 CUDA cores: {SM_COUNT_GB300} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz"
+    basis = (f"measured: register-only FMA kernel over {sms} SMs for 2 s (dlo_measure_fp32_peak), "
+             f"{peak_tflops:.1f} TFLOP/s; nominal {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz = "
+             f"{nominal:.1f}")
     if pop:
         roofline = {"bound": "alu", "kernel": "fwd_kernel (dlo_step)", "achieved": fwd_tflops,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": fwd_tflops / peak_tflops, "traffic": None,

@@ -224,7 +224,11 @@ dlo_status dlo_backward(dlo_ctx* ctx, const float* dL_dx_T, const float* dL_dv_T
  *   dlo_last_error states the sizes.
  *   Concurrency: the array is shared by every context on the device, so calls must not
  *   overlap (two calls in flight from different threads or streams race on it).  Each call
- *   synchronises its stream before returning. */
+ *   synchronises its stream before returning.
+ *   Footprint: the array is device memory of the library's own module, reserved on a device
+ *   when that module is loaded there.  With CUDA's lazy module loading (the default) that is
+ *   the first call of this function on the device; with CUDA_MODULE_LOADING=EAGER it is every
+ *   context that loads the library, whether or not it ever calls this function. */
 #define DLO_NOALLOC_SCRATCH_BYTES ((size_t)256 << 20)
 dlo_status dlo_backward_noalloc(dlo_ctx* ctx, const float* dL_dx_T, const float* dL_dv_T,
                                 const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
@@ -327,6 +331,15 @@ enum {
 
 /* Query (host `out`).  Synchronises. */
 dlo_status dlo_query(dlo_ctx* ctx, int what, void* out);
+
+/* Measurement utility, not part of the method (the paper has no counterpart): the device's
+ * FP32 throughput in TFLOP/s (an FMA counted as 2), measured by a kernel of independent
+ * register-only FMA chains on every SM, run for about `seconds` (0 < seconds <= 60) on the
+ * given stream (NULL = legacy default stream) after a short warm-up launch.  It is the
+ * denominator of the FP32 roofline fraction the benchmark reports for the rod kernels.
+ * Synchronises the stream; allocates and frees a few bytes of device memory.
+ * Errors: DLO_ERR_INVALID_ARG for a NULL result or seconds out of range; DLO_ERR_CUDA. */
+dlo_status dlo_measure_fp32_peak(double seconds, void* cuda_stream, double* tflops);
 
 const char* dlo_status_string(dlo_status s);
 const char* dlo_last_error(const dlo_ctx* ctx);

@@ -1,18 +1,13 @@
-// dlo_adjoint.cu -- hand-written adjoint of the rod stepper with gradient checkpointing.
+// dlo_adjoint.cu -- host side of the hand-written adjoint with gradient checkpointing, and the
+// FP64 adjoint of the initial reference frames.
 //
 // DLO-Lab (Sec. 3.3) differentiates whole trajectories by caching one state per segment and,
 // for each segment in reverse, re-running the forward simulation before back-propagating.
-// Here the checkpoints live in HBM (written by the forward kernel every K frames) and one
-// thread group runs the whole backward of one rod:
-//   for each segment, last first: reload its checkpoint, recompute its frames storing the
-//   frame-start states (per-rod scratch); for each frame, last first: recompute it storing
-//   the substep-start states; for each substep, last first: recompute it once more recording
-//   its intermediates (velocity before contact, PBD iteration snapshots, displacement before
-//   friction), then apply the vector-Jacobian product of every phase in reverse order.
-// Second-order terms of the elastic forces are exact: the hinge gradient (a hand reverse pass)
-// is re-run on dual numbers, giving d/de [dU/dz](x + e lambda) for every input z, which is
-// the transpose-Jacobian product of the force (U's Hessian is symmetric).  Branches (contact
-// on/off, yield, strain-limit activity, pair sets) follow the recomputed forward.
+// Here the checkpoints live in HBM (written by the forward kernel every K frames).  The
+// rollout is reversed in chunks of C frames, last first; per chunk, rec_kernel re-runs the
+// chunk's frames from their start state storing every substep's records, then rev_kernel
+// reverses them (dlo_bwd_kernel.cuh).  C is a multiple of K when C >= K, so that every chunk
+// starts at a checkpoint; otherwise the frame-start states of each segment are stored first.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -117,14 +112,26 @@ __global__ void frames_adjoint_kernel(const RodInfo* rods, int B, const float4* 
     }
 }
 
-cudaError_t launch_backward(const BwdParams& P, int nv, bool c, int grid, int warps, cudaStream_t st) {
+cudaError_t launch_rec(const BwdParams& P, int nv, bool c, int grid, int warps, cudaStream_t st) {
     switch (nv) {
-        case 32: return launch_backward_nv32(P, c, grid, warps, st);
-        case 64: return launch_backward_nv64(P, c, grid, warps, st);
-        case 128: return launch_backward_nv128(P, c, grid, warps, st);
-        case 192: return launch_backward_nv192(P, c, grid, warps, st);
-        case 224: return launch_backward_nv224(P, c, grid, warps, st);
-        case 256: return launch_backward_nv256(P, c, grid, warps, st);
+        case 32: return launch_rec_nv32(P, c, grid, warps, st);
+        case 64: return launch_rec_nv64(P, c, grid, warps, st);
+        case 128: return launch_rec_nv128(P, c, grid, warps, st);
+        case 192: return launch_rec_nv192(P, c, grid, warps, st);
+        case 224: return launch_rec_nv224(P, c, grid, warps, st);
+        case 256: return launch_rec_nv256(P, c, grid, warps, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rev(const BwdParams& P, int nv, bool c, int grid, int warps, cudaStream_t st) {
+    switch (nv) {
+        case 32: return launch_rev_nv32(P, c, grid, warps, st);
+        case 64: return launch_rev_nv64(P, c, grid, warps, st);
+        case 128: return launch_rev_nv128(P, c, grid, warps, st);
+        case 192: return launch_rev_nv192(P, c, grid, warps, st);
+        case 224: return launch_rev_nv224(P, c, grid, warps, st);
+        case 256: return launch_rev_nv256(P, c, grid, warps, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -135,14 +142,26 @@ cudaError_t launch_frames_adjoint(const RodInfo* rods, int B, const float4* X0, 
     return cudaGetLastError();
 }
 
-int backward_blocks_per_sm(int nv, bool c, int warps) {
+int rec_blocks_per_sm(int nv, bool c, int warps) {
     switch (nv) {
-        case 32: return backward_occ_nv32(c, warps);
-        case 64: return backward_occ_nv64(c, warps);
-        case 128: return backward_occ_nv128(c, warps);
-        case 192: return backward_occ_nv192(c, warps);
-        case 224: return backward_occ_nv224(c, warps);
-        case 256: return backward_occ_nv256(c, warps);
+        case 32: return rec_occ_nv32(c, warps);
+        case 64: return rec_occ_nv64(c, warps);
+        case 128: return rec_occ_nv128(c, warps);
+        case 192: return rec_occ_nv192(c, warps);
+        case 224: return rec_occ_nv224(c, warps);
+        case 256: return rec_occ_nv256(c, warps);
+    }
+    return 0;
+}
+
+int rev_blocks_per_sm(int nv, bool c, int warps) {
+    switch (nv) {
+        case 32: return rev_occ_nv32(c, warps);
+        case 64: return rev_occ_nv64(c, warps);
+        case 128: return rev_occ_nv128(c, warps);
+        case 192: return rev_occ_nv192(c, warps);
+        case 224: return rev_occ_nv224(c, warps);
+        case 256: return rev_occ_nv256(c, warps);
     }
     return 0;
 }
@@ -151,46 +170,176 @@ int backward_blocks_per_sm(int nv, bool c, int warps) {
 
 using namespace dlo;
 
-// Launch shape and workspace of the backward for checkpoint interval K: per size class the
-// rods per CTA and CTAs that keep the most rods resident, each resident rod's recompute
-// scratch (frame-start states of one segment, substep-start states and records of one
-// frame), plus the batch-wide frame cotangents and the FP64 work of the frame adjoint.
-dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out) {
+namespace {
+
+// record sizes (float4) of one rod of the class: cf. sub_rec / frame_rec / seg_state / cot_state
+size_t frame_rec_h(int NV, int n_iter, int nsub) {
+    return (size_t)(8 + NV) + (size_t)nsub * (size_t)(7 + 2 * n_iter + 2 * kPairsPerVertex) * NV;
+}
+
+// rods per CTA and CTAs per SM that keep the most rods resident
+void best_shape(int nv, bool contact, bool rec, int& w, int& nb) {
+    w = 0;
+    nb = 0;
+    for (int rpc = 1; rpc <= 16; ++rpc) {
+        const int b = rec ? rec_blocks_per_sm(nv, contact, rpc) : rev_blocks_per_sm(nv, contact, rpc);
+        if (b >= 1 && rpc * b >= w * nb) {
+            w = rpc;
+            nb = b;
+        }
+    }
+}
+
+}  // namespace
+
+// Plan of the chunked backward for checkpoint interval K: frames per chunk C (the records of
+// one chunk of every rod within rec_budget, at most 16 frames), per-rod buffer sizes and the
+// workspace of all rods at once.
+dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out, size_t rec_budget) {
     const size_t nb_ = c->buckets.size();
-    out.slot_b.assign(nb_, 0);
-    out.offset.assign(nb_, 0);
-    out.warps.assign(nb_, 0);
-    out.grid.assign(nb_, 0);
+    if (!rec_budget) {
+        const size_t budget = c->opt.hbm_budget ? c->opt.hbm_budget : ((size_t)80 << 30);
+        rec_budget = std::min<size_t>((size_t)8 << 30, budget / 8);
+    }
     out.nsmax.assign(nb_, 0);
-    size_t need = 0;
+    out.C.assign(nb_, 1);
+    out.r3_rod.assign(nb_, 0);
+    out.l2_rod.assign(nb_, 0);
+    out.cs_rod.assign(nb_, 0);
+    out.offset.assign(nb_, 0);
+    size_t per_frame = 0;
     for (size_t k = 0; k < nb_; ++k) {
         const Bucket& bk = c->buckets[k];
-        int w = 0, nb = 0;
-        for (int rpc = 1; rpc <= 16; ++rpc) {
-            const int b = backward_blocks_per_sm(bk.nv_max, bk.contact, rpc);
-            if (b >= 1 && rpc * b >= w * nb) {
-                w = rpc;
-                nb = b;
-            }
-        }
+        int w, nb;
+        best_shape(bk.nv_max, bk.contact, false, w, nb);
         if (w < 1) return set_err(c, DLO_ERR_INVALID_ARG, "rod too large for the backward kernel's shared memory");
+        best_shape(bk.nv_max, bk.contact, true, w, nb);
+        if (w < 1) return set_err(c, DLO_ERR_INVALID_ARG, "rod too large for the recompute kernel's shared memory");
         int ns = force;
         if (!ns)
             for (int b = 0; b < c->B; ++b)
-                if (size_class(c->rods_h[b].nv) == bk.nv_max)
-                    ns = std::max(ns, c->nsub[b]);
+                if (size_class(c->rods_h[b].nv) == bk.nv_max) ns = std::max(ns, c->nsub[b]);
         out.nsmax[k] = ns;
-        const size_t NV = bk.nv_max;
-        out.slot_b[k] = 16 * ((size_t)K * (5 * NV + 6) +
-                              (size_t)ns * ((7 + 2 * kPairsPerVertex) * NV + (size_t)4 * c->opt.n_iter_pbd * NV));
-        out.warps[k] = w;
-        out.grid[k] = (int)std::min<long long>((long long)nb * c->sm_count, (bk.n + w - 1) / w);
-        // each class has its own region: the classes run concurrently on their streams
-        out.offset[k] = need;
-        need += (out.slot_b[k] * (size_t)out.grid[k] * w + 255) & ~(size_t)255;
+        per_frame += 16 * (size_t)bk.n * frame_rec_h(bk.nv_max, c->opt.n_iter_pbd, ns);
     }
-    out.bytes = need + 2 * 16 * (size_t)c->Et + 4 * sizeof(V3<double>) * (size_t)c->V + 1024;
+    int C = (int)std::max<size_t>(1, std::min<size_t>(16, rec_budget / std::max<size_t>(per_frame, 1)));
+    if (C >= K) C = (C / K) * K;   // chunks start at checkpoints
+    size_t need = 0;
+    for (size_t k = 0; k < nb_; ++k) {
+        const Bucket& bk = c->buckets[k];
+        const int NV = bk.nv_max;
+        out.C[k] = C;
+        out.r3_rod[k] = (size_t)C * frame_rec_h(NV, c->opt.n_iter_pbd, out.nsmax[k]);
+        out.l2_rod[k] = C < K ? (size_t)K * (5 * (size_t)NV + 6) : 0;
+        out.cs_rod[k] = 5 * (size_t)NV + 6;
+        out.offset[k] = need;   // each class has its own region: the classes run concurrently
+        need += (16 * (size_t)bk.n * (out.r3_rod[k] + out.l2_rod[k] + out.cs_rod[k]) + 255) & ~(size_t)255;
+    }
+    out.fixed = (2 * 16 * (size_t)c->Et + 4 * sizeof(V3<double>) * (size_t)c->V + 1024 + 255) & ~(size_t)255;
+    out.bytes = out.fixed + need;
     return DLO_OK;
+}
+
+dlo_status enqueue_backward_class(dlo_ctx* c, const BwdPlan& plan, size_t k, cudaStream_t st, int item0, int n,
+                                  float4* R3, float4* L2, float4* CS, int C, const BwdParams& common) {
+    const Bucket& bk = c->buckets[k];
+    BwdParams P = common;
+    P.order = bk.d_order;
+    P.item0 = item0;
+    P.n_items = n;
+    P.counter = c->d_counters + kNumSizeClasses + k;
+    P.nsub_max = plan.nsmax[k];
+    P.R3 = R3;
+    P.L2 = L2;
+    P.CS = CS;
+    backward_rod_f4(c, plan, k, C, P.r3_rod, P.l2_rod, P.cs_rod);
+    int rec_w, rec_nb, rev_w, rev_nb;
+    best_shape(bk.nv_max, bk.contact, true, rec_w, rec_nb);
+    best_shape(bk.nv_max, bk.contact, false, rev_w, rev_nb);
+    const int rec_grid = (int)std::min<long long>((long long)rec_nb * c->sm_count, (n + rec_w - 1) / rec_w);
+    const int rev_grid = (int)std::min<long long>((long long)rev_nb * c->sm_count, (n + rev_w - 1) / rev_w);
+    const int K = c->ck_every, F = c->rec_frames;
+    // the chunks, first to last: from every checkpoint when C >= K (C a multiple of K), else
+    // within each segment
+    std::vector<std::pair<int, int>> chunks;
+    if (C >= K) {
+        for (int fa = 0; fa < F; fa += C) chunks.push_back({fa, std::min(fa + C, F)});
+    } else {
+        for (int f0 = 0; f0 < F; f0 += K) {
+            const int f1 = std::min(f0 + K, F);
+            for (int fa = f0; fa < f1; fa += C) chunks.push_back({fa, std::min(fa + C, f1)});
+        }
+    }
+    for (size_t q = chunks.size(); q-- > 0;) {
+        const int fa = chunks[q].first, fb = chunks[q].second;
+        const int f0 = (fa / K) * K;
+        cudaError_t e = cudaSuccess;
+        if (C < K && fb == std::min(f0 + K, F)) {   // entering a segment: its frame-start states
+            P.mode = 0;
+            P.fa = f0;
+            P.fb = f0;
+            e = cudaMemsetAsync(P.counter, 0, sizeof(int), st);
+            if (e == cudaSuccess) e = launch_rec(P, bk.nv_max, bk.contact, rec_grid, rec_w, st);
+            c->launches++;
+        }
+        P.mode = 1;
+        P.fa = fa;
+        P.fb = fb;
+        if (e == cudaSuccess) e = cudaMemsetAsync(P.counter, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = launch_rec(P, bk.nv_max, bk.contact, rec_grid, rec_w, st);
+        P.first_chunk = fb == F;
+        P.last_chunk = fa == 0;
+        if (e == cudaSuccess) e = cudaMemsetAsync(P.counter, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = launch_rev(P, bk.nv_max, bk.contact, rev_grid, rev_w, st);
+        c->launches += 2;
+        if (e != cudaSuccess) return cuda_err(c, e, "backward launch");
+    }
+    return DLO_OK;
+}
+
+void backward_rod_f4(dlo_ctx* c, const BwdPlan& plan, size_t k, int C, size_t& r3, size_t& l2, size_t& cs) {
+    const int NV = c->buckets[k].nv_max, K = c->ck_every;
+    r3 = (size_t)C * frame_rec_h(NV, c->opt.n_iter_pbd, plan.nsmax[k]);
+    l2 = C < K ? (size_t)K * (5 * (size_t)NV + 6) : 0;
+    cs = plan.cs_rod[k];
+}
+
+int backward_resident_rods(dlo_ctx* c, size_t k) {
+    int w, nb;
+    best_shape(c->buckets[k].nv_max, c->buckets[k].contact, false, w, nb);
+    return w * nb * c->sm_count;
+}
+
+// the inputs and outputs shared by every launch of one backward
+BwdParams backward_common(dlo_ctx* c, int force, const float* dL_dx_T, const float* dL_dv_T, const float* dL_dtheta_T,
+                          float* dL_dactions, float* dL_dmaterial, float* dL_dx0, float* dL_dv0, float* dL_dtheta0,
+                          float4* gtb0, float4* gd1b0) {
+    BwdParams P{};
+    P.rods = c->d_rods;
+    P.ck = c->ck;
+    P.ck_strideV = c->V;
+    P.ck_strideE = c->Et;
+    P.ck_strideB = 24LL * c->B;
+    P.ck_every = c->ck_every;
+    P.ck_count = c->ck_count;
+    P.KIN = c->d_kin;
+    P.ES = c->d_es;
+    P.actions = c->rec_actions;
+    P.frames = c->rec_frames;
+    P.B = c->B;
+    P.force_nsub = force;
+    P.dLdx = reinterpret_cast<const float4*>(dL_dx_T);
+    P.dLdv = reinterpret_cast<const float4*>(dL_dv_T);
+    P.dLdth = dL_dtheta_T;
+    P.gact = dL_dactions;
+    P.gmat = dL_dmaterial;
+    P.gx0 = reinterpret_cast<float4*>(dL_dx0);
+    P.gv0 = reinterpret_cast<float4*>(dL_dv0);
+    P.gth0 = dL_dtheta0;
+    P.gtb0 = gtb0;
+    P.gd1b0 = gd1b0;
+    P.scene = c->scene;
+    return P;
 }
 
 extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float* dL_dv_T, const float* dL_dtheta_T,
@@ -207,65 +356,30 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
     BwdPlan plan;
     dlo_status pst = bwd_plan(c, force, c->ck_every, plan);
     if (pst != DLO_OK) return pst;
-    const size_t need = plan.bytes;
-    const std::vector<size_t>& slot_b = plan.slot_b;
-    const std::vector<int>&warps = plan.warps, &grid = plan.grid, &nsmax = plan.nsmax;
-    const std::vector<size_t>& offset = plan.offset;
-    if (need > c->bw_bytes) {
+    if (plan.bytes > c->bw_bytes) {
         dev_free(c, c->bw_mem);
-        c->bw_mem = dev_alloc(c, need);
-        c->bw_bytes = c->bw_mem ? need : 0;
-        if (!c->bw_mem) return set_err(c, DLO_ERR_OOM, "backward scratch allocation failed");
+        c->bw_mem = dev_alloc(c, plan.bytes);
+        c->bw_bytes = c->bw_mem ? plan.bytes : 0;
+        if (!c->bw_mem) return set_err(c, DLO_ERR_OOM, "backward workspace allocation failed");
     }
     char* p = reinterpret_cast<char*>(c->bw_mem);
     float4* gtb0 = reinterpret_cast<float4*>(p);
     float4* gd1b0 = gtb0 + c->Et;
     V3<double>* work = reinterpret_cast<V3<double>*>(gd1b0 + c->Et);
-    char* scratch = reinterpret_cast<char*>(work + 4 * (size_t)c->V);
-    scratch = reinterpret_cast<char*>(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
+    char* region = p + plan.fixed;
+    const BwdParams common = backward_common(c, force, dL_dx_T, dL_dv_T, dL_dtheta_T, dL_dactions, dL_dmaterial,
+                                             dL_dx0, dL_dv0, dL_dtheta0, gtb0, gd1b0);
     {
         cudaError_t fe = fork_classes(c);
         if (fe != cudaSuccess) return cuda_err(c, fe, "fork");
     }
     for (size_t k = 0; k < c->buckets.size(); ++k) {
-        const Bucket& bk = c->buckets[k];
-        BwdParams P{};
-        P.rods = c->d_rods;
-        P.order = bk.d_order;
-        P.n_order = bk.n;
-        P.counter = c->d_counters + kNumSizeClasses + k;
-        P.ck = c->ck;
-        P.ck_strideV = c->V;
-        P.ck_strideE = c->Et;
-        P.ck_strideB = 24LL * c->B;
-        P.ck_every = c->ck_every;
-        P.ck_count = c->ck_count;
-        P.KIN = c->d_kin;
-        P.ES = c->d_es;
-        P.actions = c->rec_actions;
-        P.frames = c->rec_frames;
-        P.B = c->B;
-        P.force_nsub = force;
-        P.dLdx = reinterpret_cast<const float4*>(dL_dx_T);
-        P.dLdv = reinterpret_cast<const float4*>(dL_dv_T);
-        P.dLdth = dL_dtheta_T;
-        P.gact = dL_dactions;
-        P.gmat = dL_dmaterial;
-        P.gx0 = reinterpret_cast<float4*>(dL_dx0);
-        P.gv0 = reinterpret_cast<float4*>(dL_dv0);
-        P.gth0 = dL_dtheta0;
-        P.gtb0 = gtb0;
-        P.gd1b0 = gd1b0;
-        P.scratch = scratch + offset[k];
-        P.slot_bytes = slot_b[k];
-        P.K = c->ck_every;
-        P.nsub_max = nsmax[k];
-        P.scene = c->scene;
-        cudaStream_t sk = class_stream(c, k);
-        cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), sk);
-        if (e == cudaSuccess) e = launch_backward(P, bk.nv_max, bk.contact, grid[k], warps[k], sk);
-        c->launches++;
-        if (e != cudaSuccess) return cuda_err(c, e, "backward launch");
+        const int n = c->buckets[k].n;
+        float4* R3 = reinterpret_cast<float4*>(region + plan.offset[k]);
+        float4* L2 = R3 + (size_t)n * plan.r3_rod[k];
+        float4* CS = L2 + (size_t)n * plan.l2_rod[k];
+        dlo_status st = enqueue_backward_class(c, plan, k, class_stream(c, k), 0, n, R3, L2, CS, plan.C[k], common);
+        if (st != DLO_OK) return st;
     }
     {
         cudaError_t je = join_classes(c);

@@ -2,19 +2,24 @@
 //
 // DLO-Lab (Sec. 3.3) differentiates whole trajectories by caching one state per segment and,
 // for each segment in reverse, re-running the forward simulation before back-propagating.
-// Here the checkpoints live in HBM (written by the forward kernel every K frames) and one
-// thread group runs the whole backward of one rod:
-//   for each segment, last first: reload its checkpoint, recompute its frames storing the
-//   frame-start states (per-rod scratch); for each frame, last first: recompute it storing
-//   the substep-start states; for each substep, last first: recompute it once more recording
-//   its intermediates (velocity before contact, PBD iteration snapshots, displacement before
-//   friction), then apply the vector-Jacobian product of every phase in reverse order.
+// Here the checkpoints live in HBM (written by the forward kernel every K frames) and the
+// rollout is reversed in chunks of frames, last first, by two persistent kernels per chunk:
+//   rec_kernel   forward-like (several rods per CTA): re-runs the chunk's frames from their
+//                start state and stores every substep's records in HBM: its start state, the
+//                velocity before rigid contact, the displacement before friction, one record
+//                per edge and projection iteration (direction and target / length), the
+//                displacements before each contact sweep and the first iteration's pair data;
+//                for checkpoints more than a chunk apart it first stores the start state of
+//                each of the segment's frames
+//   rev_kernel   one group per rod: for each frame and substep, last first, loads the records
+//                and applies the vector-Jacobian product of every phase in reverse order; the
+//                cotangents of the rod's state are carried to the next chunk in HBM
 // Second-order terms of the elastic forces are exact: the hinge gradient (a hand reverse pass)
 // is re-run on dual numbers, giving d/de [dU/dz](x + e lambda) for every input z, which is
 // the transpose-Jacobian product of the force (U's Hessian is symmetric).  Branches (contact
 // on/off, yield, strain-limit activity, pair sets) follow the recomputed forward.
 #pragma once
-#include "dlo_step.cuh"
+#include "dlo_fwd_kernel.cuh"
 
 namespace dlo {
 
@@ -207,12 +212,14 @@ __device__ __forceinline__ V3<float> mul_rm(const float* o, V3<float> v) {
 // On entry the shared state holds S_n (the substep's start), the recorded intermediates and,
 // for a self-contact rod, the frame's pair list and the projection data of the first
 // iteration; the cotangent arrays hold the cotangents of S_{n+1}.  On exit they hold those
-// of S_n.  gm accumulates (kA, Bm, beta, sigma_y, c_d) cotangents, lpf/lphif the frame-start
-// pose cotangents and ga the frame's action cotangents (all per g.tid).
+// of S_n.  PBD: the substep's projection records ([n_iter][NV], see Rec::pbd); CSN: its
+// displacements before each contact sweep ([n_iter][NV]).  gm accumulates (kA, Bm, beta,
+// sigma_y, c_d) cotangents, lpf/lphif the frame-start pose cotangents and ga the frame's
+// action cotangents (all per g.tid).
 template <int NV, bool CONTACT, int TPR>
 __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& R, Smem<NV, CONTACT>& s,
-                                AdjArrays<NV, CONTACT>& a, const float4* SN, const float4* CS, const Grp<TPR>& g, float h,
-                                float c0, float c1, int np,
+                                AdjArrays<NV, CONTACT>& a, const float4* PBD, const float4* CSN, const Grp<TPR>& g,
+                                float h, float c0, float c1, int np,
                                 double* gm, float* lpf, float* lphif, float* ga) {
     const SceneDev& sc = P.scene;
     const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
@@ -244,8 +251,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
     // ---- B2: self-contact friction
     if (CONTACT && np > 0) {
         // displacements at the first contact sweep (after the colours of iteration 0)
-        const int ncol0 = lenc ? ((closed && (ne & 1)) ? 3 : 2) : 0;
-        const float4* T0 = ncol0 ? CS + (size_t)(ncol0 - 1) * NV : SN;
+        const float4* T0 = CSN;
         float4* LTMP = s.HB0;
         for (int i = g.tid; i < nv; i += TPR) LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         g.sync();
@@ -312,11 +318,8 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
     if (lenc || (CONTACT && np > 0)) {
         const int ncol = lenc ? ((closed && (ne & 1)) ? 3 : 2) : 0;
         for (int it = sc.n_iter - 1; it >= 0; --it) {
-            // displacements before colour k (k < ncol) and before the contact sweep (k = ncol)
-            const float4* Cpre[4] = {SN + (size_t)it * NV, CS + ((size_t)it * 3) * NV, CS + ((size_t)it * 3 + 1) * NV,
-                                     CS + ((size_t)it * 3 + 2) * NV};
             if (CONTACT && np > 0) {
-                const float4* Dc = Cpre[ncol];
+                const float4* Dc = CSN + (size_t)it * NV;   // displacements before the contact sweep
                 float4* LTMP = a.LG;
                 for (int i = g.tid; i < nv; i += TPR) LTMP[i] = make_float4(0.f, 0.f, 0.f, 0.f);
                 g.sync();
@@ -374,32 +377,21 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                 }
                 g.sync();
             }
+            // colours in reverse, from each edge's record (unit direction t, ratio r = target /
+            // length): the projection moved its ends by -+ w lambda t, lambda = (l - target) / ws
+            const float4* Q = PBD + (size_t)it * NV;
             for (int k = ncol - 1; k >= 0; --k) {
-                const float4* D = Cpre[k];
                 int first, last;
                 color_range(ne, closed, k, first, last);
-                const bool inext = R.flags & ROD_INEXT;
                 for (int j = first + 2 * g.tid; j < last; j += 2 * TPR) {
                     const int j1 = (j + 1 == nv) ? 0 : j + 1;
-                    float4 A = D[j], B = D[j1];
-                    V3<float> e = (f3(s.X0[j1]) - f3(s.X0[j])) + (f3(B) - f3(A));
-                    float ell = sqrtf(dot(e, e));
-                    float eb = s.ET[j].w, target;
-                    bool active;
-                    if (inext) {
-                        target = eb;
-                        active = true;
-                    } else {
-                        float hi = (1.f + R.slim) * eb, lo = (1.f - R.slim) * eb;
-                        active = (ell > hi) || (ell < lo);
-                        target = ell > hi ? hi : lo;
-                    }
-                    float ws = A.w + B.w;
-                    if (!active || !(ws > 0.f)) continue;
-                    V3<float> t = e / ell;
+                    const float4 q = Q[j];
+                    if (q.x == 0.f && q.y == 0.f && q.z == 0.f) continue;   // the projection did nothing
+                    const float wa = s.X0[j].w, wb = s.X0[j1].w, ws = wa + wb;
+                    const V3<float> t = f3(q);
                     V3<float> la = f3(a.LD[j]), lb = f3(a.LD[j1]);
-                    V3<float> mu = (A.w / ws) * la - (B.w / ws) * lb;
-                    V3<float> le = mu - (target / ell) * (mu - dot(mu, t) * t);
+                    V3<float> mu = (wa / ws) * la - (wb / ws) * lb;
+                    V3<float> le = mu - q.w * (mu - dot(mu, t) * t);
                     a.LD[j] = f4(la - le, 0.f);
                     a.LD[j1] = f4(lb + le, 0.f);
                     a.LX[j] = f4(f3(a.LX[j]) - le, 0.f);
@@ -637,9 +629,136 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
     g.sync();
 }
 
-// ------------------------------------------------------------------ the backward kernel
+// ------------------------------------------------------------------ record layout
+// Records of one chunk of frames, per rod (float4 units; NV the size class, n the substeps
+// reserved per frame, N the projection iterations):
+//   per frame, kFrameHead + NV:  its start pose (24 floats) and candidate count (int at float 24),
+//                                then its candidate pairs (4 NV uint32)
+//   per substep, sub_rec(NV, N): start state (X0, V, HG, ED, ET; 5 NV), v1 (NV), dfin (NV),
+//                                projection records (N NV), contact snapshots (N NV), first-
+//                                iteration pair data fr0, fr1 (4 NV each)
+// Only what a frame uses is written and read (projection records for length-constrained rods,
+// snapshots and pair data for frames with candidates).
+constexpr int kFrameHead = 8;
+__host__ __device__ constexpr size_t sub_rec(int NV, int n_iter) {
+    return (size_t)(7 + 2 * n_iter + 2 * kPairsPerVertex) * NV;
+}
+__host__ __device__ constexpr size_t frame_rec(int NV, int n_iter, int nsub) {
+    return (size_t)(kFrameHead + NV) + (size_t)nsub * sub_rec(NV, n_iter);
+}
+// frame-start state of one frame of a segment: X0, V, HG, ED, ET and the pose (24 floats)
+__host__ __device__ constexpr size_t seg_state(int NV) { return (size_t)5 * NV + 6; }
+// cotangent state carried from one chunk's reverse to the next: LX, LV, LE, LT, LK, then the
+// material sums (5 doubles) and the frame-start pose cotangents (12 floats)
+__host__ __device__ constexpr size_t cot_state(int NV) { return (size_t)5 * NV + 6; }
+
+// ------------------------------------------------------------------ the recompute kernel
+// Persistent, forward-like (a group of threads per rod, state in shared memory, several rods
+// per CTA).  mode 0: from the checkpoint of the segment that holds frame fa, store the start
+// state of each of the segment's frames (L2).  mode 1: from the start state of frame fa (a
+// checkpoint, or the segment's stored state), run frames fa .. fb-1 storing every substep's
+// records (R3).
 template <int NV, bool CONTACT>
-__global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
+__global__ void __launch_bounds__(kFwdMaxThreads) rec_kernel(BwdParams P) {
+    constexpr int TPR = threads_per_rod(NV);
+    extern __shared__ float4 dyn_smem[];
+    const int slot = threadIdx.x / TPR;
+    Smem<NV, CONTACT> s(dyn_smem + slot * (rod_smem_bytes(NV, CONTACT) / 16));
+    const Grp<TPR> g{(int)(threadIdx.x % TPR), 1 + slot, s.red};
+    const SceneDev& sc = P.scene;
+    const int n_iter = sc.n_iter;
+    const size_t SR = sub_rec(NV, n_iter), FR = frame_rec(NV, n_iter, P.nsub_max);
+    if (CONTACT)   // the contact accumulators start at zero; every sweep leaves them at zero
+        for (int i = g.tid; i < NV; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
+    for (;;) {
+        const int k = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
+        if (k >= P.n_items) break;
+        const int rod = P.order[P.item0 + k];
+        const RodInfo R = P.rods[rod];
+        const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
+        const float h = sc.dt / (float)nsub;
+        const int seg = P.fa / P.ck_every, f0 = seg * P.ck_every;
+        float4* L2 = P.L2 + (size_t)k * P.l2_rod;
+        if (P.mode == 0 || P.fa == f0) {   // the segment's checkpoint
+            const long long oV = seg * P.ck_strideV, oE = seg * P.ck_strideE;
+            for (int i = g.tid; i < R.nv; i += TPR) {
+                const float4 x = P.ck.X[oV + R.v0 + i];
+                s.X0[i] = x;
+                s.X[i] = x;
+                s.V[i] = P.ck.Vl[oV + R.v0 + i];
+                s.HG[i] = P.ck.HG[oV + R.v0 + i];
+            }
+            for (int j = g.tid; j < R.ne; j += TPR) {
+                s.ED[j] = P.ck.ED[oE + R.e0 + j];
+                s.ET[j] = P.ck.ET[oE + R.e0 + j];
+            }
+            if (g.tid < 24) s.fp[g.tid] = P.ck.GP[seg * P.ck_strideB + 24LL * rod + g.tid];
+        } else {                            // the stored start state of frame fa
+            const float4* e = L2 + (size_t)(P.fa - f0) * seg_state(NV);
+            for (int i = g.tid; i < R.nv; i += TPR) {
+                const float4 x = e[i];
+                s.X0[i] = x;
+                s.X[i] = x;
+                s.V[i] = e[NV + i];
+                s.HG[i] = e[2 * NV + i];
+            }
+            for (int j = g.tid; j < R.ne; j += TPR) {
+                s.ED[j] = e[3 * NV + j];
+                s.ET[j] = e[4 * NV + j];
+            }
+            if (g.tid < 24) s.fp[g.tid] = reinterpret_cast<const float*>(e + 5 * NV)[g.tid];
+        }
+        g.sync();
+        bool ovf = false;
+        if (P.mode == 0) {
+            const int f1 = min(f0 + P.ck_every, P.frames);
+            for (int f = f0; f < f1; ++f) {
+                float4* e = L2 + (size_t)(f - f0) * seg_state(NV);
+                save_state<NV, CONTACT, TPR>(e, R, g, s);
+                if (g.tid < 24) reinterpret_cast<float*>(e + 5 * NV)[g.tid] = s.fp[g.tid];
+                if (f + 1 == f1) break;   // the segment's last frame only needs its start state
+                if (g.tid < 12) s.act[g.tid] = P.actions[((size_t)f * P.B + rod) * 12 + g.tid];
+                g.sync();
+                run_frame<NV, CONTACT, TPR, true>(sc, P.KIN, P.ES, R, s, g, nsub, h, ovf,
+                                                  [](int) -> const Rec* { return nullptr; });
+            }
+        } else {
+            float4* R3 = P.R3 + (size_t)k * P.r3_rod;
+            for (int f = P.fa; f < P.fb; ++f) {
+                float4* fb = R3 + (size_t)(f - P.fa) * FR;
+                if (g.tid < 24) reinterpret_cast<float*>(fb)[g.tid] = s.fp[g.tid];
+                if (g.tid < 12) s.act[g.tid] = P.actions[((size_t)f * P.B + rod) * 12 + g.tid];
+                g.sync();
+                Rec recs;
+                const int np = run_frame<NV, CONTACT, TPR, true>(
+                    sc, P.KIN, P.ES, R, s, g, nsub, h, ovf, [&](int sb) -> const Rec* {
+                        float4* e3 = fb + kFrameHead + NV + (size_t)sb * SR;
+                        save_state<NV, CONTACT, TPR>(e3, R, g, s);
+                        recs = Rec{e3 + 5 * NV, e3 + 6 * NV, e3 + 7 * NV, e3 + (size_t)(7 + n_iter) * NV,
+                                   e3 + (size_t)(7 + 2 * n_iter) * NV,
+                                   e3 + (size_t)(7 + 2 * n_iter + kPairsPerVertex) * NV, NV};
+                        g.sync();   // the substep overwrites what was just stored
+                        return &recs;
+                    });
+                if (CONTACT) {
+                    uint32_t* pl = reinterpret_cast<uint32_t*>(fb + kFrameHead);
+                    for (int p = g.tid; p < np; p += TPR) pl[p] = s.pairs[p];
+                    if (g.tid == 0) reinterpret_cast<int*>(fb)[24] = np;
+                }
+            }
+        }
+        g.sync();
+    }
+}
+
+// ------------------------------------------------------------------ the reverse kernel
+// Persistent, one group of threads per rod: for frames fb-1 .. fa, last first, and each
+// frame's substeps, last first, load the substep's records and apply the reverse of every
+// phase (reverse_substep).  The cotangents of the rod's state at frame fb come from dL/d(final
+// state) on the first chunk (fb = F), else from the previous chunk's launch (CS); those at fa
+// go to CS, or to the outputs on the last chunk (fa = 0).
+template <int NV, bool CONTACT>
+__global__ void __launch_bounds__(kBwdMaxThreads) rev_kernel(BwdParams P) {
     constexpr int TPR = threads_per_rod(NV);
     extern __shared__ float4 dyn_smem[];
     const int rs = threadIdx.x / TPR;
@@ -647,181 +766,176 @@ __global__ void __launch_bounds__(kBwdMaxThreads) bwd_kernel(BwdParams P) {
     Smem<NV, CONTACT> s(base);
     AdjArrays<NV, CONTACT> a(base + rod_smem_bytes(NV, CONTACT) / 16);
     const Grp<TPR> g{(int)(threadIdx.x % TPR), 1 + rs, s.red};
-    const size_t slot = (size_t)blockIdx.x * (blockDim.x / TPR) + rs;
-    float4* L2 = reinterpret_cast<float4*>(P.scratch + slot * P.slot_bytes);
-    // per-rod scratch: frame-start states of one segment (L2), then per substep of one frame
-    // its start state and recorded intermediates (L3): state 5 NV, v1 NV, dfin NV, pair data
-    // 2 x kPairsPerVertex NV, PBD iteration snapshots n_iter NV, colour snapshots 3 n_iter NV
-    const size_t E2 = 5 * NV + 6, E3 = (size_t)(7 + 2 * kPairsPerVertex) * NV + (size_t)4 * P.scene.n_iter * NV;
-    float4* L3 = L2 + (size_t)P.K * E2;
     const SceneDev& sc = P.scene;
-    if (CONTACT)   // the contact accumulators start at zero; every sweep leaves them at zero
-        for (int i = g.tid; i < NV; i += TPR) s.acc[i] = make_int4(0, 0, 0, 0);
+    const int n_iter = sc.n_iter;
+    const size_t SR = sub_rec(NV, n_iter), FR = frame_rec(NV, n_iter, P.nsub_max);
     for (;;) {
-        const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
-        if (item >= P.n_order) break;
-        const int rod = P.order[item];
+        const int k = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
+        if (k >= P.n_items) break;
+        const int rod = P.order[P.item0 + k];
         const RodInfo R = P.rods[rod];
         const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
         const float h = sc.dt / (float)nsub;
-        for (int i = g.tid; i < R.nv; i += TPR) {
-            float4 dx = P.dLdx ? P.dLdx[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 dv = P.dLdv ? P.dLdv[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!(R.flags & ROD_CLOSED) && i == R.nv - 1) dv.w = 0.f;
-            a.LX[i] = make_float4(dx.x, dx.y, dx.z, 0.f);
-            a.LV[i] = dv;
-            a.LK[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        for (int j = g.tid; j < R.ne; j += TPR) {
-            a.LE[j] = make_float4(0.f, 0.f, 0.f, P.dLdth ? P.dLdth[R.e0 + j] : 0.f);
-            a.LT[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        g.sync();
+        float4* CS = P.CS + (size_t)k * P.cs_rod;
         double gm[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // FP64: these sums cancel strongly
         float lpf[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, lphif[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (P.first_chunk) {
+            for (int i = g.tid; i < R.nv; i += TPR) {
+                float4 dx = P.dLdx ? P.dLdx[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 dv = P.dLdv ? P.dLdv[R.v0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!(R.flags & ROD_CLOSED) && i == R.nv - 1) dv.w = 0.f;
+                a.LX[i] = make_float4(dx.x, dx.y, dx.z, 0.f);
+                a.LV[i] = dv;
+                a.LK[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            for (int j = g.tid; j < R.ne; j += TPR) {
+                a.LE[j] = make_float4(0.f, 0.f, 0.f, P.dLdth ? P.dLdth[R.e0 + j] : 0.f);
+                a.LT[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {   // the sums are carried by thread 0 of the group
+            for (int i = g.tid; i < R.nv; i += TPR) {
+                a.LX[i] = CS[i];
+                a.LV[i] = CS[NV + i];
+                a.LK[i] = CS[4 * NV + i];
+            }
+            for (int j = g.tid; j < R.ne; j += TPR) {
+                a.LE[j] = CS[2 * NV + j];
+                a.LT[j] = CS[3 * NV + j];
+            }
+            if (g.tid == 0) {
+                const double* d = reinterpret_cast<const double*>(CS + 5 * NV);
+                const float* q = reinterpret_cast<const float*>(CS + 5 * NV + 3);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) gm[c] = d[c];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    lpf[c] = q[c];
+                    lphif[c] = q[6 + c];
+                }
+            }
+        }
         float ga[12];
-        bool ovf = false;
-        for (int seg = P.ck_count - 1; seg >= 0; --seg) {
-            const int f0 = seg * P.ck_every, f1 = min(f0 + P.ck_every, P.frames);
-            // reload the checkpoint of the segment
-            {
-                const long long oV = seg * P.ck_strideV, oE = seg * P.ck_strideE;
-                for (int i = g.tid; i < R.nv; i += TPR) {
-                    float4 x = P.ck.X[oV + R.v0 + i];
-                    s.X0[i] = x;
-                    s.X[i] = x;
-                    s.V[i] = P.ck.Vl[oV + R.v0 + i];
-                    s.HG[i] = P.ck.HG[oV + R.v0 + i];
-                }
-                for (int j = g.tid; j < R.ne; j += TPR) {
-                    s.ED[j] = P.ck.ED[oE + R.e0 + j];
-                    s.ET[j] = P.ck.ET[oE + R.e0 + j];
-                }
-                g.sync();
+        for (int f = P.fb - 1; f >= P.fa; --f) {
+            const float4* fb = P.R3 + (size_t)k * P.r3_rod + (size_t)(f - P.fa) * FR;
+            g.sync();   // the previous frame's reverse has finished reading s.act, s.f0 and the pairs
+            if (g.tid < 12) s.act[g.tid] = P.actions[((size_t)f * P.B + rod) * 12 + g.tid];
+            if (g.tid < 24) s.f0[g.tid] = reinterpret_cast<const float*>(fb)[g.tid];
+            int np = 0;
+            if (CONTACT) {
+                np = reinterpret_cast<const int*>(fb)[24];
+                const uint32_t* pl = reinterpret_cast<const uint32_t*>(fb + kFrameHead);
+                for (int p = g.tid; p < np; p += TPR) s.pairs[p] = pl[p];
             }
-            if (g.tid < 24) s.fp[g.tid] = P.ck.GP[seg * P.ck_strideB + 24LL * rod + g.tid];
             g.sync();
-            // level 2: frame-start states of the segment
-            for (int f = f0; f < f1; ++f) {
-                float4* e = L2 + (size_t)(f - f0) * E2;
-                save_state<NV, CONTACT, TPR>(e, R, g, s);
-                if (g.tid < 24) reinterpret_cast<float*>(e + 5 * NV)[g.tid] = s.fp[g.tid];
-                g.sync();
-                if (f + 1 == f1) break;   // the segment's last frame only needs its start state
-                if (g.tid < 12) s.act[g.tid] = P.actions[((size_t)f * P.B + rod) * 12 + g.tid];
-                g.sync();
-                run_frame<NV, CONTACT, TPR, false>(sc, P.KIN, P.ES, R, s, g, nsub, h, ovf,
-                                            [](int) -> const Rec* { return nullptr; });
+            // carry the pose cotangent of frame f+1's start into this frame's actions
+#pragma unroll
+            for (int c = 0; c < 12; ++c) ga[c] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q >= R.ngrip) break;
+                const V3<float> dphi = f3(s.act[6 * q + 3], s.act[6 * q + 4], s.act[6 * q + 5]);
+                const V3<float> lp = get3(lpf, q), lr = get3(lphif, q);
+                ga[6 * q] = lp.x;
+                ga[6 * q + 1] = lp.y;
+                ga[6 * q + 2] = lp.z;
+                const V3<float> jr = jl_t(dphi, lr);
+                ga[6 * q + 3] = jr.x;
+                ga[6 * q + 4] = jr.y;
+                ga[6 * q + 5] = jr.z;
+                const V3<float> nr = mulT(expmap(dphi), lr);
+                lphif[3 * q] = nr.x;
+                lphif[3 * q + 1] = nr.y;
+                lphif[3 * q + 2] = nr.z;
             }
-            for (int f = f1 - 1; f >= f0; --f) {
-                g.sync();   // the previous frame's reverse has finished reading s.act
-                if (g.tid < 12) s.act[g.tid] = P.actions[((size_t)f * P.B + rod) * 12 + g.tid];
-                g.sync();
-                // carry the pose cotangent of frame f+1's start into this frame's actions
-#pragma unroll
-                for (int k = 0; k < 12; ++k) ga[k] = 0.f;
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    if (q >= R.ngrip) break;
-                    const V3<float> dphi = f3(s.act[6 * q + 3], s.act[6 * q + 4], s.act[6 * q + 5]);
-                    const V3<float> lp = get3(lpf, q), lr = get3(lphif, q);
-                    ga[6 * q] = lp.x;
-                    ga[6 * q + 1] = lp.y;
-                    ga[6 * q + 2] = lp.z;
-                    const V3<float> jr = jl_t(dphi, lr);
-                    ga[6 * q + 3] = jr.x;
-                    ga[6 * q + 4] = jr.y;
-                    ga[6 * q + 5] = jr.z;
-                    const V3<float> nr = mulT(expmap(dphi), lr);
-                    lphif[3 * q] = nr.x;
-                    lphif[3 * q + 1] = nr.y;
-                    lphif[3 * q + 2] = nr.z;
+            for (int sb = nsub - 1; sb >= 0; --sb) {
+                const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
+                // the substep's gripper block (read after the barrier below)
+                if (g.tid < R.ngrip) substep_pose(s.f0, s.act, g.tid, c0, c1, sb == 0, 1.f / sc.dt, s.sp);
+                // the reverse's pose maps, on other threads (another warp where there is one)
+                constexpr int PT = TPR > 32 ? 32 : 2;
+                if (g.tid >= PT && g.tid < PT + 4 * R.ngrip) pose_rev_mat(s.act, g.tid - PT, c0, c1, a.PM);
+                // the substep's start state and recorded intermediates
+                const float4* e3 = fb + kFrameHead + NV + (size_t)sb * SR;
+                load_state<NV, CONTACT, TPR>(e3, R, g, s);
+                for (int i = g.tid; i < R.nv; i += TPR) {
+                    a.V1[i] = e3[5 * NV + i];
+                    a.DF[i] = e3[6 * NV + i];
                 }
-                // level 3: substep-start states of this frame
-                const float4* e = L2 + (size_t)(f - f0) * E2;
-                load_state<NV, CONTACT, TPR>(e, R, g, s);
-                if (g.tid < 24) {   // the frame's start pose: s.f0 for the reverse, s.fp to step from
-                    const float pv = reinterpret_cast<const float*>(e + 5 * NV)[g.tid];
-                    s.f0[g.tid] = pv;
-                    s.fp[g.tid] = pv;
-                }
-                g.sync();
-                Rec recs;
-                const int np = run_frame<NV, CONTACT, TPR, true>(
-                    sc, P.KIN, P.ES, R, s, g, nsub, h, ovf, [&](int sb) -> const Rec* {
-                        float4* e3 = L3 + (size_t)sb * E3;
-                        save_state<NV, CONTACT, TPR>(e3, R, g, s);
-                        float4* sn = e3 + (7 + 2 * kPairsPerVertex) * NV;
-                        recs = Rec{sn, e3 + 5 * NV, e3 + 6 * NV, e3 + 7 * NV, e3 + (7 + kPairsPerVertex) * NV,
-                                   sn + (size_t)sc.n_iter * NV, NV};
-                        return &recs;
-                    });
-                g.sync();
-                for (int sb = nsub - 1; sb >= 0; --sb) {
-                    const float c0 = (float)sb / (float)nsub, c1 = (float)(sb + 1) / (float)nsub;
-                    // the substep's gripper block (read after the barrier below)
-                    if (g.tid < R.ngrip) substep_pose(s.f0, s.act, g.tid, c0, c1, sb == 0, 1.f / sc.dt, s.sp);
-                    // the reverse's pose maps, on other threads (another warp where there is one)
-                    constexpr int PT = TPR > 32 ? 32 : 2;
-                    if (g.tid >= PT && g.tid < PT + 4 * R.ngrip) pose_rev_mat(s.act, g.tid - PT, c0, c1, a.PM);
-                    // the substep's start state and recorded intermediates
-                    const float4* e3 = L3 + (size_t)sb * E3;
-                    load_state<NV, CONTACT, TPR>(e3, R, g, s);
-                    for (int i = g.tid; i < R.nv; i += TPR) {
-                        a.V1[i] = e3[5 * NV + i];
-                        a.DF[i] = e3[6 * NV + i];
+                if (CONTACT)
+                    for (int p = g.tid; p < np; p += TPR) {
+                        s.fr0[p] = e3[(7 + 2 * n_iter) * NV + p];
+                        s.fr1[p] = e3[(7 + 2 * n_iter + kPairsPerVertex) * NV + p];
                     }
-                    if (CONTACT)
-                        for (int p = g.tid; p < np; p += TPR) {
-                            s.fr0[p] = e3[7 * NV + p];
-                            s.fr1[p] = e3[(7 + kPairsPerVertex) * NV + p];
-                        }
-                    g.sync();
-                    const float4* sn = e3 + (7 + 2 * kPairsPerVertex) * NV;
-                    reverse_substep<NV, CONTACT, TPR>(P, R, s, a, sn, sn + (size_t)sc.n_iter * NV, g, h, c0, c1, np,
-                                                      gm, lpf, lphif, ga);
-                }
-                if (P.gact) {
+                g.sync();
+                reverse_substep<NV, CONTACT, TPR>(P, R, s, a, e3 + 7 * NV, e3 + (size_t)(7 + n_iter) * NV, g, h, c0,
+                                                  c1, np, gm, lpf, lphif, ga);
+            }
+            if (P.gact) {
 #pragma unroll
-                    for (int k = 0; k < 12; ++k) {
-                        if (k >= 6 * R.ngrip) break;
-                        const float v = (float)grp_sum<TPR>((double)ga[k], g);
-                        if (g.tid == 0) P.gact[((size_t)f * P.B + rod) * 12 + k] = v;
-                    }
-                    if (g.tid == 0)
-                        for (int k = 6 * R.ngrip; k < 12; ++k) P.gact[((size_t)f * P.B + rod) * 12 + k] = 0.f;
+                for (int c = 0; c < 12; ++c) {
+                    if (c >= 6 * R.ngrip) break;
+                    const float v = (float)grp_sum<TPR>((double)ga[c], g);
+                    if (g.tid == 0) P.gact[((size_t)f * P.B + rod) * 12 + c] = v;
                 }
+                if (g.tid == 0)
+                    for (int c = 6 * R.ngrip; c < 12; ++c) P.gact[((size_t)f * P.B + rod) * 12 + c] = 0.f;
             }
         }
-        // outputs
-        for (int i = g.tid; i < R.nv; i += TPR) {
-            if (P.gx0) P.gx0[R.v0 + i] = a.LX[i];
-            if (P.gv0) P.gv0[R.v0 + i] = a.LV[i];
-        }
-        for (int j = g.tid; j < R.ne; j += TPR) {
-            if (P.gth0) P.gth0[R.e0 + j] = a.LE[j].w;
-            P.gtb0[R.e0 + j] = a.LT[j];
-            P.gd1b0[R.e0 + j] = make_float4(a.LE[j].x, a.LE[j].y, a.LE[j].z, 0.f);
-        }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) gm[k] = grp_sum<TPR>(gm[k], g);
-        if (g.tid == 0 && P.gmat) {
-            const double r = R.radius, A = 3.14159265358979323846 * r * r, r2 = r * r;
-            P.gmat[5 * rod + 0] = R.kA > 0.f ? (float)(gm[0] * A) : 0.f;   // K_stretch
-            P.gmat[5 * rod + 1] = (float)(gm[1] * A * r2 / 4.0);            // E_bend
-            P.gmat[5 * rod + 2] = (float)(gm[2] * A * r2 / 2.0);            // G_twist
-            P.gmat[5 * rod + 3] = (float)gm[3];                             // yield curvature
-            P.gmat[5 * rod + 4] = (float)gm[4];                             // damping
+        for (int c = 0; c < 5; ++c) gm[c] = grp_sum<TPR>(gm[c], g);
+        if (P.last_chunk) {   // outputs: the cotangents of the initial state and the material
+            for (int i = g.tid; i < R.nv; i += TPR) {
+                if (P.gx0) P.gx0[R.v0 + i] = a.LX[i];
+                if (P.gv0) P.gv0[R.v0 + i] = a.LV[i];
+            }
+            for (int j = g.tid; j < R.ne; j += TPR) {
+                if (P.gth0) P.gth0[R.e0 + j] = a.LE[j].w;
+                P.gtb0[R.e0 + j] = a.LT[j];
+                P.gd1b0[R.e0 + j] = make_float4(a.LE[j].x, a.LE[j].y, a.LE[j].z, 0.f);
+            }
+            if (g.tid == 0 && P.gmat) {
+                const double r = R.radius, A = 3.14159265358979323846 * r * r, r2 = r * r;
+                P.gmat[5 * rod + 0] = R.kA > 0.f ? (float)(gm[0] * A) : 0.f;   // K_stretch
+                P.gmat[5 * rod + 1] = (float)(gm[1] * A * r2 / 4.0);            // E_bend
+                P.gmat[5 * rod + 2] = (float)(gm[2] * A * r2 / 2.0);            // G_twist
+                P.gmat[5 * rod + 3] = (float)gm[3];                             // yield curvature
+                P.gmat[5 * rod + 4] = (float)gm[4];                             // damping
+            }
+        } else {   // carry to the next chunk: arrays, and the group sums of gm, lpf, lphif
+            for (int i = g.tid; i < R.nv; i += TPR) {
+                CS[i] = a.LX[i];
+                CS[NV + i] = a.LV[i];
+                CS[4 * NV + i] = a.LK[i];
+            }
+            for (int j = g.tid; j < R.ne; j += TPR) {
+                CS[2 * NV + j] = a.LE[j];
+                CS[3 * NV + j] = a.LT[j];
+            }
+            float q[12];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                q[c] = (float)grp_sum<TPR>((double)lpf[c], g);
+                q[6 + c] = (float)grp_sum<TPR>((double)lphif[c], g);
+            }
+            if (g.tid == 0) {
+                double* d = reinterpret_cast<double*>(CS + 5 * NV);
+                float* qq = reinterpret_cast<float*>(CS + 5 * NV + 3);
+#pragma unroll
+                for (int c = 0; c < 5; ++c) d[c] = gm[c];
+#pragma unroll
+                for (int c = 0; c < 12; ++c) qq[c] = q[c];
+            }
         }
         g.sync();
     }
 }
 
+// ------------------------------------------------------------------ launch helpers
 template <int NV, bool C>
-static int bwd_occ_t(int rpc) {
+static int rev_occ_t(int rpc) {
     if (rpc < 1 || rpc * threads_per_rod(NV) > kBwdMaxThreads) return 0;
     size_t smem = bwd_smem_bytes(NV, C) * rpc;
-    auto k = bwd_kernel<NV, C>;
+    auto k = rev_kernel<NV, C>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -834,9 +948,34 @@ static int bwd_occ_t(int rpc) {
     return nb;
 }
 template <int NV, bool C>
-static cudaError_t launch_bwd_t(const BwdParams& P, int grid, int rpc, cudaStream_t st) {
+static cudaError_t launch_rev_t(const BwdParams& P, int grid, int rpc, cudaStream_t st) {
     size_t smem = bwd_smem_bytes(NV, C) * rpc;
-    auto k = bwd_kernel<NV, C>;
+    auto k = rev_kernel<NV, C>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads_per_rod(NV) * rpc, smem, st>>>(P);
+    return cudaGetLastError();
+}
+template <int NV, bool C>
+static int rec_occ_t(int rpc) {
+    if (rpc < 1 || rpc * threads_per_rod(NV) > kFwdMaxThreads) return 0;
+    size_t smem = rod_smem_bytes(NV, C) * rpc;
+    auto k = rec_kernel<NV, C>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads_per_rod(NV) * rpc, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+template <int NV, bool C>
+static cudaError_t launch_rec_t(const BwdParams& P, int grid, int rpc, cudaStream_t st) {
+    size_t smem = rod_smem_bytes(NV, C) * rpc;
+    auto k = rec_kernel<NV, C>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, threads_per_rod(NV) * rpc, smem, st>>>(P);

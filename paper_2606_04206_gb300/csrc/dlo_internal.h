@@ -75,29 +75,33 @@ struct FwdParams {
 
 struct BwdParams {
     const RodInfo* rods;
-    const int* order;
-    int n_order;
-    int* counter;
+    const int* order;         // rods of the size class in decreasing cost
+    int item0, n_items;       // this launch processes order[item0 .. item0 + n_items)
+    int* counter;             // work-queue head (zeroed before each launch)
     StateRef ck;
     long long ck_strideV, ck_strideE, ck_strideB;
     int ck_every, ck_count;
     const float4* KIN;
     const float2* ES;
-    const float* actions;   // recorded [F][B][12]
-    int frames, B, force_nsub;
-    const float4* dLdx;     // [V] or null
-    const float4* dLdv;     // [V] or null
-    const float* dLdth;     // [Etot] or null
-    float* gact;            // [F][B][12] or null
-    float* gmat;            // [B][5] or null
-    float4* gx0;            // [V] or null
-    float4* gv0;            // [V] or null
-    float* gth0;            // [Etot] or null
-    float4* gtb0;           // [Etot] cotangent of the initial base tangents
-    float4* gd1b0;          // [Etot] cotangent of the initial base d1
-    char* scratch;
-    size_t slot_bytes;
-    int K, nsub_max;
+    const float* actions;     // recorded [F][B][12]
+    int frames, B, force_nsub, nsub_max;
+    int fa, fb;               // the chunk of frames [fa, fb) of this launch
+    int mode;                 // recompute: 0 = the segment's frame-start states, 1 = the chunk's records
+    int first_chunk, last_chunk;  // reverse: fb is the last frame / fa is frame 0
+    float4* L2;               // [n_items][K][5 NV + 6] frame-start states of the current segment
+    float4* R3;               // [n_items][fb - fa][frame record] the chunk's records
+    float4* CS;               // [n_items][5 NV + 6] cotangent state carried between chunks
+    size_t l2_rod, r3_rod, cs_rod;   // float4 per item of L2, R3, CS
+    const float4* dLdx;       // [V] or null
+    const float4* dLdv;       // [V] or null
+    const float* dLdth;       // [Etot] or null
+    float* gact;              // [F][B][12] or null
+    float* gmat;              // [B][5] or null
+    float4* gx0;              // [V] or null
+    float4* gv0;              // [V] or null
+    float* gth0;              // [Etot] or null
+    float4* gtb0;             // [Etot] cotangent of the initial base tangents
+    float4* gd1b0;            // [Etot] cotangent of the initial base d1
     SceneDev scene;
 };
 

@@ -21,30 +21,45 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int NV, bool contact) {
 // Per size class (dlo_nv*.cu).
 cudaError_t launch_forward_nv32(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int forward_occ_nv32(bool c, int warps);
-cudaError_t launch_backward_nv32(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
-int backward_occ_nv32(bool c, int warps);
+cudaError_t launch_rec_nv32(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rec_occ_nv32(bool c, int warps);
+cudaError_t launch_rev_nv32(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rev_occ_nv32(bool c, int warps);
 cudaError_t launch_forward_nv64(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int forward_occ_nv64(bool c, int warps);
-cudaError_t launch_backward_nv64(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
-int backward_occ_nv64(bool c, int warps);
+cudaError_t launch_rec_nv64(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rec_occ_nv64(bool c, int warps);
+cudaError_t launch_rev_nv64(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rev_occ_nv64(bool c, int warps);
 cudaError_t launch_forward_nv128(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int forward_occ_nv128(bool c, int warps);
-cudaError_t launch_backward_nv128(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
-int backward_occ_nv128(bool c, int warps);
+cudaError_t launch_rec_nv128(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rec_occ_nv128(bool c, int warps);
+cudaError_t launch_rev_nv128(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rev_occ_nv128(bool c, int warps);
 cudaError_t launch_forward_nv192(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int forward_occ_nv192(bool c, int warps);
-cudaError_t launch_backward_nv192(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
-int backward_occ_nv192(bool c, int warps);
+cudaError_t launch_rec_nv192(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rec_occ_nv192(bool c, int warps);
+cudaError_t launch_rev_nv192(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rev_occ_nv192(bool c, int warps);
 cudaError_t launch_forward_nv224(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int forward_occ_nv224(bool c, int warps);
-cudaError_t launch_backward_nv224(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
-int backward_occ_nv224(bool c, int warps);
+cudaError_t launch_rec_nv224(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rec_occ_nv224(bool c, int warps);
+cudaError_t launch_rev_nv224(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rev_occ_nv224(bool c, int warps);
 cudaError_t launch_forward_nv256(const FwdParams& P, bool c, int grid, int warps, cudaStream_t st);
 int forward_occ_nv256(bool c, int warps);
-cudaError_t launch_backward_nv256(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
-int backward_occ_nv256(bool c, int warps);
-cudaError_t launch_backward(const BwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
-int backward_blocks_per_sm(int nv_max, bool contact, int warps);
+cudaError_t launch_rec_nv256(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rec_occ_nv256(bool c, int warps);
+cudaError_t launch_rev_nv256(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st);
+int rev_occ_nv256(bool c, int warps);
+// the backward's recompute and reverse kernels (dlo_adjoint.cu dispatches to the size classes)
+cudaError_t launch_rec(const BwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
+int rec_blocks_per_sm(int nv_max, bool contact, int warps);
+cudaError_t launch_rev(const BwdParams& P, int nv_max, bool contact, int grid, int warps, cudaStream_t st);
+int rev_blocks_per_sm(int nv_max, bool contact, int warps);
 // Shared memory of one rod: its arrays plus a 256-byte header for group reductions.
 // per rod: the arrays above, 256 B of group-reduction scratch and the 512 B gripper block
 __host__ __device__ constexpr size_t rod_smem_bytes(int NV, bool contact) { return warp_smem_bytes(NV, contact) + 768; }

@@ -8,7 +8,9 @@
 // run, and a caller that holds its memory layout fixed for its whole lifetime wants no
 // allocator activity at all.  This entry point serves them: every temporary it needs comes
 // from one file-scope static device array of kStaticScratchBytes, and it runs the same
-// backward kernels as dlo_backward with as many resident rod slots as that array holds.
+// backward kernels as dlo_backward, on as many rods at a time as that array holds: the rods
+// of each size class are reversed in groups, one group after another, each with its own
+// chunk records, frame-start states and carried cotangents in the array.
 //
 // The array is shared by every context on a device, so calls on one device must not
 // overlap: two calls in flight at once (from different host threads, or on different
@@ -80,7 +82,6 @@ extern "C" dlo_status dlo_backward_noalloc(dlo_ctx* c, const float* dL_dx_T, con
         if (p && ((uintptr_t)p & 15u)) return set_err(c, DLO_ERR_INVALID_ARG, "float4 arrays must be 16-byte aligned");
     if (c->opt.self_contact && c->opt.n_iter_pbd < 1)
         return set_err(c, DLO_ERR_INVALID_ARG, "self-contact gradients need at least one projection iteration");
-    if (c->buckets.size() > (size_t)kNumSizeClasses) return set_err(c, DLO_ERR_INVALID_ARG, "more size classes than expected");
     char* base = nullptr;
     dlo_status st = scratch_address(c, &base);
     if (st != DLO_OK) return st;
@@ -91,87 +92,52 @@ extern "C" dlo_status dlo_backward_noalloc(dlo_ctx* c, const float* dL_dx_T, con
     const size_t fixed_raw = 2 * 16 * (size_t)c->Et + (frames_adj ? 4 * sizeof(V3<double>) * (size_t)c->V : 0);
     const size_t fixed = (fixed_raw + 255) & ~(size_t)255;
     const int force = c->rec_nsub > 0 ? c->rec_nsub : 0;
-    size_t slot_b[kNumSizeClasses];
-    int warps[kNumSizeClasses], grid[kNumSizeClasses], nsmax[kNumSizeClasses];
+    BwdPlan plan;
+    st = bwd_plan(c, force, c->ck_every, plan);
+    if (st != DLO_OK) return st;
+    const size_t avail = fixed < kStaticScratchBytes ? kStaticScratchBytes - fixed : 0;
+    const int K = c->ck_every, F = c->rec_frames;
+    float4* gtb0 = reinterpret_cast<float4*>(base);
+    float4* gd1b0 = gtb0 + c->Et;
+    V3<double>* work = reinterpret_cast<V3<double>*>(gd1b0 + c->Et);
+    char* region = base + fixed;
+    const BwdParams common = backward_common(c, force, dL_dx_T, dL_dv_T, dL_dtheta_T, dL_dactions, dL_dmaterial,
+                                             dL_dx0, dL_dv0, dL_dtheta0, gtb0, gd1b0);
+    // the classes one after the other on the stream, each over the whole array
     for (size_t k = 0; k < c->buckets.size(); ++k) {
-        const Bucket& bk = c->buckets[k];
-        int w = 0, nb = 0;
-        for (int rpc = 1; rpc <= 16; ++rpc) {
-            const int b = backward_blocks_per_sm(bk.nv_max, bk.contact, rpc);
-            if (b >= 1 && rpc * b >= w * nb) {
-                w = rpc;
-                nb = b;
+        const int n = c->buckets[k].n;
+        const int want = std::min(n, backward_resident_rods(c, k));
+        // frames per chunk: the most (up to 16, a multiple of K from K on) with which the
+        // array still holds as many rods as the reverse keeps resident; else one frame
+        int C = 1, per_pass = 0;
+        size_t r3, l2, cs;
+        for (int cand = std::min(16, F); cand >= 1; --cand) {
+            if (cand > K && cand % K) continue;
+            backward_rod_f4(c, plan, k, cand, r3, l2, cs);
+            const int fit = (int)std::min<size_t>((size_t)n, avail / (16 * (r3 + l2 + cs)));
+            if (fit >= want || cand == 1) {
+                C = cand;
+                per_pass = fit;
+                break;
             }
         }
-        if (w < 1) return set_err(c, DLO_ERR_INVALID_ARG, "rod too large for the backward kernel's shared memory");
-        int ns = force;
-        if (!ns)
-            for (int b = 0; b < c->B; ++b)
-                if (size_class(c->rods_h[b].nv) == bk.nv_max) ns = std::max(ns, c->nsub[b]);
-        nsmax[k] = ns;
-        const size_t NV = bk.nv_max;
-        slot_b[k] = 16 * ((size_t)c->ck_every * (5 * NV + 6) +
-                          (size_t)ns * ((7 + 2 * kPairsPerVertex) * NV + (size_t)4 * c->opt.n_iter_pbd * NV));
-        // reject what cannot run even one rod at a time
-        if (fixed + slot_b[k] > kStaticScratchBytes) {
+        if (per_pass < 1) {
             char msg[256];
             snprintf(msg, sizeof msg,
                      "the backward needs %zu bytes of scratch for one rod of %d vertices plus %zu for the whole "
                      "batch; the static scratch holds %zu (use dlo_backward, or a shorter checkpoint interval)",
-                     slot_b[k], bk.nv_max, fixed, kStaticScratchBytes);
+                     16 * (r3 + l2 + cs), c->buckets[k].nv_max, fixed, kStaticScratchBytes);
             return set_err(c, DLO_ERR_CAPACITY, msg);
         }
-        // as many resident rod slots as the array holds, at most the natural persistent grid
-        const size_t slots = (kStaticScratchBytes - fixed) / slot_b[k];
-        w = (int)std::min<size_t>((size_t)w, slots);
-        const long long natural = std::min<long long>((long long)nb * c->sm_count, (bk.n + w - 1) / w);
-        grid[k] = (int)std::min<long long>(natural, (long long)(slots / (size_t)w));
-        warps[k] = w;
-    }
-    float4* gtb0 = reinterpret_cast<float4*>(base);
-    float4* gd1b0 = gtb0 + c->Et;
-    V3<double>* work = reinterpret_cast<V3<double>*>(gd1b0 + c->Et);
-    char* scratch = base + fixed;
-    // the buckets run one after the other on the stream, each over the whole slot area
-    for (size_t k = 0; k < c->buckets.size(); ++k) {
-        const Bucket& bk = c->buckets[k];
-        BwdParams P{};
-        P.rods = c->d_rods;
-        P.order = bk.d_order;
-        P.n_order = bk.n;
-        P.counter = c->d_counters + kNumSizeClasses + k;
-        P.ck = c->ck;
-        P.ck_strideV = c->V;
-        P.ck_strideE = c->Et;
-        P.ck_strideB = 24LL * c->B;
-        P.ck_every = c->ck_every;
-        P.ck_count = c->ck_count;
-        P.KIN = c->d_kin;
-        P.ES = c->d_es;
-        P.actions = c->rec_actions;
-        P.frames = c->rec_frames;
-        P.B = c->B;
-        P.force_nsub = force;
-        P.dLdx = reinterpret_cast<const float4*>(dL_dx_T);
-        P.dLdv = reinterpret_cast<const float4*>(dL_dv_T);
-        P.dLdth = dL_dtheta_T;
-        P.gact = dL_dactions;
-        P.gmat = dL_dmaterial;
-        P.gx0 = reinterpret_cast<float4*>(dL_dx0);
-        P.gv0 = reinterpret_cast<float4*>(dL_dv0);
-        P.gth0 = dL_dtheta0;
-        P.gtb0 = gtb0;
-        P.gd1b0 = gd1b0;
-        P.scratch = scratch;
-        P.slot_bytes = slot_b[k];
-        P.K = c->ck_every;
-        P.nsub_max = nsmax[k];
-        P.scene = c->scene;
-        // the work-queue head (context memory from dlo_create) must start at zero
-        cudaError_t e = cudaMemsetAsync(P.counter, 0, sizeof(int), c->stream);
-        if (e == cudaSuccess) e = launch_backward(P, bk.nv_max, bk.contact, grid[k], warps[k], c->stream);
-        c->launches++;
-        if (e != cudaSuccess) return cuda_err(c, e, "backward launch");
+        backward_rod_f4(c, plan, k, C, r3, l2, cs);
+        for (int i0 = 0; i0 < n; i0 += per_pass) {
+            const int m = std::min(per_pass, n - i0);
+            float4* R3 = reinterpret_cast<float4*>(region);
+            float4* L2 = R3 + (size_t)m * r3;
+            float4* CS = L2 + (size_t)m * l2;
+            st = enqueue_backward_class(c, plan, k, c->stream, i0, m, R3, L2, CS, C, common);
+            if (st != DLO_OK) return st;
+        }
     }
     if (frames_adj) {
         cudaError_t e = launch_frames_adjoint(c->d_rods, c->B, c->ck.X, gtb0, gd1b0,

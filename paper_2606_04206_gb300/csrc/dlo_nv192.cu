@@ -8,9 +8,13 @@ cudaError_t launch_forward_nv192(const FwdParams& P, bool c, int grid, int warps
     return c ? launch_fwd_t<192, true>(P, grid, warps, st) : launch_fwd_t<192, false>(P, grid, warps, st);
 }
 int forward_occ_nv192(bool c, int warps) { return c ? fwd_occ_t<192, true>(warps) : fwd_occ_t<192, false>(warps); }
-cudaError_t launch_backward_nv192(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st) {
-    return c ? launch_bwd_t<192, true>(P, grid, warps, st) : launch_bwd_t<192, false>(P, grid, warps, st);
+cudaError_t launch_rec_nv192(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st) {
+    return c ? launch_rec_t<192, true>(P, grid, warps, st) : launch_rec_t<192, false>(P, grid, warps, st);
 }
-int backward_occ_nv192(bool c, int warps) { return c ? bwd_occ_t<192, true>(warps) : bwd_occ_t<192, false>(warps); }
+int rec_occ_nv192(bool c, int warps) { return c ? rec_occ_t<192, true>(warps) : rec_occ_t<192, false>(warps); }
+cudaError_t launch_rev_nv192(const BwdParams& P, bool c, int grid, int warps, cudaStream_t st) {
+    return c ? launch_rev_t<192, true>(P, grid, warps, st) : launch_rev_t<192, false>(P, grid, warps, st);
+}
+int rev_occ_nv192(bool c, int warps) { return c ? rev_occ_t<192, true>(warps) : rev_occ_t<192, false>(warps); }
 
 }  // namespace dlo

@@ -79,17 +79,35 @@ struct dlo_ctx {
     size_t sil_bytes = 0;
 };
 
-// launch shape and workspace size of the backward for a checkpoint interval (dlo_adjoint.cu)
+// launch shapes and workspace of the chunked backward for a checkpoint interval (dlo_adjoint.cu)
 struct BwdPlan {
-    std::vector<size_t> slot_b, offset;   // per class: bytes per resident rod, scratch offset
-    std::vector<int> warps, grid, nsmax;
-    size_t bytes = 0;
+    // per size class: substeps reserved per frame, frames per chunk, float4 per rod of the
+    // chunk records (R3), of the segment's frame-start states (L2, empty when chunks start at
+    // checkpoints) and of the carried cotangent state (CS); the class's region in the workspace
+    std::vector<int> nsmax, C;
+    std::vector<size_t> r3_rod, l2_rod, cs_rod, offset;
+    size_t fixed = 0;    // initial-frame cotangents and the frame-initialisation adjoint's work
+    size_t bytes = 0;    // everything, for all rods at once
 };
 // the stream of size class k, and the fork / join around work issued on those streams
 cudaStream_t class_stream(dlo_ctx* c, size_t k);
 cudaError_t fork_classes(dlo_ctx* c);
 cudaError_t join_classes(dlo_ctx* c);
-dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out);
+// rec_budget: bytes allowed for the chunk records of all classes (0 = the default)
+dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out, size_t rec_budget = 0);
+// Enqueue the backward of size class k for the rods order[item0 .. item0 + n) on stream st,
+// with that class's R3 / L2 / CS buffers sized for n rods; common holds the outputs and inputs.
+dlo_status enqueue_backward_class(dlo_ctx* c, const BwdPlan& plan, size_t k, cudaStream_t st, int item0, int n,
+                                  float4* R3, float4* L2, float4* CS, int C, const dlo::BwdParams& common);
+// the launch inputs and outputs shared by every kernel of one backward
+dlo::BwdParams backward_common(dlo_ctx* c, int force, const float* dL_dx_T, const float* dL_dv_T,
+                               const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial, float* dL_dx0,
+                               float* dL_dv0, float* dL_dtheta0, float4* gtb0, float4* gd1b0);
+// float4 per rod of size class k with C frames per chunk: chunk records, segment frame-start
+// states, carried cotangents; and the rods the reverse kernel keeps resident on the device
+void backward_rod_f4(dlo_ctx* c, const BwdPlan& plan, size_t k, int C, size_t& r3, size_t& l2, size_t& cs);
+int backward_resident_rods(dlo_ctx* c, size_t k);
+
 
 dlo_status set_err(dlo_ctx* c, dlo_status s, const std::string& msg);
 dlo_status cuda_err(dlo_ctx* c, cudaError_t e, const char* where);

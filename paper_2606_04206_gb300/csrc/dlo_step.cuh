@@ -117,14 +117,15 @@ __device__ __forceinline__ int grp_excl_scan(int v, const Grp<TPR>& g) {
 }
 
 // Optional recording of a substep's intermediates for the adjoint (rec != nullptr): all in
-// global memory, one record per substep of the frame being reversed.
+// global memory, one record per substep of the frames being reversed.
 struct Rec {
-    float4* snap;   // [n_iter][NV]: displacements at the start of each PBD iteration
     float4* v1;     // [NV]: velocity after the force update, before rigid contact
     float4* dfin;   // [NV]: displacement after the PBD iterations, before friction
+    float4* pbd;    // [n_iter][NV]: per edge, the unit direction and target / length of its
+                    // inextensibility or strain-limit projection, (0, 0, 0, 1) where it did nothing
+    float4* csnap;  // [n_iter][NV]: displacements before each self-contact sweep (frames with candidates)
     float4* fr0;    // [pair capacity]: first-iteration projection data of each pair
     float4* fr1;
-    float4* csnap;  // [n_iter][3][NV]: displacements after each colour of each PBD iteration
     int nvmax;
 };
 
@@ -304,9 +305,10 @@ __device__ __forceinline__ void color_range(int ne, bool closed, int color, int&
 
 // One colour of inextensibility / strain-limit projections (App. A.1) on displacements D
 // from start positions X0: C = |x_{j+1} - x_j| - |ebar|, lambda = C / (w_j + w_{j+1}).
+// prec (optional): receives each edge's projection record (see Rec::pbd).
 template <int TPR>
 __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* X0, float4* D, const float4* ET,
-                                                const Grp<TPR>& g, int color, bool closed) {
+                                                const Grp<TPR>& g, int color, bool closed, float4* prec = nullptr) {
     const int ne = R.ne, nv = R.nv;
     int first, last;
     color_range(ne, closed, color, first, last);
@@ -328,9 +330,13 @@ __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* 
             target = ell > hi ? hi : lo;
         }
         float ws = A.w + B.w;
-        if (!active || !(ws > 0.f)) continue;
+        if (!active || !(ws > 0.f)) {
+            if (prec) prec[j] = make_float4(0.f, 0.f, 0.f, 1.f);
+            continue;
+        }
         float lam = (ell - target) / ws;
         V3<float> t = e / ell;
+        if (prec) prec[j] = f4(t, target / ell);
         V3<float> da = (lam * A.w) * t, db = (lam * B.w) * t;
         D[j] = make_float4(A.x + da.x, A.y + da.y, A.z + da.z, A.w);
         D[j1] = make_float4(B.x - db.x, B.y - db.y, B.z - db.z, B.w);
@@ -340,8 +346,8 @@ __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* 
 
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void inext_color(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int color,
-                                            bool closed) {
-    inext_color_arr<TPR>(R, s.X0, s.X, s.ET, g, color, closed);
+                                            bool closed, float4* prec = nullptr) {
+    inext_color_arr<TPR>(R, s.X0, s.X, s.ET, g, color, closed, prec);
 }
 
 template <int NV, bool CONTACT, int TPR>
@@ -552,21 +558,18 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
     const bool lenc = R.flags & (ROD_INEXT | ROD_SLIMIT);
     if (lenc || np > 0) {
         for (int it = 0; it < sc.n_iter; ++it) {
-            if (rec) {
-                for (int i = g.tid; i < nv; i += TPR) rec->snap[(size_t)it * rec->nvmax + i] = s.X[i];
-                g.sync();
-            }
             if (lenc) {
                 const int ncol = (closed && (ne & 1)) ? 3 : 2;
-                for (int k = 0; k < ncol; ++k) {
-                    inext_color<NV, CONTACT, TPR>(R, s, g, k, closed);
-                    if (rec) {
-                        for (int i = g.tid; i < nv; i += TPR) rec->csnap[((size_t)it * 3 + k) * rec->nvmax + i] = s.X[i];
-                        g.sync();
-                    }
-                }
+                for (int k = 0; k < ncol; ++k)
+                    inext_color<NV, CONTACT, TPR>(R, s, g, k, closed, rec ? rec->pbd + (size_t)it * rec->nvmax : nullptr);
             }
-            if (CONTACT && np > 0) contact_sweep<NV, CONTACT, TPR>(R, s, g, np, it == 0);
+            if (CONTACT && np > 0) {
+                // each thread stores its own vertices; the sweep reads s.X and writes only the
+                // accumulators before its own barrier
+                if (rec)
+                    for (int i = g.tid; i < nv; i += TPR) rec->csnap[(size_t)it * rec->nvmax + i] = s.X[i];
+                contact_sweep<NV, CONTACT, TPR>(R, s, g, np, it == 0);
+            }
         }
     }
     // --- velocity from the displacement, friction, new positions

@@ -105,6 +105,8 @@ def load(path: str | None = None):
     lib.dlo_reaction.restype = st
     lib.dlo_query.argtypes = [vp, ip, vp]
     lib.dlo_query.restype = st
+    lib.dlo_measure_fp32_peak.argtypes = [C.c_double, vp, C.POINTER(C.c_double)]
+    lib.dlo_measure_fp32_peak.restype = st
     lib.dlo_status_string.argtypes = [st]
     lib.dlo_status_string.restype = C.c_char_p
     lib.dlo_last_error.argtypes = [vp]
@@ -506,3 +508,14 @@ def rollout(sim, x0, v0, theta0, actions, material=None):
     if material is None:
         material = sim.material_tensor()
     return _rollout_function().apply(sim, x0, v0, theta0, actions, material)
+
+
+def measure_fp32_peak(seconds=1.0):
+    """dlo_measure_fp32_peak on torch's current stream: the device's FP32 TFLOP/s."""
+    import torch
+    lib = load()
+    out = C.c_double()
+    st = lib.dlo_measure_fp32_peak(float(seconds), C.c_void_p(torch.cuda.current_stream().cuda_stream), C.byref(out))
+    if st != 0:
+        raise DloError(st, "dlo_measure_fp32_peak failed")
+    return out.value

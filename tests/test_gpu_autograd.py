@@ -66,7 +66,7 @@ def changed_material(p):
     m[:, 2] *= 0.5
     m[:, 3] = np.where(p.plastic, 0.7 * m[:, 3], m[:, 3])
     m[:, 4] = 2.5
-    m[0, :2] = [1e8, 1e8]
+    m[0, :3] = [1e8, 1e8, 4e7]
     return inputs.f32(m)
 
 

@@ -138,13 +138,20 @@ def test_self_contact_candidates_and_projection_match_oracle():
 
 
 def test_self_contact_candidates_match_brute_force_on_knots():
-    p = inputs.small_case("selfcontact", n_rods=6, n=60, frames=3)
+    """Knotted bands falling onto the box and the ground: once their crossings come within the
+    candidate distance, the device's candidate set of a frame equals the oracle's brute-force
+    set from the same state (P11), rod by rod."""
+    p = inputs.small_case("selfcontact", n_rods=6, n=60, frames=400)
     sim = sim_for(p)
     sim.reset()
     acts = actions_dev(p)
-    sim.step(acts[:2].contiguous(), 2)
+    f = 0
+    while f < 380 and sim.query(6).sum() == 0:       # DLO_Q_PAIRS of the last dlo_step
+        sim.step(acts[f:f + 20].contiguous(), 20)
+        f += 20
+    assert sim.query(6).sum() > 0, "the knots never came into self-contact"
     o = oracle_from_device_state(p, sim)
-    sim.step(acts[2:3].contiguous(), 1)
+    sim.step(acts[f:f + 1].contiguous(), 1)
     got = sim.pair_sets()
     n = 0
     for G, S in zip(o.groups, o.state):
