@@ -50,6 +50,8 @@ FP32_LANES_PER_SM = 128     # for the nominal figure printed beside the measured
 
 
 def metric_for(workload):
+    if workload == "trajopt-opt":
+        return "rod-vertex-steps/s fwd+bwd over Adam iterations of trajectory optimisation, fused vs plain, final losses"
     if workload == "cmaes":
         return "rod-vertex-steps/s of one CMA-ES generation (forward rollouts + device scores)"
     if workload == "trajopt":
@@ -63,12 +65,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="trajopt", choices=["trajopt", "batching", "selfcontact", "diff", "cmaes", "sysid"],
+    ap.add_argument("--workload", default="trajopt",
+                    choices=["trajopt", "batching", "selfcontact", "diff", "cmaes", "sysid", "trajopt-opt"],
                     help="trajopt is the headline line; the others measure the other configurations")
+    ap.add_argument("--iters", type=int, default=50, help="trajopt-opt: Adam iterations")
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--rods", type=int, default=None)
     ap.add_argument("--verts", type=int, default=None)
     ap.add_argument("--no-self-contact", action="store_true")
+    ap.add_argument("--broad-phase", default="all-pairs", choices=["all-pairs", "hash"],
+                    help="self-contact candidates: every edge pair (default) or the per-rod spatial hash")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--plain-frames", type=int, default=20)
@@ -256,8 +262,10 @@ def run_reference(args, rank, ws):
 # --------------------------------------------------------------------------- native arm
 # rods, vertices per rod, frames of each workload (the configurations' own sizes)
 WORKLOADS = {"trajopt": (4096, 128, 2000), "batching": (1024, None, 1000), "selfcontact": (4096, 200, 300),
-             "diff": (256, 64, 500), "cmaes": (400, 128, 2000), "sysid": (256, 64, 500)}
+             "diff": (256, 64, 500), "cmaes": (400, 128, 2000), "sysid": (256, 64, 500),
+             "trajopt-opt": (512, 128, 200)}
 SIL_HW, SIL_TAU = 256, 0.5  # system identification: two 256 x 256 cameras, edge softness in pixels
+ACTION_UNIT = 1e-3         # trajopt-opt: the optimised action corrections are in mm and mrad per frame
 REPULSION_WEIGHT = 1e3     # the Unknotting penalty's weight against the crossing sum
 
 
@@ -268,7 +276,13 @@ def make_workload(args, rank):
     N = args.verts or N0
     F = args.frames or F0
     w = args.workload
-    if w == "trajopt":
+    if w == "trajopt-opt":
+        prob = inputs.trajopt(n_rods=R, frames=F, seed=4000 + rank, n=N, self_contact=not args.no_self_contact)
+        desc = (f"trajopt-opt: {args.iters} Adam iterations (lr 1e-3 cosine to 1e-6) on the gripper actions of "
+                f"{R} rods x {N} vertices per GPU, {F} frames (dt 1e-3 s, 5 substeps), cable/rope/wire thirds, "
+                f"2 grippers, ground, self-contact={'on' if not args.no_self_contact else 'off'}; loss = mean squared "
+                f"distance of the final vertices to seeded target curves")
+    elif w == "trajopt":
         prob = inputs.trajopt(n_rods=R, frames=F, seed=4000 + rank, n=N, self_contact=not args.no_self_contact)
         desc = (f"trajopt: {R} rods x {N} vertices per GPU, {F} frames (dt 1e-3 s, 5 substeps), cable/rope/wire "
                 f"thirds, 2 grippers, ground, self-contact={'on' if not args.no_self_contact else 'off'}")
@@ -302,7 +316,7 @@ def run_native(args, rank, ws):
     build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     prob, desc, R, F = make_workload(args, rank)
-    sim = dlo.DloSim(prob)
+    sim = dlo.DloSim(prob, broad_phase=int(args.broad_phase == "hash"))
     V = sim.V
     N = int(np.max(prob.n_verts))
     units = float(np.sum(prob.n_verts)) * F
@@ -516,6 +530,7 @@ def run_native(args, rank, ws):
                 "config": {"workload": desc,
                            "rods_per_gpu": R, "verts_per_rod": N, "frames": F, "substeps": nsub,
                            "n_iter_pbd": 10, "checkpoint_every": int(sim.query(dlo.Q_CONFIG)[1]),
+                           "broad_phase": args.broad_phase,
                            "l2": "256 MiB buffer written before every timed step"},
                 "fwd_value": fwd_value, "ms_fwd": ms_fwd, ("ms_score" if pop else "ms_bwd"): ms_bwd,
                 "e2e": {"value": units * ws / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -525,11 +540,108 @@ def run_native(args, rank, ws):
         print(json.dumps(line), flush=True)
 
 
+def run_trajopt_opt(args, rank, ws):
+    """Trajectory optimisation (App. B's gradient-descent setting): Adam on the per-frame gripper
+    actions through DloRollout, once with the fused kernels and once with the plain per-phase
+    comparator, from identical inputs.  One step = one iteration (rollout, loss, backward, Adam
+    update).  value = fused fwd+bwd rod-vertex-steps/s over the iterations."""
+    import numpy as np
+    import torch
+    from paper_2606_04206_gb300 import build, dlo
+
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prob, desc, R, F = make_workload(args, rank)
+    units = float(np.sum(prob.n_verts)) * F
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    h_acts = torch.as_tensor(np.ascontiguousarray(prob.actions, np.float32)).pin_memory()
+    h_target = torch.zeros(int(prob.vert_off[-1]), 4)
+    h_target[:, :3] = torch.as_tensor(prob.target, dtype=torch.float32)
+    h_target = h_target.pin_memory()
+    h_loss = torch.empty(1).pin_memory()
+
+    def optimise(plain, iters, clocks=None):
+        sim = dlo.DloSim(prob)
+        stream = torch.cuda.current_stream()
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        acts0 = h_acts.to(dev, non_blocking=True)
+        target = h_target.to(dev, non_blocking=True)
+        x0, v0, th0 = sim.tensors_from_problem()
+        # decision variables: corrections to the per-frame actions in mm and mrad per frame
+        u = torch.zeros_like(acts0, requires_grad=True)
+        opt = torch.optim.Adam([u], lr=1e-3)
+        sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, T_max=max(1, iters - 1), eta_min=1e-6)
+        losses = []
+        n_bad = torch.zeros((), dtype=torch.int64, device=dev)
+        for _ in range(iters):
+            opt.zero_grad(set_to_none=True)
+            x, _, _ = dlo.rollout(sim, x0, v0, th0, acts0 + ACTION_UNIT * u, plain=plain)
+            loss = ((x - target)[:, :3] ** 2).sum(1).mean()
+            loss.backward()
+            # where a rod's sensitivity overflows float32 (self-contact can make it grow without
+            # bound: ~1e48 in FP64 for some rods over 200 frames), those entries are zeroed
+            bad = ~torch.isfinite(u.grad)
+            n_bad += bad.sum()
+            u.grad.masked_fill_(bad, 0.0)
+            opt.step()
+            sched.step()
+            losses.append(loss.detach())
+        x, _, _ = dlo.rollout(sim, x0, v0, th0, (acts0 + ACTION_UNIT * u).detach(), plain=plain)
+        final = ((x - target)[:, :3] ** 2).sum(1).mean()
+        h_loss.copy_(final.reshape(1), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = sim.query(dlo.Q_LAUNCHES)
+        sim.close()
+        return ms, float(h_loss[0]), [float(l) for l in losses], launches, int(n_bad)
+
+    for _ in range(args.warmup):        # warm-up: one short run of each path
+        optimise(False, 1)
+        optimise(True, 1)
+    clocks = Clocks(torch.cuda.current_device())
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ms_f, loss_f, hist_f, launches, bad_f = optimise(False, args.iters)
+    clk = clocks.stop()
+    ms_p, loss_p, hist_p, _, bad_p = optimise(True, args.iters)
+    ms_f = max_over_ranks(ms_f, ws)
+    ms_p = max_over_ranks(ms_p, ws)
+    total_units = units * (args.iters + 1)   # iterations plus the final evaluation rollout
+    value = total_units * ws / (ms_f / 1e3)
+    plain_value = total_units * ws / (ms_p / 1e3)
+    if rank == 0:
+        line = {"metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.iters, "warmup": args.warmup, "ms_per_step": ms_f / args.iters,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": desc, "rods_per_gpu": R, "verts_per_rod": int(np.max(prob.n_verts)),
+                           "frames": F, "iterations": args.iters,
+                           "optimizer": "Adam, lr 1e-3 cosine to 1e-6, on action corrections in mm / mrad per frame",
+                           "l2": "256 MiB buffer written before each timed optimisation"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h_acts.numel() * 4 + h_target.numel() * 4),
+                        "d2h_bytes_per_step": 4},
+                "gpu_launches": int(launches),
+                "loss": {"initial": hist_f[0], "final_fused": loss_f, "final_plain": loss_p,
+                         "rel_diff": abs(loss_f - loss_p) / max(abs(loss_p), 1e-30),
+                         "history_fused": hist_f[:: max(1, args.iters // 10)],
+                         "history_plain": hist_p[:: max(1, args.iters // 10)],
+                         "nonfinite_gradient_entries_zeroed": {"fused": bad_f, "plain": bad_p}},
+                "plain": {"value": plain_value, "unit": UNIT, "ms_total": ms_p, "speedup": value / plain_value},
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, ws = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, ws)
+    elif args.workload == "trajopt-opt":
+        run_trajopt_opt(args, rank, ws)
     else:
         run_native(args, rank, ws)
 

@@ -102,6 +102,10 @@ typedef struct {
     int    warps_per_cta;   /* rods per CTA of the persistent kernels; 0 = autotune */
     int    reaction;        /* 1: dlo_step accumulates the impulse every rigid contact gives each
                                vertex (read with dlo_reaction); 0: off, no cost */
+    int    broad_phase;     /* self-contact candidates, once per frame: 0 every edge pair of the rod
+                               behind a bounding-sphere filter; 1 a per-rod spatial hash of the
+                               edge midpoints (cells of the candidate distance plus the frame's
+                               longest edge).  Both give the same candidate set */
 } dlo_options;
 
 typedef struct {
@@ -182,9 +186,20 @@ dlo_status dlo_step(dlo_ctx* ctx, const float* actions, int frames, int substeps
 
 /* The same rollout computed by the plain per-phase kernels (one launch per phase per
  * substep, state in HBM, one thread per element): the speed comparator.  Same arguments and
- * errors as dlo_step (without x_frames); it does not record, and it ends any armed
- * recording.  Defined by: the same passages as dlo_step. */
+ * errors as dlo_step (without x_frames).  Armed by dlo_begin_rollout it records checkpoints
+ * and actions as dlo_step does (the rollout can then be differentiated by dlo_backward or
+ * dlo_backward_plain).  Defined by: the same passages as dlo_step. */
 dlo_status dlo_step_plain(dlo_ctx* ctx, const float* actions, int frames, int substeps);
+
+/* The adjoint of dlo_backward computed the plain way, the comparator of the fused adjoint:
+ * per frame, last first, the frame's start state is restored from its checkpoint (and the
+ * frames before it in its segment re-run), the frame is re-run by the plain per-phase
+ * kernels storing every substep's intermediates in HBM, and each substep is reversed by one
+ * kernel launch per phase, one thread per element, every cotangent in HBM.  Same arguments,
+ * outputs and errors as dlo_backward.  Defined by: the gradient through time of Sec. 3.3. */
+dlo_status dlo_backward_plain(dlo_ctx* ctx, const float* dL_dx_T, const float* dL_dv_T,
+                              const float* dL_dtheta_T, float* dL_dactions, float* dL_dmaterial,
+                              float* dL_dx0, float* dL_dv0, float* dL_dtheta0);
 
 /* Differentiate the recorded rollout (the gradient through time of Sec. 3.3, computed by a
  * hand-written adjoint that replays each frame from its checkpoint).  Inputs (device, may be

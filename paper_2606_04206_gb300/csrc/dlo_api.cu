@@ -103,7 +103,8 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
     if (batch <= 0 || batch > (1 << 24) || !n_verts || !mat || !x_rest || !opt) return DLO_ERR_INVALID_ARG;
     if (!(opt->dt > 0.f) || opt->n_iter_pbd < 0 || opt->n_iter_pbd > 1000 || opt->substeps_min < 1 ||
         opt->checkpoint_every < 0 || opt->warps_per_cta < 0 || opt->warps_per_cta > 8 || !(opt->eps_soft > 0.f) ||
-        opt->contact_margin < 0.f || opt->mu_self < 0.f || opt->mu_rigid < 0.f || opt->restitution < 0.f)
+        opt->contact_margin < 0.f || opt->mu_self < 0.f || opt->mu_rigid < 0.f || opt->restitution < 0.f ||
+        opt->broad_phase < 0 || opt->broad_phase > 1)
         return DLO_ERR_INVALID_ARG;
     // self-contact friction acts on the contact set of the first projection iteration
     if (opt->self_contact && opt->n_iter_pbd < 1) return DLO_ERR_INVALID_ARG;
@@ -252,7 +253,7 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         R.nsub = ns;
         R.flags = (inext ? ROD_INEXT : 0) | (m.plastic ? ROD_PLASTIC : 0) |
                   (!inext && m.strain_limit > 0.f ? ROD_SLIMIT : 0) | (opt->self_contact ? ROD_SELF : 0) |
-                  (closed ? ROD_CLOSED : 0);
+                  (closed ? ROD_CLOSED : 0) | (opt->broad_phase == 1 ? ROD_HASH : 0);
         R.ngrip = ng;
         R.excl = std::max(1, (int)std::ceil(2.0 * r / lmin));
         set_moduli(R, m, ns, opt->dt);

@@ -10,7 +10,8 @@ enum RodFlags : int {
     ROD_PLASTIC = 2,     // bending plasticity
     ROD_SLIMIT = 4,      // elastic stretching plus strain-limit projection
     ROD_SELF = 8,        // self-contact on
-    ROD_CLOSED = 16
+    ROD_CLOSED = 16,
+    ROD_HASH = 32        // self-contact candidates through the per-rod spatial hash
 };
 
 // One rod: offsets into the packed arrays and its per-rod constants (64 bytes).

@@ -84,6 +84,21 @@ __device__ __forceinline__ unsigned grp_or(unsigned v, const Grp<TPR>& g) {
     return s;
 }
 
+// Largest value over the group (non-negative floats: their bit patterns order like the values).
+template <int TPR>
+__device__ __forceinline__ float grp_max_nonneg(float v, const Grp<TPR>& g) {
+    const unsigned w = __reduce_max_sync(0xffffffffu, __float_as_uint(v));
+    if (TPR == 32) return __uint_as_float(w);
+    unsigned* r = reinterpret_cast<unsigned*>(g.red) + 60;
+    if ((g.tid & 31) == 0) r[g.tid >> 5] = w;
+    g.sync();
+    unsigned m = 0u;
+#pragma unroll
+    for (int k = 0; k < TPR / 32; ++k) m = max(m, r[k]);
+    g.sync();
+    return __uint_as_float(m);
+}
+
 // Value held by thread 0 of the group.
 template <int TPR>
 __device__ __forceinline__ int grp_bcast0(int v, const Grp<TPR>& g) {
@@ -286,6 +301,111 @@ __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR
     g.sync();
     overflow = grp_any<TPR>(ovf, g);
     const int np = *cnt;
+    g.sync();
+    return min(np, cap);
+}
+
+__device__ __forceinline__ unsigned cell_hash(int ix, int iy, int iz, int mask) {
+    return ((unsigned)ix * 73856093u ^ (unsigned)iy * 19349663u ^ (unsigned)iz * 83492791u) & (unsigned)mask;
+}
+
+// The same candidates found through a per-rod spatial hash of the edge midpoints (the option
+// ROD_HASH).  Cells are the candidate distance plus the frame's longest edge, so that the 27
+// cells around an edge's cell hold every edge whose segment can come within the candidate
+// distance of it (two midpoints are at most that far apart then).  Midpoints are counting-
+// sorted into a table of buckets in shared memory (HB0 and HB1, free at this point); each
+// edge then tests the edges of its 27 neighbouring cells.
+template <int NV, bool CONTACT, int TPR>
+__device__ int broad_phase_hash(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, bool closed,
+                                bool& overflow) {
+    constexpr int TBL = NV <= 32 ? 64 : (NV <= 64 ? 128 : (NV <= 128 ? 256 : 512));
+    static_assert(2 * NV + TBL + 1 <= 8 * NV, "the hash table fits in HB0 and HB1");
+    int* keys = reinterpret_cast<int*>(s.HB0);
+    int* cnt = keys + NV;            // TBL bucket counters, then the pair counter
+    int* sorted = cnt + TBL + 1;
+    const int ne = R.ne, nv = R.nv;
+    float lmax = 0.f;
+    for (int j = g.tid; j < ne; j += TPR) {
+        const int j1 = (j + 1 == nv) ? 0 : j + 1;
+        const V3<float> e = f3(s.X[j1]) - f3(s.X[j]);
+        lmax = fmaxf(lmax, sqrtf(dot(e, e)));
+    }
+    for (int k = g.tid; k <= TBL; k += TPR) cnt[k] = 0;
+    lmax = grp_max_nonneg<TPR>(lmax, g);
+    const float inv_cell = 1.f / (R.contact_d + lmax);
+    const V3<float> org = f3(s.X[0]);
+    for (int j = g.tid; j < ne; j += TPR) {
+        const int j1 = (j + 1 == nv) ? 0 : j + 1;
+        const V3<float> m = 0.5f * (f3(s.X[j]) + f3(s.X[j1])) - org;
+        const int ix = min(max(__float2int_rd(m.x * inv_cell), -510), 510) + 512;
+        const int iy = min(max(__float2int_rd(m.y * inv_cell), -510), 510) + 512;
+        const int iz = min(max(__float2int_rd(m.z * inv_cell), -510), 510) + 512;
+        keys[j] = (ix << 20) | (iy << 10) | iz;
+        atomicAdd(&cnt[cell_hash(ix, iy, iz, TBL - 1)], 1);
+    }
+    g.sync();
+    {   // exclusive scan of the bucket counts, TBL / TPR consecutive buckets per thread
+        constexpr int PER = TBL / TPR;
+        int loc[PER];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            loc[k] = cnt[g.tid * PER + k];
+            sum += loc[k];
+        }
+        int run = grp_excl_scan<TPR>(sum, g);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            cnt[g.tid * PER + k] = run;
+            run += loc[k];
+        }
+    }
+    g.sync();
+    for (int j = g.tid; j < ne; j += TPR) {
+        const int key = keys[j];
+        const int pos = atomicAdd(&cnt[cell_hash(key >> 20, (key >> 10) & 1023, key & 1023, TBL - 1)], 1);
+        sorted[pos] = j;
+    }
+    g.sync();
+    // after the scatter cnt[h] is the end of bucket h (and the start of bucket h + 1)
+    const int cap = R.pair_cap;
+    const float cd = R.contact_d;
+    bool ovf = false;
+    for (int a = g.tid; a < ne; a += TPR) {
+        const int key = keys[a];
+        const int ix = key >> 20, iy = (key >> 10) & 1023, iz = key & 1023;
+        const int a1 = (a + 1 == nv) ? 0 : a + 1;
+        const V3<float> pa0 = f3(s.X[a]), pa1 = f3(s.X[a1]);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int cx = ix + dx, cy = iy + dy, cz = iz + dz;
+                    const int nk = (cx << 20) | (cy << 10) | cz;
+                    const unsigned hh = cell_hash(cx, cy, cz, TBL - 1);
+                    const int beg = hh ? cnt[hh - 1] : 0, end = cnt[hh];
+                    for (int q = beg; q < end; ++q) {
+                        const int b = sorted[q];
+                        if (b <= a || keys[b] != nk) continue;
+                        int sep = b - a;
+                        if (closed) sep = min(sep, ne - sep);
+                        if (sep <= R.excl) continue;
+                        const int b1 = (b + 1 == nv) ? 0 : b + 1;
+                        const V3<float> pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
+                        float su, uu;
+                        closest_params(pa0, pa1, pb0, pb1, su, uu);
+                        const V3<float> dd = (pa0 + su * (pa1 - pa0)) - (pb0 + uu * (pb1 - pb0));
+                        if (!(sqrtf(dot(dd, dd)) < cd)) continue;
+                        const int idx = atomicAdd(&cnt[TBL], 1);
+                        if (idx < cap)
+                            s.pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
+                        else
+                            ovf = true;
+                    }
+                }
+    }
+    g.sync();
+    overflow = grp_any<TPR>(ovf, g);
+    const int np = cnt[TBL];
     g.sync();
     return min(np, cap);
 }
@@ -668,7 +788,9 @@ __device__ __forceinline__ int run_frame(const SceneDev& sc, const float4* __res
                          const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, int nsub, float h, bool& ovf,
                          PreSub pre, float4* imp = nullptr, float* mv = nullptr) {
     int np = 0;
-    if (CONTACT && (R.flags & ROD_SELF)) np = broad_phase<NV, CONTACT, TPR>(R, s, g, (R.flags & ROD_CLOSED) != 0, ovf);
+    if (CONTACT && (R.flags & ROD_SELF))
+        np = (R.flags & ROD_HASH) ? broad_phase_hash<NV, CONTACT, TPR>(R, s, g, (R.flags & ROD_CLOSED) != 0, ovf)
+                                  : broad_phase<NV, CONTACT, TPR>(R, s, g, (R.flags & ROD_CLOSED) != 0, ovf);
     const float inv_dt = 1.f / sc.dt;
     for (int sb = 0; sb < nsub; ++sb) {
         const Rec* rec = pre(sb);

@@ -52,7 +52,7 @@ class Options(C.Structure):
                 ("mu_self", C.c_float), ("mu_rigid", C.c_float), ("restitution", C.c_float),
                 ("eps_soft", C.c_float), ("contact_margin", C.c_float), ("self_contact", C.c_int),
                 ("checkpoint_every", C.c_int), ("hbm_budget", C.c_size_t), ("warps_per_cta", C.c_int),
-                ("reaction", C.c_int)]
+                ("reaction", C.c_int), ("broad_phase", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -95,6 +95,8 @@ def load(path: str | None = None):
     lib.dlo_step_plain.restype = st
     lib.dlo_backward.argtypes = [vp] * 9
     lib.dlo_backward.restype = st
+    lib.dlo_backward_plain.argtypes = [vp] * 9
+    lib.dlo_backward_plain.restype = st
     lib.dlo_backward_noalloc.argtypes = [vp] * 9
     lib.dlo_backward_noalloc.restype = st
     lib.dlo_loss.argtypes = [vp, ip, vp, vp, ip, vp, vp, vp]
@@ -136,7 +138,7 @@ def options_from(prob, **over) -> Options:
     o = Options(dt=prob.dt, n_iter_pbd=prob.n_iter, substeps_min=prob.substeps_min, gravity=prob.gravity,
                 mu_self=prob.mu_self, mu_rigid=prob.mu_rigid, restitution=prob.restitution,
                 eps_soft=prob.eps_soft, contact_margin=prob.contact_margin, self_contact=int(prob.self_contact),
-                checkpoint_every=0, hbm_budget=0, warps_per_cta=0, reaction=0)
+                checkpoint_every=0, hbm_budget=0, warps_per_cta=0, reaction=0, broad_phase=0)
     for k, v in over.items():
         setattr(o, k, v)
     return o
@@ -335,12 +337,19 @@ class DloSim:
                 self._rec_left = 0
 
     def step_plain(self, actions=None, frames=None, substeps=0):
-        self.rollout_id += 1
         if frames is None:
             frames = actions.shape[0]
         self._check(self.lib.dlo_step_plain(self.ctx, _ptr(actions), int(frames), int(substeps)), "dlo_step_plain")
+        if frames > 0:   # recorded like dlo_step when a rollout is armed
+            if getattr(self, "_rec_left", 0) >= frames:
+                self._rec_left -= frames
+            else:
+                self.rollout_id += 1
+                self._rec_left = 0
 
-    def backward(self, dL_dx=None, dL_dv=None, dL_dtheta=None, want=("actions", "material", "x0", "v0", "theta0")):
+    def backward(self, dL_dx=None, dL_dv=None, dL_dtheta=None, want=("actions", "material", "x0", "v0", "theta0"),
+                 plain=False):
+        """dlo_backward (plain=True: dlo_backward_plain, the per-phase comparator)."""
         torch = self.torch
         n = getattr(self, "_rollout_frames", 0)
         out = {}
@@ -354,10 +363,10 @@ class DloSim:
             out["v0"] = torch.zeros(self.V, 4, device=self.device)
         if "theta0" in want:
             out["theta0"] = torch.zeros(self.E, device=self.device)
-        st = self.lib.dlo_backward(self.ctx, _ptr(dL_dx), _ptr(dL_dv), _ptr(dL_dtheta), _ptr(out.get("actions")),
-                                   _ptr(out.get("material")), _ptr(out.get("x0")), _ptr(out.get("v0")),
-                                   _ptr(out.get("theta0")))
-        self._check(st, "dlo_backward")
+        fn = self.lib.dlo_backward_plain if plain else self.lib.dlo_backward
+        st = fn(self.ctx, _ptr(dL_dx), _ptr(dL_dv), _ptr(dL_dtheta), _ptr(out.get("actions")),
+                _ptr(out.get("material")), _ptr(out.get("x0")), _ptr(out.get("v0")), _ptr(out.get("theta0")))
+        self._check(st, "dlo_backward_plain" if plain else "dlo_backward")
         return out
 
     def backward_noalloc(self, dL_dx=None, dL_dv=None, dL_dtheta=None,
@@ -473,7 +482,7 @@ def _rollout_function():
         rollout)."""
 
         @staticmethod
-        def forward(ctx, sim, x0, v0, theta0, actions, material):
+        def forward(ctx, sim, x0, v0, theta0, actions, material, plain=False):
             frames = actions.shape[0]
             mat = material.detach().float().cpu().numpy()
             if mat.shape != sim._mat.shape:
@@ -482,9 +491,13 @@ def _rollout_function():
                 sim.set_material(mat)
             sim.set_state(x0.contiguous(), v0.contiguous(), theta0.contiguous())
             sim.begin_rollout(frames)
-            sim.step(actions.contiguous(), frames)
+            if plain:
+                sim.step_plain(actions.contiguous(), frames)
+            else:
+                sim.step(actions.contiguous(), frames)
             x, v, th = sim.get_state()
             ctx.sim = sim
+            ctx.plain = plain
             ctx.rollout_id = sim.rollout_id
             return x, v, th
 
@@ -496,18 +509,19 @@ def _rollout_function():
             need = ctx.needs_input_grad
             want = [k for k, n in zip(("x0", "v0", "theta0", "actions", "material"), need[1:]) if n]
             g = ctx.sim.backward(None if gx is None else gx.contiguous(), None if gv is None else gv.contiguous(),
-                                 None if gth is None else gth.contiguous(), want=tuple(want))
-            return (None, g.get("x0"), g.get("v0"), g.get("theta0"), g.get("actions"), g.get("material"))
+                                 None if gth is None else gth.contiguous(), want=tuple(want), plain=ctx.plain)
+            return (None, g.get("x0"), g.get("v0"), g.get("theta0"), g.get("actions"), g.get("material"), None)
 
     return DloRollout
 
 
-def rollout(sim, x0, v0, theta0, actions, material=None):
+def rollout(sim, x0, v0, theta0, actions, material=None, plain=False):
     """Differentiable rollout through the library: final (x, v, theta) after actions.shape[0]
-    frames, with gradients with respect to every tensor input (DloRollout)."""
+    frames, with gradients with respect to every tensor input (DloRollout).  plain=True runs
+    the plain per-phase comparator (dlo_step_plain, dlo_backward_plain) instead."""
     if material is None:
         material = sim.material_tensor()
-    return _rollout_function().apply(sim, x0, v0, theta0, actions, material)
+    return _rollout_function().apply(sim, x0, v0, theta0, actions, material, plain)
 
 
 def measure_fp32_peak(seconds=1.0):

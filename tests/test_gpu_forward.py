@@ -117,9 +117,10 @@ def pair_set(cand):
     return {(int(a), int(b)) for a, b in cand.tolist()}
 
 
-def test_self_contact_candidates_and_projection_match_oracle():
+@pytest.mark.parametrize("broad_phase", [0, 1], ids=["all-pairs", "spatial-hash"])
+def test_self_contact_candidates_and_projection_match_oracle(broad_phase):
     p = coils()
-    sim = sim_for(p)
+    sim = sim_for(p, broad_phase=broad_phase)
     sim.reset()
     acts = actions_dev(p)
     o = oracle_from_device_state(p, sim)
@@ -137,12 +138,13 @@ def test_self_contact_candidates_and_projection_match_oracle():
     assert rel_inf(fg["v"], fo["v"]) <= 2e-3
 
 
-def test_self_contact_candidates_match_brute_force_on_knots():
+@pytest.mark.parametrize("broad_phase", [0, 1], ids=["all-pairs", "spatial-hash"])
+def test_self_contact_candidates_match_brute_force_on_knots(broad_phase):
     """Knotted bands falling onto the box and the ground: once their crossings come within the
     candidate distance, the device's candidate set of a frame equals the oracle's brute-force
-    set from the same state (P11), rod by rod."""
+    set from the same state (P11), rod by rod, with either broad phase."""
     p = inputs.small_case("selfcontact", n_rods=6, n=60, frames=400)
-    sim = sim_for(p)
+    sim = sim_for(p, broad_phase=broad_phase)
     sim.reset()
     acts = actions_dev(p)
     f = 0
