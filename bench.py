@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--plain-frames", type=int, default=20)
+    ap.add_argument("--no-side", action="store_true",
+                    help="trajopt: skip the one-shot measurements of the self-contact and batching workloads")
     return ap.parse_args()
 
 
@@ -308,6 +310,72 @@ def make_workload(args, rank):
     return prob, desc, R, F
 
 
+def side_workloads(args, rank):
+    """One timed forward + backward of the self-contact configuration (4096 knotted bands x 200
+    vertices, 300 frames, with each broad phase) and of the batching configuration (1024 rods of
+    16..256 vertices, per-rod substeps; 100 of its 1000 frames), after one warm-up each, with
+    the plain per-phase forward on the same rods.  Reported beside the headline, not in it."""
+    import copy
+    import numpy as np
+    import torch
+    from paper_2606_04206_gb300 import dlo
+    out = {}
+    for kind, frames in (("selfcontact", 300), ("batching", 100)):
+        a2 = copy.copy(args)
+        a2.workload, a2.frames, a2.rods, a2.verts = kind, frames, None, None
+        prob, desc, R, F = make_workload(a2, rank)
+        units = float(np.sum(prob.n_verts)) * F
+        res = {"workload": desc, "frames": F}
+        for bp in ((0, 1) if kind == "selfcontact" else (0,)):
+            sim = dlo.DloSim(prob, broad_phase=bp)
+            dev = sim.device
+            stream = torch.cuda.current_stream()
+            acts = torch.as_tensor(np.ascontiguousarray(prob.actions, np.float32), device=dev)
+            x0, v0, th0 = sim.tensors_from_problem()
+            gz = torch.zeros(sim.V, 4, device=dev)
+            gz[:, 2] = 1.0 / sim.V          # L = mean height of the vertices
+
+            def fb():
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                sim.set_state(x0, v0, th0)
+                ev[0].record(stream)
+                sim.begin_rollout(F)
+                sim.step(acts, F)
+                ev[1].record(stream)
+                sim.backward(dL_dx=gz, want=("actions", "material", "x0"))
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+
+            fb()
+            ms_f, ms_b = fb()
+            key = "hash" if bp else "all_pairs"
+            if bp:
+                res["fwd_value_spatial_hash"] = units / (ms_f / 1e3)
+                res["ms_fwd_spatial_hash"] = ms_f
+            else:
+                res.update({"value": units / ((ms_f + ms_b) / 1e3), "fwd_value": units / (ms_f / 1e3),
+                            "ms_fwd": ms_f, "ms_bwd": ms_b, "substeps_max": int(np.max(sim.query(dlo.Q_SUBSTEPS))),
+                            "pairs_max_per_rod": int(np.max(sim.query(dlo.Q_PAIRS)))})
+                pf = 5
+                sim.set_state(x0, v0, th0)
+                sim.step_plain(acts[:2].contiguous(), 2)
+                sim.set_state(x0, v0, th0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step_plain(acts[:pf].contiguous(), pf)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                pv = float(np.sum(prob.n_verts)) * pf / (e0.elapsed_time(e1) / 1e3)
+                res["plain_fwd_value"] = pv
+                res["speedup_fwd_vs_plain"] = res["fwd_value"] / pv
+            sim.close()
+            del sim
+            torch.cuda.empty_cache()
+        out[kind] = res
+    return out
+
+
 def run_native(args, rank, ws):
     import numpy as np
     import torch
@@ -523,13 +591,24 @@ def run_native(args, rank, ws):
                "sample": f"2 rods x {N} vertices x {frames} frames of the same workload, FP64 forward + "
                          f"{what}, {dt:.1f} s"}
 
+    ck_used = int(sim.query(dlo.Q_CONFIG)[1])
+    side = None
+    if args.workload == "trajopt" and not args.no_side and rank == 0:
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        try:
+            side = side_workloads(args, rank)
+        except Exception as exc:   # supplementary: say why it is missing rather than lose the line
+            side = {"unavailable": str(exc)[:200]}
+
     if rank == 0:
         line = {"metric": metric_for(args.workload), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": desc,
                            "rods_per_gpu": R, "verts_per_rod": N, "frames": F, "substeps": nsub,
-                           "n_iter_pbd": 10, "checkpoint_every": int(sim.query(dlo.Q_CONFIG)[1]),
+                           "n_iter_pbd": 10, "checkpoint_every": ck_used,
                            "broad_phase": args.broad_phase,
                            "l2": "256 MiB buffer written before every timed step"},
                 "fwd_value": fwd_value, "ms_fwd": ms_fwd, ("ms_score" if pop else "ms_bwd"): ms_bwd,
@@ -537,6 +616,8 @@ def run_native(args, rank, ws):
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(max(launches)), "roofline": roofline, "cpu_baseline": cpu, "plain": plain,
                 "clocks": clk}
+        if side is not None:
+            line["workloads"] = side
         print(json.dumps(line), flush=True)
 
 
