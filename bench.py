@@ -42,10 +42,11 @@ UNIT = "rod-vertex-steps/s"
 # kernels' own element templates; tests/test_flop_count.py keeps these in step)
 FLOPS_FWD_PER_VS = 912.3
 FLOPS_BWD_PER_VS = 3650.0
-# DRAM bytes (read + write) of bwd_kernel per rod-frame of the 128-vertex self-contact
-# workload, from one ncu capture of a 304-rod x 50-frame case of it (its recompute scratch
-# grows with rod-frames; profiles/fwd_bwd_kernels_trajopt_304x128x50.md)
-BWD_DRAM_BYTES_PER_ROD_FRAME = (209.585664e6 + 861.888e6) / (304 * 50)
+# DRAM bytes (read + write) of the backward per rod-frame of the 128-vertex self-contact
+# workload, from ncu captures (cold cache) of a 304-rod x 50-frame case of it: rev_kernel
+# 66.78 + 7.39 MB over a 2-frame chunk, rec_kernel 10.50 + 457.05 MB over a 16-frame chunk
+# (profiles/rec_rev_kernels_trajopt_304x128x50.md)
+BWD_DRAM_BYTES_PER_ROD_FRAME = (66.775808e6 + 7.391232e6) / (304 * 2) + (10.496256e6 + 457.048576e6) / (304 * 16)
 FP32_LANES_PER_SM = 128     # for the nominal figure printed beside the measured peak
 
 
@@ -554,7 +555,7 @@ def run_native(args, rank, ws):
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": fwd_tflops / peak_tflops, "traffic": None,
                     "peak_basis": basis}
     else:
-        roofline = {"bound": "alu", "kernel": "bwd_kernel (dlo_backward)", "achieved": bwd_tflops,
+        roofline = {"bound": "alu", "kernel": "backward: rec_kernel + rev_kernel (dlo_backward)", "achieved": bwd_tflops,
                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": bwd_tflops / peak_tflops, "traffic": traffic,
                     "peak_basis": basis, "forward": {"achieved": fwd_tflops, "frac": fwd_tflops / peak_tflops}}
 

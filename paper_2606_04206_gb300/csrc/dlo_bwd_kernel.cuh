@@ -495,7 +495,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float wi = x4.w;
             lvn = f4((1.f - h * R.cd) * lam, 0.f);
             lg = f4((-h * wi) * lam, 0.f);
-            gm[4] += -(double)h * (double)dot(f3(vn), lam);
+            gm[4] += (double)(-h * dot(f3(vn), lam));
             a.LX[i] = f4(f3(a.LX[i]) + lx_acc, 0.f);
         } else if (kind >= 2) {
             // d = target(pose at the substep end) - x0
@@ -510,7 +510,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float invI = P.ES[e0 + i].y;
             lvn.w = (1.f - h * R.cd) * lw1;
             lg.w = -h * invI * lw1;
-            gm[4] += -(double)h * (double)vn.w * (double)lw1;
+            gm[4] += (double)(-h * vn.w * lw1);
         }
         a.LV[i] = lvn;
         a.LG[i] = lg;
@@ -559,7 +559,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float eb = P.ES[e0 + j].x;
             const float tl = dot(E.t, les);
             le += R.kA * ((tl / eb) * E.t + (E.ell / eb - 1.f) / E.ell * (les - tl * E.t));
-            gm[0] += (double)(E.ell / eb - 1.f) * (double)tl;
+            gm[0] += (double)((E.ell / eb - 1.f) * tl);
         }
         s.HB1[j] = f4(le, 0.f);
         a.LT[j] = f4(gtb, 0.f);
@@ -592,8 +592,9 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         const bool yielded = plastic && plastic_update(hk0, hk1, kb0, kb1, R.sy * lbar, R.rc);
         dualf e0d = Hd.k0 - kb0, e1d = Hd.k1 - kb1, emd = Hd.m - hg.z;
         dualf gk0 = (R.Bm * il) * e0d, gk1 = (R.Bm * il) * e1d, gmt = (R.beta * il) * emd;
-        gm[1] += (double)il * ((double)e0d.v * e0d.d + (double)e1d.v * e1d.d);
-        gm[2] += (double)il * (double)emd.v * (double)emd.d;
+        // each term in float, added to the FP64 sums (the cancellation is across terms)
+        gm[1] += (double)(il * (e0d.v * e0d.d + e1d.v * e1d.d));
+        gm[2] += (double)(il * emd.v * emd.d);
         // rest curvature: cotangent of the one used (-d gk / d .) plus the carried one
         float lk0 = a.LK[i].x - gk0.d, lk1 = a.LK[i].y - gk1.d;
         if (yielded) {
@@ -602,7 +603,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float g = R.rc * (n - thr) / n;
             const float kk = R.rc * thr / (n * n * n) * (el0 * lk0 + el1 * lk1);
             const float le0 = g * lk0 + kk * el0, le1 = g * lk1 + kk * el1;     // cotangent of kappa_el
-            gm[3] += -(double)R.rc * lbar * ((double)el0 * lk0 + (double)el1 * lk1) / n;
+            gm[3] += (double)(-R.rc * lbar * (el0 * lk0 + el1 * lk1) / n);
             // The first-order reverse of kappa from seeds (le0, le1) is needed too.  The hinge
             // reverse is linear in its seeds, so adding them to the derivative part of the
             // dual seeds makes the reverse below return J^T le on top of the Hessian term.
