@@ -183,19 +183,114 @@ def hinge_strains(t, d1r, d1, d2, theta, mprev, closed: bool):
     return kappa, mref, m
 
 
-def elastic_energy(x, theta, tb, d1b, mprev, kbar, R, closed: bool):
+def elastic_energy(x, theta, tb, d1b, mprev, kbar, R, closed: bool, strands=None):
     """Total elastic energy per rod, U = U_s + U_b + U_t (App. A.1).
 
     U_s = 1/2 sum_j K A (|e^j|/|ebar^j| - 1)^2 |ebar^j|        (off for inextensible rods)
     U_b = 1/2 sum_i (1/lbar_i) (kappa_i - kbar_i)^T B_i (kappa_i - kbar_i), B_i = E A r^2/4 I
     U_t = 1/2 sum_i beta_i (m_i - mbar_i)^2 / lbar_i,           beta_i = G A r^2 / 2
-    ``R`` holds the per-rod constants (see OracleSim._group)."""
+    ``R`` holds the per-rod constants (see OracleSim._group).  ``strands``: the vertex ranges
+    of an environment's DLOs (see ``strand_parts``); its energy is the sum of theirs."""
+    if strands is not None:
+        return sum(elastic_energy(x[:, vs], theta[:, es], tb[:, es], d1b[:, es], mprev[:, hs], kbar[:, hs],
+                                  strand_constants(R, es, hs), False)
+                   for vs, es, hs in strand_parts(strands))
     t, ell, d1r, d1, d2 = edge_frames(x, theta, tb, d1b, closed)
     kappa, mref, m = hinge_strains(t, d1r, d1, d2, theta, mprev, closed)
     Us = 0.5 * R["kA"][:, None] * (ell / R["ebar"] - 1.0) ** 2 * R["ebar"]
     Ub = 0.5 * R["Bm"][:, None] / R["lbar"] * ((kappa - kbar) ** 2).sum(-1)
     Ut = 0.5 * R["beta"][:, None] * (m - R["mbar"]) ** 2 / R["lbar"]
     return Us.sum(1) + Ub.sum(1) + Ut.sum(1)
+
+
+# --------------------------------------------------------------------------- environments of several DLOs
+#
+# Several DLOs of one environment (two ropes in Separation, the ropes of Letter Art; Sec. 4)
+# are stored as one record whose vertices are the DLOs' vertices back to back ("strands").
+# reading: the DLOs interact only through the self-collision projection and friction of
+# App. A.1, applied between segments of different strands exactly as between segments of
+# one; every other term (stretching, bending, twisting, plasticity, the length projection)
+# belongs to one strand.  With strands (v0, v1), edge j joins vertices j and j + 1 and hinge
+# index h sits at vertex h + 1, as for a single open rod; the edge v1 - 1 between two
+# strands ("break") and the hinges at its two ends are not part of the model.  A break edge
+# keeps the frame it was given (tangent z, d1 = x) and its twist angle only decays under
+# damping.
+
+def strand_parts(strands):
+    """(vertex slice, edge slice, hinge slice) of every strand of an open record."""
+    return [(slice(v0, v1), slice(v0, v1 - 1), slice(v0, v1 - 2)) for v0, v1 in strands]
+
+
+def strand_constants(R, es, hs):
+    """The constants of ``elastic_energy`` restricted to one strand's edges and hinges."""
+    return dict(kA=R["kA"], Bm=R["Bm"], beta=R["beta"], ebar=R["ebar"][:, es], lbar=R["lbar"][:, hs],
+                mbar=R["mbar"][:, hs])
+
+
+def _fill(default, parts):
+    """``default`` (dim 1) with the slices of ``parts`` [(slice, values)] replaced."""
+    out, pos = [], 0
+    for sl, val in parts:
+        if sl.start > pos:
+            out.append(default[:, pos:sl.start])
+        out.append(val)
+        pos = sl.stop
+    if pos < default.shape[1]:
+        out.append(default[:, pos:])
+    return torch.cat(out, 1)
+
+
+def frames_of(x, theta, tb, d1b, closed: bool, strands=None):
+    """``edge_frames`` of a record; a break edge keeps its stored frame (length 0)."""
+    if strands is None:
+        return edge_frames(x, theta, tb, d1b, closed)
+    parts = [(es, edge_frames(x[:, vs], theta[:, es], tb[:, es], d1b[:, es], False))
+             for vs, es, hs in strand_parts(strands)]
+    dflt = (tb, torch.zeros_like(theta), d1b, d1b, cross(tb, d1b))
+    return tuple(_fill(dflt[k], [(es, f[k]) for es, f in parts]) for k in range(5))
+
+
+def strains_of(t, d1r, d1, d2, theta, mprev, closed: bool, strands=None):
+    """``hinge_strains`` of a record; hinges at the ends of a break edge have no strain and
+    keep their reference twist."""
+    if strands is None:
+        return hinge_strains(t, d1r, d1, d2, theta, mprev, closed)
+    parts = [(hs, hinge_strains(t[:, es], d1r[:, es], d1[:, es], d2[:, es], theta[:, es], mprev[:, hs], False))
+             for vs, es, hs in strand_parts(strands)]
+    B, H = mprev.shape
+    dflt = (torch.zeros(B, H, 2, dtype=mprev.dtype), mprev, torch.zeros_like(mprev))
+    return tuple(_fill(dflt[k], [(hs, f[k]) for hs, f in parts]) for k in range(3))
+
+
+def build_frames_of(x, closed: bool, strands=None):
+    """Initial frames (``build_frames``) of every strand on its own; break edges get
+    tangent z and d1 = x."""
+    if strands is None:
+        return build_frames(x, closed)
+    B, N = x.shape[:2]
+    tz = torch.zeros(B, N - 1, 3, dtype=x.dtype)
+    tz[..., 2] = 1.0
+    dx = torch.zeros(B, N - 1, 3, dtype=x.dtype)
+    dx[..., 0] = 1.0
+    parts = [(es, build_frames(x[:, vs], False)) for vs, es, hs in strand_parts(strands)]
+    t = _fill(tz, [(es, f[0]) for es, f in parts])
+    d1 = _fill(dx, [(es, f[1]) for es, f in parts])
+    return t, d1, torch.zeros(B, dtype=x.dtype)
+
+
+def initial_reference_twist(t, d1r, closed: bool, strands=None):
+    """First reference twist of every hinge: the plain signed angle from the space-transported
+    reference d1 of edge i-1 to that of edge i (0 at the hinges of a break edge)."""
+    def one(t, d1r, closed):
+        ra, rb = hinge_sides(d1r, closed)
+        ta, tb_ = hinge_sides(t, closed)
+        return signed_angle(transport(ta, tb_, ra), rb, tb_)
+    if strands is None:
+        return one(t, d1r, closed)
+    B = t.shape[0]
+    H = t.shape[1] - 1
+    return _fill(torch.zeros(B, H, dtype=t.dtype), [(hs, one(t[:, es], d1r[:, es], False))
+                                                     for vs, es, hs in strand_parts(strands)])
 
 
 class ElasticGradient(torch.autograd.Function):
@@ -211,19 +306,23 @@ class ElasticGradient(torch.autograd.Function):
     angles, reference frames, reference twist, rest curvature and the moduli k_s, B, beta."""
 
     @staticmethod
-    def forward(ctx, x, th, tb, d1b, mprev, kbar, kA, Bm, beta, R, closed):
+    def forward(ctx, x, th, tb, d1b, mprev, kbar, kA, Bm, beta, R, closed, strands=None):
         leaves = [a.detach().requires_grad_(True) for a in (x, th, tb, d1b, mprev, kbar, kA, Bm, beta)]
         with torch.enable_grad():
             R2 = dict(R, kA=leaves[6], Bm=leaves[7], beta=leaves[8])
-            U = elastic_energy(*leaves[:6], R2, closed)
-            gx, gth = torch.autograd.grad(U.sum(), leaves[:2], create_graph=True)
+            U = elastic_energy(*leaves[:6], R2, closed, strands)
+            gx, gth = torch.autograd.grad(U.sum(), leaves[:2], create_graph=True, allow_unused=True)
+            gx = torch.zeros_like(leaves[0]) if gx is None else gx
+            gth = torch.zeros_like(leaves[1]) if gth is None else gth
         ctx.leaves, ctx.outs = leaves, (gx, gth)
         return gx.detach(), gth.detach()
 
     @staticmethod
     def backward(ctx, ggx, ggth):
-        g = torch.autograd.grad(ctx.outs, ctx.leaves, (ggx, ggth), allow_unused=True)
-        return (*g, None, None)
+        outs = [o for o in ctx.outs if o.requires_grad]
+        cots = [c for o, c in zip(ctx.outs, (ggx, ggth)) if o.requires_grad]
+        g = torch.autograd.grad(outs, ctx.leaves, cots, allow_unused=True)
+        return (*g, None, None, None)
 
 
 # --------------------------------------------------------------------------- contact geometry
@@ -317,19 +416,29 @@ class OracleSim:
         self.mat = {k: torch.as_tensor(np.asarray(getattr(prob, k), np.float64)).to(dtype) for k in self.GRAD_PARAMS}
         if params:
             self.mat.update(params)
-        # rest lengths and substep counts per rod
-        self.ebar, self.nsub = [], []
+        # strands of each record (one for a single DLO), rest lengths (0 on break edges) and
+        # substep counts per record
+        starts = getattr(prob, "strand_start", None)
+        self.ebar, self.nsub, self.strands = [], [], []
         for b in range(B):
+            n = int(prob.n_verts[b])
+            st = [0] if starts is None else [0] + [i for i in range(1, n) if starts[self.vo[b] + i]]
+            st.append(n)
+            self.strands.append(tuple(zip(st[:-1], st[1:])))
+            if len(st) > 2 and (prob.closed[b] or min(np.diff(st)) < 2):
+                raise ValueError(f"record {b}: strands need an open record and >= 2 vertices each")
             xr = prob.x_rest[self.vo[b]:self.vo[b + 1]]
             e = (np.roll(xr, -1, 0) - xr) if prob.closed[b] else np.diff(xr, axis=0)
             eb = np.sqrt((e * e).sum(1))
+            for v0, v1 in self.strands[b][:-1]:
+                eb[v1 - 1] = 0.0
             self.ebar.append(eb)
             self.nsub.append(substeps_for(prob.dt, prob.substeps_min, float(prob.density[b]),
                                           float(prob.radius[b]), float(prob.K[b]), float(prob.E[b]),
-                                          float(prob.G[b]), bool(prob.inextensible[b]), float(eb.min())))
+                                          float(prob.G[b]), bool(prob.inextensible[b]), float(eb[eb > 0].min())))
         keys = {}
         for b in range(B):
-            keys.setdefault((int(prob.n_verts[b]), bool(prob.closed[b]), self.nsub[b]), []).append(b)
+            keys.setdefault((int(prob.n_verts[b]), bool(prob.closed[b]), self.nsub[b], self.strands[b]), []).append(b)
         self.groups = [self._group(np.array(ids), *k) for k, ids in sorted(keys.items())]
         self.state = None
         # branch trace: when set to a list, every branch decision of the step (rigid contact
@@ -338,10 +447,23 @@ class OracleSim:
         self.trace = None
 
     # ------------------------------------------------------------------ static per-group data
-    def _group(self, ids, N, closed, nsub):
+    def _group(self, ids, N, closed, nsub, strands):
         p = self.p
         t64 = lambda a: torch.as_tensor(np.asarray(a, np.float64)).to(self.dtype)
-        G = dict(ids=ids, N=N, closed=closed, nsub=nsub, E=N - 1 + int(closed), H=N if closed else N - 2)
+        G = dict(ids=ids, N=N, closed=closed, nsub=nsub, E=N - 1 + int(closed), H=N if closed else N - 2,
+                 strands=strands if len(strands) > 1 else None)
+        # edges and hinges that belong to a strand (all of them for a single DLO), strand of each edge
+        sid = np.full(G["E"], -1, np.int64)
+        for k, (v0, v1) in enumerate(strands):
+            sid[v0:v1 - 1] = k
+        if closed:
+            sid[:] = 0
+        G["sid"] = torch.as_tensor(sid)
+        G["ereal"] = torch.as_tensor(sid >= 0)
+        hreal = np.ones(G["H"], bool)
+        if not closed:
+            hreal = (sid[:-1] >= 0) & (sid[1:] >= 0)
+        G["hreal"] = torch.as_tensor(hreal)
         r = t64(p.radius[ids])
         rho = t64(p.density[ids])
         A = math.pi * r ** 2
@@ -354,6 +476,7 @@ class OracleSim:
         ea, eb_ = hinge_sides(ebar, closed)
         mass = rho[:, None] * A[:, None] * lv                 # reading: lumped Voronoi mass
         inertia = 0.5 * rho[:, None] * A[:, None] * ebar * r[:, None] ** 2   # reading: solid-cylinder axial inertia
+        inertia = torch.where(G["ereal"], inertia, torch.full_like(inertia, math.inf))   # break edges: no twist dynamics
         # kinematic vertices: pinned, or grasped by a gripper (Sec. 3.2)
         kind = np.zeros((len(ids), N), np.int64)
         off = np.zeros((len(ids), N, 3))
@@ -387,10 +510,12 @@ class OracleSim:
         # planar circle of the same length, kbar = (0, 2 tan(pi/N_e)); rest twist = the
         # twist of the initial (rest) frames, so the rest state stores no twist energy)
         xr = t64(np.stack([p.x_rest[self.vo[b]:self.vo[b + 1]] for b in ids]))
-        t0, d10, _ = build_frames(xr, closed)
+        st = G["strands"]
+        t0, d10, _ = build_frames_of(xr, closed, st)
         zero = torch.zeros(len(ids), G["E"], dtype=self.dtype)
-        _, _, d1r0, d1m0, d2m0 = edge_frames(xr, zero, t0, d10, closed)
-        _, mref0, m0 = hinge_strains(t0, d1r0, d1m0, d2m0, zero, torch.zeros(len(ids), G["H"], dtype=self.dtype), closed)
+        _, _, d1r0, d1m0, d2m0 = frames_of(xr, zero, t0, d10, closed, st)
+        _, mref0, m0 = strains_of(t0, d1r0, d1m0, d2m0, zero, torch.zeros(len(ids), G["H"], dtype=self.dtype),
+                                  closed, st)
         R["mbar"] = m0
         kb = torch.zeros(len(ids), G["H"], 2, dtype=self.dtype)
         if closed:
@@ -400,16 +525,19 @@ class OracleSim:
         # never tested; k = max(1, ceil(2r / shortest rest edge)) is the smallest window that
         # leaves a straight rod at its rest lengths with no pair inside the contact distance 2r,
         # so edges two apart still collide and keep a hinge from folding through itself)
-        R["excl"] = [max(1, int(math.ceil(2 * float(p.radius[b]) / float(self.ebar[b].min())))) for b in ids]
+        R["excl"] = [max(1, int(math.ceil(2 * float(p.radius[b]) / float(self.ebar[b][self.ebar[b] > 0].min()))))
+                     for b in ids]
         G["R"] = R
         G["gpos0"] = t64(p.grip_pos[ids])
         G["grot0"] = t64(p.grip_rot[ids])
         G["ngrip"] = torch.as_tensor(p.n_grippers[ids].astype(np.int64))
         # inextensibility colouring (reading: red-black Gauss-Seidel, even edges then odd;
         # loops with an odd edge count give the closing edge a third colour)
+        # (reading: in an environment of several DLOs an edge's colour is the parity of its
+        # index in the record, break edges are skipped)
         E = G["E"]
-        ev = list(range(0, E - (1 if closed and E % 2 == 1 else 0), 2))
-        colors = [ev, list(range(1, E, 2))]
+        ev = [j for j in range(0, E - (1 if closed and E % 2 == 1 else 0), 2) if sid[j] >= 0]
+        colors = [ev, [j for j in range(1, E, 2) if sid[j] >= 0]]
         if closed and E % 2 == 1:
             colors.append([E - 1])
         G["colors"] = [torch.as_tensor(c, dtype=torch.long) for c in colors if c]
@@ -427,16 +555,14 @@ class OracleSim:
         for G in self.groups:
             dt = self.dtype
             xs = self._split(x, G).to(dt)
-            t, d1, _ = build_frames(xs, G["closed"])
+            t, d1, _ = build_frames_of(xs, G["closed"], G["strands"])
             th = self._split(theta, G, "e").to(dt)
             S = dict(x=xs, v=self._split(v, G).to(dt), theta=th, omega=self._split(omega, G, "e").to(dt),
                      tb=t, d1b=d1, kbar=G["R"]["kbar0"].clone(), gp=G["gpos0"].clone(), gR=G["grot0"].clone())
             z = torch.zeros(len(G["ids"]), G["H"], dtype=dt)
-            _, _, d1r, d1m, d2m = edge_frames(xs, th, t, d1, G["closed"])
+            _, _, d1r, d1m, d2m = frames_of(xs, th, t, d1, G["closed"], G["strands"])
             # reading: the first reference twist is the plain signed angle (nothing to unwrap against)
-            ra, rb = hinge_sides(d1r, G["closed"])
-            ta, tb_ = hinge_sides(t, G["closed"])
-            S["mprev"] = signed_angle(transport(ta, tb_, ra), rb, tb_) + z
+            S["mprev"] = initial_reference_twist(t, d1r, G["closed"], G["strands"]) + z
             self.state.append(S)
 
     def set_full_state(self, st):
@@ -512,18 +638,19 @@ class OracleSim:
         p1 = S["gp"] + ((s + 1) / n) * dp
         R1 = expmap(((s + 1) / n) * dphi) @ S["gR"]
         # A1/A3: frames at x, then bending plasticity on the rest curvature
-        t, ell, d1r, d1, d2 = edge_frames(x, th, S["tb"], S["d1b"], closed)
-        kappa, mref, _ = hinge_strains(t, d1r, d1, d2, th, S["mprev"], closed)
+        st = G["strands"]
+        t, ell, d1r, d1, d2 = frames_of(x, th, S["tb"], S["d1b"], closed, st)
+        kappa, mref, _ = strains_of(t, d1r, d1, d2, th, S["mprev"], closed, st)
         kbar = self.plastic_update(G, kappa, S["kbar"])
         # A2: F = -dU/dx, tau = -dU/dtheta (autograd of the energy at the updated kbar)
         if diff:
             gx, gth = ElasticGradient.apply(x, th, S["tb"], S["d1b"], S["mprev"], kbar, R["kA"], R["Bm"],
-                                            R["beta"], R, closed)
+                                            R["beta"], R, closed, st)
         else:
             dx = torch.zeros_like(x, requires_grad=True)
             dth = torch.zeros_like(th, requires_grad=True)
             with torch.enable_grad():
-                U = elastic_energy(x + dx, th + dth, S["tb"], S["d1b"], S["mprev"], kbar, R, closed)
+                U = elastic_energy(x + dx, th + dth, S["tb"], S["d1b"], S["mprev"], kbar, R, closed, st)
                 gx, gth = torch.autograd.grad(U.sum(), [dx, dth])
         # A4/A5: gravity, damping, symplectic Euler velocity update
         grav = torch.tensor([0.0, 0.0, -p.gravity], dtype=self.dtype)
@@ -570,7 +697,7 @@ class OracleSim:
         kel = kappa - kbar
         nk = safe_norm(kel)
         thr = R["sy"][:, None] * R["lbar"]
-        y = R["plastic"][:, None] & (nk > thr)
+        y = R["plastic"][:, None] & (nk > thr) & G["hreal"][None]
         self._note("yield", y)
         nks = torch.where(y, nk, torch.ones_like(nk))
         upd = kbar + (R["rc"][:, None] * (nk - thr) / nks)[..., None] * kel
@@ -667,7 +794,9 @@ class OracleSim:
 
     def candidates(self, G, x):
         """Self-contact candidate pairs for one frame, per rod: edge pairs (a < b) outside the
-        exclusion window whose segments are closer than 2r + margin at the frame start.
+        exclusion window whose segments are closer than 2r + margin at the frame start.  In an
+        environment of several DLOs the window applies within a strand only, and break edges
+        are no segments.
         reading: the paper does not describe its broad phase; the candidate set is defined
         here by this distance test (any exact broad phase returns the same set)."""
         out = []
@@ -676,9 +805,13 @@ class OracleSim:
         sep = ib - ia
         if closed:
             sep = torch.minimum(sep, E - sep)
+        # edges of two different strands (DLOs of one environment) are never excluded
+        sid = G["sid"]
+        real = (sid[ia] >= 0) & (sid[ib] >= 0)
+        other = sid[ia] != sid[ib]
         for i, b in enumerate(G["ids"]):
             k = G["R"]["excl"][i]
-            keep = sep > k
+            keep = real & ((sep > k) | other)
             a, c = ia[keep], ib[keep]
             xb = x[i].detach()
             s, u = closest_params(xb[a], xb[(a + 1) % N], xb[c], xb[(c + 1) % N])
@@ -785,8 +918,10 @@ class OracleSim:
         out = np.zeros((self.p.batch, 3))
         for G, S in zip(self.groups, self.state):
             R = G["R"]
-            U = elastic_energy(S["x"], S["theta"], S["tb"], S["d1b"], S["mprev"], S["kbar"], R, G["closed"])
-            ke = 0.5 * (R["mass"] * dot(S["v"], S["v"])).sum(1) + 0.5 * (R["inertia"] * S["omega"] ** 2).sum(1)
+            U = elastic_energy(S["x"], S["theta"], S["tb"], S["d1b"], S["mprev"], S["kbar"], R, G["closed"],
+                               G["strands"])
+            Iw = torch.where(G["ereal"], R["inertia"] * S["omega"] ** 2, torch.zeros_like(S["omega"]))
+            ke = 0.5 * (R["mass"] * dot(S["v"], S["v"])).sum(1) + 0.5 * Iw.sum(1)
             pe = (R["mass"] * S["x"][..., 2]).sum(1) * self.p.gravity
             out[G["ids"]] = torch.stack([ke, U, pe], 1).detach().numpy()
         return out

@@ -29,6 +29,11 @@ Workloads (seeds are ``numpy.random.default_rng(config_index*1000 + repeat)``):
                  elastic rope (Unknotting row), plastic wire (Letter-Art row),
                  grasped at 1/4 and 3/4 of their length by two grippers with
                  smooth random 6-DoF trajectories, 2000 frames.
+* ``separation`` 4096 environments of the Separation task: two tangled ropes
+                 of 30 vertices (inextensible, E=5e3 Pa, G=1e3 Pa), 0.6 m,
+                 stored as one record of two strands, one gripper on each,
+                 pulled apart and lifted along smooth random trajectories,
+                 self-contact (which couples the ropes), 2000 frames.
 * ``cmaes``      one CMA-ES generation of Unknotting: 400 copies of one knotted
                  rope (128 vertices, opened trefoil-family curve on the table,
                  Unknotting row), mean gripper trajectory plus per-candidate
@@ -45,7 +50,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field, replace
 import numpy as np
 
-__all__ = ["Problem", "plain", "batching", "diff", "selfcontact", "trajopt", "cmaes",
+__all__ = ["Problem", "plain", "batching", "diff", "selfcontact", "trajopt", "cmaes", "separation",
            "small_case", "custom", "f32"]
 
 
@@ -93,6 +98,7 @@ class Problem:
     gravity: float = 9.81
     checkpoint_every: int = 50
     target: np.ndarray | None = None   # [V,3] loss target (diff / trajopt)
+    strand_start: np.ndarray | None = None   # [V] bool: vertex begins another DLO of its environment
     x0: np.ndarray | None = None
     v0: np.ndarray | None = None
     theta0: np.ndarray | None = None
@@ -101,6 +107,9 @@ class Problem:
     def __post_init__(self):
         self.n_verts = np.asarray(self.n_verts, np.int32)
         self.closed = np.asarray(self.closed, bool)
+        if self.strand_start is None:
+            self.strand_start = np.zeros(len(self.x_rest), bool)
+        self.strand_start = np.asarray(self.strand_start, bool)
         if self.x0 is None:
             self.x0 = self.x_rest.copy()
         if self.v0 is None:
@@ -139,6 +148,7 @@ class Problem:
             "strain_limit", "plastic", "yield_curv", "creep_rate", "damping",
             "n_grippers", "grip_pos", "grip_rot")}
         return replace(self, x_rest=self.x_rest[vsel], pinned=self.pinned[vsel],
+                       strand_start=self.strand_start[vsel],
                        actions=self.actions[:f, rods], frames=f,
                        target=None if self.target is None else self.target[vsel],
                        x0=self.x0[vsel], v0=self.v0[vsel], theta0=self.theta0[esel],
@@ -421,6 +431,80 @@ def cmaes(pop: int = 400, frames: int = 2000, seed: int = 5000, n: int = 128, si
                      planes=np.array([[0.0, 0.0, 1.0, 0.0]]), self_contact=True)
 
 
+def _tangled_pair(rng, n: int, length: float, radius: float, z_min: float):
+    """Two ropes of n vertices and the given length lying across each other on the table.
+
+    Both follow x over the same span; across it the offsets (y, z) = +-(a sin th, d cos th)
+    with th = 2 pi k s + phi put them on opposite sides of a common centre line, so they
+    cross wherever sin th = 0, one over and one under, the order alternating from crossing to
+    crossing (a braid: the ropes are tangled).  At every parameter s they are at least 2 d
+    apart, d = 1.5 r, a gap of one radius.  A shared smooth sideways wiggle, a random heading
+    and a random place on the table follow.  The span is 0.85 of the length, so each rope is
+    about ``length`` long.  Returns the two (n, 3) ropes."""
+    dense = 2048
+    d = 1.5 * radius
+    for _ in range(200):
+        k = rng.uniform(1.2, 1.8)
+        phi = rng.uniform(0.0, 2.0 * np.pi)
+        a = rng.uniform(0.03, 0.05)
+        s = np.linspace(0.0, 1.0, dense)
+        th = 2.0 * np.pi * k * s + phi
+        wig = np.zeros(dense)
+        for m in range(1, 3):
+            wig += rng.uniform(-0.02, 0.02) / m * np.sin(2.0 * np.pi * m * s + rng.uniform(0.0, 2.0 * np.pi))
+        span = length * 0.85
+        base = np.stack([(s - 0.5) * span, wig, np.full(dense, z_min + d)], axis=1)
+        off = np.stack([np.zeros(dense), a * np.sin(th), d * np.cos(th)], axis=1)
+        ropes = [_resample(base + sign * off, n) for sign in (1.0, -1.0)]
+        ang = rng.uniform(0.0, 2.0 * np.pi)
+        Rz = np.array([[np.cos(ang), -np.sin(ang), 0.0], [np.sin(ang), np.cos(ang), 0.0], [0.0, 0.0, 1.0]])
+        c = np.append(rng.uniform(-0.25, 0.25, 2), 0.0)
+        ropes = [r @ Rz.T + c for r in ropes]
+        gap = np.linalg.norm(ropes[0][:, None] - ropes[1][None], axis=2).min()
+        crossings = np.count_nonzero(np.diff(np.sign(np.sin(th))) != 0)
+        if gap >= 2.5 * radius and crossings >= 2 and _max_curvature(ropes[0]) <= 50.0:
+            return ropes
+    raise RuntimeError("could not draw a tangled pair of ropes")
+
+
+def separation(n_envs: int = 4096, frames: int = 2000, seed: int = 6000, n: int = 30,
+               length: float = 0.6) -> Problem:
+    """The Separation task's scene, repeated over environments: two tangled ropes of n
+    vertices each (Separation rows: inextensible, E = 5e3 Pa, G = 1e3 Pa), stored as one
+    record of two strands, on the table.  Gripper 0 holds the first rope and gripper 1 the
+    second, each at the vertex of its half where the ropes are furthest apart; they follow
+    smooth random 6-DoF trajectories plus a drift that pulls the ropes apart sideways (0.15 m
+    over the episode) and lifts them by 3 cm.  Self-contact on, which is what couples the
+    two ropes."""
+    rng = np.random.default_rng(seed)
+    recs, gp, gr, drift = [], np.zeros((n_envs, 2, 3)), np.tile(np.eye(3), (n_envs, 2, 1, 1)), []
+    for b in range(n_envs):
+        A, Bp = _tangled_pair(rng, n, length, 0.002, 0.005)
+        recs.append(np.concatenate([A, Bp]))
+        sep = np.linalg.norm(A - Bp, axis=1)
+        lo, hi = int(0.15 * (n - 1)), int(0.4 * (n - 1))
+        ka = lo + int(np.argmax(sep[lo:hi + 1]))
+        kb = (n - 1 - hi) + int(np.argmax(sep[n - 1 - hi:n - lo]))
+        for g, (rope, k) in enumerate(((A, ka), (Bp, kb))):
+            gp[b, g] = rope[k]
+            gr[b, g] = _gripper_frame(rope[min(k + 1, n - 1)] - rope[max(k - 1, 0)])
+        out = A[ka] - Bp[kb]
+        out[2] = 0.0
+        out /= max(np.linalg.norm(out), 1e-9)
+        drift.append(out)
+    acts = _smooth_actions(rng, frames, n_envs, 1e-3)
+    dirs = np.stack(drift)
+    acts[:, :, 0, :3] += (0.15 / frames) * dirs[None]
+    acts[:, :, 1, :3] -= (0.15 / frames) * dirs[None]
+    acts[:, :, :, 2] += 0.03 / frames
+    start = np.zeros(2 * n * n_envs, bool)
+    start[n::2 * n] = True
+    return _assemble("separation", recs, np.zeros(n_envs, bool),
+                     dict(K=0.0, E=5e3, G=1e3, inextensible=True),
+                     frames, acts, np.full(n_envs, 2), gp, gr,
+                     planes=np.array([[0.0, 0.0, 1.0, 0.0]]), self_contact=True, strand_start=start)
+
+
 def custom(rods_x, closed=None, frames: int = 1, actions=None, n_grippers=None, grip_pos=None,
            grip_rot=None, pinned=None, **kw) -> Problem:
     """A hand-made workload: explicit rod shapes plus material / option overrides."""
@@ -455,4 +539,6 @@ def small_case(kind: str, n_rods: int = 4, n: int = 24, frames: int = 10, seed: 
         return cmaes(n_rods, frames, seed, n)
     if kind == "trajopt":
         return trajopt(n_rods, frames, seed, n, self_contact=True)
+    if kind == "separation":
+        return separation(n_rods, frames, seed, n)
     raise ValueError(kind)

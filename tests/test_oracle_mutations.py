@@ -4,8 +4,9 @@ Each case edits one expression of one oracle function (a flipped sign, a dropped
 swapped operand, a wrong index or weight), installs the edited copy in place of the original
 for the duration of the test, and runs the pin that is meant to catch that mistake: the pin
 must fail with an assertion.  This shows that the pins of the self-collision projection, the
-gripper kinematics, damping and self-contact friction constrain the oracle's arithmetic and
-not only its shape.  Nothing here touches the device code.
+gripper kinematics, damping, self-contact friction and environments of several DLOs
+constrain the oracle's arithmetic and not only its shape.  Nothing here touches the device
+code.
 """
 import inspect
 import textwrap
@@ -13,6 +14,7 @@ import textwrap
 import pytest
 
 import oracle.dlo as O
+import test_oracle_envs as V
 import test_oracle_pins as P
 
 
@@ -100,9 +102,41 @@ def test_friction_pin_catches(what, old, new, monkeypatch):
     run_pin(P.test_self_contact_friction_obeys_coulomb, 0)
 
 
+ENVIRONMENT = [
+    ("window applied across strands", "keep = real & ((sep > k) | other)", "keep = real & (sep > k)",
+     O.OracleSim, "candidates", V.test_adjacent_segments_of_different_strands_collide, (0,)),
+    ("break edge taken as a segment", "keep = real & ((sep > k) | other)", "keep = (sep > k) | other",
+     O.OracleSim, "candidates", V.test_the_edge_between_strands_is_no_segment, ()),
+    ("break edge projected to its length", "colors = [ev, [j for j in range(1, E, 2) if sid[j] >= 0]]",
+     "colors = [ev, list(range(1, E, 2))]", O.OracleSim, "_group",
+     V.test_far_apart_strands_step_like_separate_rods, ("plastic_inext",)),
+    ("break edge counted in the Voronoi masses", "eb[v1 - 1] = 0.0", "eb[v1 - 1] = eb[v1 - 1]",
+     O.OracleSim, "__init__", V.test_far_apart_strands_step_like_separate_rods, ("elastic",)),
+    ("energy taken over the whole record", "st = G[\"strands\"]\n", "st = None\n",
+     O.OracleSim, "substep", V.test_far_apart_strands_step_like_separate_rods, ("elastic",)),
+    ("frames transported across the break", "    if strands is None:\n        return build_frames(x, closed)",
+     "    if True:\n        return build_frames(x, closed)", O, "build_frames_of",
+     V.test_far_apart_strands_step_like_separate_rods, ("elastic",)),
+    ("contact moves one strand only", "delta = delta.index_add(0, c0, -(k * w[c0] * (1 - u))[:, None] * nrm)",
+     "delta = delta.index_add(0, c0, 0.0 * (k * w[c0] * (1 - u))[:, None] * nrm)", O.OracleSim, "contact_sweep",
+     V.test_momentum_conserved_between_two_ropes, ()),
+]
+
+
+@pytest.mark.parametrize("what,old,new,owner,fn,pin,args", ENVIRONMENT, ids=[c[0] for c in ENVIRONMENT])
+def test_environment_pins_catch(what, old, new, owner, fn, pin, args, monkeypatch):
+    install_mutant(monkeypatch, owner, fn, old, new)
+    run_pin(pin, *args)
+
+
 def test_unmutated_pins_pass():
     """The same pins with the oracle as it is (the baseline of the cases above)."""
     P.test_self_contact_projection_single_pair(0)
     P.test_gripper_kinematics_closed_form("both")
     P.test_damping_decays_velocity_and_twist_rate_geometrically()
     P.test_self_contact_friction_obeys_coulomb(0)
+    V.test_adjacent_segments_of_different_strands_collide(0)
+    V.test_the_edge_between_strands_is_no_segment()
+    V.test_far_apart_strands_step_like_separate_rods("plastic_inext")
+    V.test_far_apart_strands_step_like_separate_rods("elastic")
+    V.test_momentum_conserved_between_two_ropes()
