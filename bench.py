@@ -17,9 +17,10 @@ roofline     the dominant kernel (the backward) against the FP32 CUDA-core peak 
 cpu_baseline the FP64 oracle on the host cores, on a bounded sample of the same workload
 plain        the plain per-phase GPU step (dlo_step_plain) on the same rods
 
-`--workload` selects the other configurations (batching, selfcontact, diff) or ``cmaes``: one
-CMA-ES generation of the Unknotting task per step (400 candidate rollouts of one knotted rope,
-forward only, each scored on the device by its crossing sum and self-repulsion penalty).
+`--workload` selects the other configurations (batching, selfcontact, diff, separation: two
+tangled ropes per environment coupled by contact) or ``cmaes``: one CMA-ES generation of the
+Unknotting task per step (400 candidate rollouts of one knotted rope, forward only, each
+scored on the device by its crossing sum and self-repulsion penalty).
 
 `--impl reference` times the oracle instead (the reference arm of this benchmark).
 """
@@ -67,7 +68,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="trajopt",
-                    choices=["trajopt", "batching", "selfcontact", "diff", "cmaes", "sysid", "trajopt-opt"],
+                    choices=["trajopt", "batching", "selfcontact", "diff", "cmaes", "sysid", "trajopt-opt",
+                             "separation"],
                     help="trajopt is the headline line; the others measure the other configurations")
     ap.add_argument("--iters", type=int, default=50, help="trajopt-opt: Adam iterations")
     ap.add_argument("--frames", type=int, default=None)
@@ -80,7 +82,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--plain-frames", type=int, default=20)
     ap.add_argument("--no-side", action="store_true",
-                    help="trajopt: skip the one-shot measurements of the self-contact and batching workloads")
+                    help="trajopt: skip the one-shot measurements of the self-contact, batching and separation "
+                         "workloads")
     return ap.parse_args()
 
 
@@ -266,7 +269,7 @@ def run_reference(args, rank, ws):
 # rods, vertices per rod, frames of each workload (the configurations' own sizes)
 WORKLOADS = {"trajopt": (4096, 128, 2000), "batching": (1024, None, 1000), "selfcontact": (4096, 200, 300),
              "diff": (256, 64, 500), "cmaes": (400, 128, 2000), "sysid": (256, 64, 500),
-             "trajopt-opt": (512, 128, 200)}
+             "trajopt-opt": (512, 128, 200), "separation": (4096, 30, 2000)}
 SIL_HW, SIL_TAU = 256, 0.5  # system identification: two 256 x 256 cameras, edge softness in pixels
 ACTION_UNIT = 1e-3         # trajopt-opt: the optimised action corrections are in mm and mrad per frame
 REPULSION_WEIGHT = 1e3     # the Unknotting penalty's weight against the crossing sum
@@ -302,6 +305,11 @@ def make_workload(args, rank):
         prob = inputs.cmaes(pop=R, frames=F, seed=5000 + rank, n=N)
         desc = (f"cmaes: one CMA-ES generation of Unknotting, population {R} x {N} vertices (one knotted rope, "
                 f"sigma 5e-2), {F} frames forward, ground, self-contact, crossing-sum + repulsion scores")
+    elif w == "separation":
+        prob = inputs.separation(n_envs=R, frames=F, seed=6000 + rank, n=N)
+        desc = (f"separation: {R} environments x 2 tangled ropes of {N} vertices (one record of two strands, "
+                f"inextensible, E 5e3 Pa, G 1e3 Pa), one gripper on each rope pulling them apart, ground, "
+                f"self-contact between and within the ropes, {F} frames")
     elif w == "selfcontact":
         prob = inputs.selfcontact(n_rods=R, frames=F, seed=3000 + rank, n=N)
         desc = f"selfcontact: {R} knotted closed bands x {N} vertices, ground + box, self-contact, {F} frames"
@@ -313,21 +321,23 @@ def make_workload(args, rank):
 
 def side_workloads(args, rank):
     """One timed forward + backward of the self-contact configuration (4096 knotted bands x 200
-    vertices, 300 frames, with each broad phase) and of the batching configuration (1024 rods of
-    16..256 vertices, per-rod substeps; 100 of its 1000 frames), after one warm-up each, with
-    the plain per-phase forward on the same rods.  Reported beside the headline, not in it."""
+    vertices, 300 frames, with each broad phase), of the batching configuration (1024 rods of
+    16..256 vertices, per-rod substeps; 100 of its 1000 frames) and of the Separation
+    environments (4096 x two tangled 30-vertex ropes, 300 of its 2000 frames, with each broad
+    phase), after one warm-up each, with the plain per-phase forward on the same rods.
+    Reported beside the headline, not in it."""
     import copy
     import numpy as np
     import torch
     from paper_2606_04206_gb300 import dlo
     out = {}
-    for kind, frames in (("selfcontact", 300), ("batching", 100)):
+    for kind, frames in (("selfcontact", 300), ("batching", 100), ("separation", 300)):
         a2 = copy.copy(args)
         a2.workload, a2.frames, a2.rods, a2.verts = kind, frames, None, None
         prob, desc, R, F = make_workload(a2, rank)
         units = float(np.sum(prob.n_verts)) * F
         res = {"workload": desc, "frames": F}
-        for bp in ((0, 1) if kind == "selfcontact" else (0,)):
+        for bp in ((0, 1) if kind in ("selfcontact", "separation") else (0,)):
             sim = dlo.DloSim(prob, broad_phase=bp)
             dev = sim.device
             stream = torch.cuda.current_stream()

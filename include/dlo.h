@@ -71,7 +71,8 @@ typedef struct {
     int   closed;         /* 1: closed loop (edge Nv-1 joins vertex Nv-1 to vertex 0) */
 } dlo_material;
 
-/* Rigid scene shared by every rod (each rod is its own environment), plus per-rod grippers. */
+/* Rigid scene shared by every rod (each rod is its own environment), plus per-rod grippers
+ * and, optionally, the strands of rods that hold several DLOs of one environment. */
 typedef struct {
     int          n_planes;      /* <= 4 */
     const float* planes;        /* host [n_planes][4]: unit normal n, offset o (n.x = o) */
@@ -83,6 +84,15 @@ typedef struct {
     float        grip_radius;   /* capsule radius, m */
     float        grip_half_len; /* capsule half length, m */
     const unsigned char* pinned;/* host [V] 1 = vertex fixed in space, or NULL */
+    const unsigned char* strand_start; /* host [V] 1 = the vertex begins another DLO of the same
+                                   environment, or NULL.  A rod with strand starts holds several
+                                   DLOs back to back ("strands", e.g. the two ropes of the
+                                   Separation task, Sec. 4): they share its material, substeps
+                                   and grippers, interact only through self-collision and friction
+                                   (App. A.1), and nothing joins them; the edge between two
+                                   strands has no force, no length constraint, keeps its frame
+                                   (tangent z, d1 = x) and is no contact segment.  Only open rods;
+                                   every strand has >= 2 vertices (else DLO_ERR_INVALID_ARG) */
 } dlo_scene;
 
 typedef struct {
@@ -277,8 +287,9 @@ enum {
  * terms in App. B; the crossing sum's pair term is the standard closed form of the Gauss
  * integral for straight segments (a reading of "signed crossing contributions").
  * Errors: DLO_ERR_INVALID_ARG for an unknown kind, a missing or unaligned array, m out of
- * range or rods of more than 256 vertices.  A repulsion window k < 1 (read on the device)
- * is taken as 1. */
+ * range, rods of more than 256 vertices, or a loss over edges (winding, crossing,
+ * repulsion) on a context with strands (dlo_scene.strand_start).  A repulsion window k < 1
+ * (read on the device) is taken as 1. */
 dlo_status dlo_loss(dlo_ctx* ctx, int kind, const float* x, const float* aux, int m, const float* g, float* q,
                     float* dL_dx);
 
@@ -301,8 +312,8 @@ dlo_status dlo_loss(dlo_ctx* ctx, int kind, const float* x, const float* aux, in
  *   render  [B][n_cams][height][width] device floats: the soft silhouettes o (NULL = not wanted)
  * Grows a context workspace of B * height * width floats.  Enqueued on the context's stream,
  * deterministic.  Errors: DLO_ERR_INVALID_ARG for a missing or unaligned array, no camera,
- * more than 2^24 pixels, tau <= 0 or rods of more than 256 vertices; DLO_ERR_OOM when the
- * workspace cannot grow. */
+ * more than 2^24 pixels, tau <= 0, rods of more than 256 vertices or a context with strands
+ * (dlo_scene.strand_start); DLO_ERR_OOM when the workspace cannot grow. */
 dlo_status dlo_loss_silhouette(dlo_ctx* ctx, const float* x, const float* cams, int n_cams, int height, int width,
                                const unsigned char* masks, float tau, const float* g, float* q, float* dL_dx,
                                float* render);

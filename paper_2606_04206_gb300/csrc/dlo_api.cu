@@ -169,9 +169,35 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         const bool closed = m.closed != 0;
         const int ne = nv - 1 + (closed ? 1 : 0);
         const double r = m.radius, rho = m.density, A = M_PI * r * r;
+        // strands: edge j is a break edge when vertex j + 1 begins another DLO; every strand
+        // has at least two vertices, and only open rods have strands
+        std::vector<char> brk(ne, 0);
+        bool has_strands = false;
+        if (scene && scene->strand_start) {
+            int last = 0;
+            for (int i = 1; i < nv; ++i)
+                if (scene->strand_start[v0 + i]) {
+                    if (closed || i - last < 2) {
+                        delete c;
+                        return DLO_ERR_INVALID_ARG;
+                    }
+                    brk[i - 1] = 1;
+                    last = i;
+                    has_strands = true;
+                }
+            if (has_strands && nv - last < 2) {
+                delete c;
+                return DLO_ERR_INVALID_ARG;
+            }
+        }
         std::vector<double> eb(ne);
         double lmin = 1e300;
         for (int j = 0; j < ne; ++j) {
+            if (brk[j]) {   // rest length 0, no axial inertia (its twist angle only decays)
+                eb[j] = 0.0;
+                es[e0 + j] = make_float2(0.f, 0.f);
+                continue;
+            }
             int j1 = (j + 1 == nv) ? 0 : j + 1;
             double dx = (double)x_rest[3 * (v0 + j1)] - x_rest[3 * (v0 + j)];
             double dy = (double)x_rest[3 * (v0 + j1) + 1] - x_rest[3 * (v0 + j) + 1];
@@ -253,7 +279,8 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
         R.nsub = ns;
         R.flags = (inext ? ROD_INEXT : 0) | (m.plastic ? ROD_PLASTIC : 0) |
                   (!inext && m.strain_limit > 0.f ? ROD_SLIMIT : 0) | (opt->self_contact ? ROD_SELF : 0) |
-                  (closed ? ROD_CLOSED : 0) | (opt->broad_phase == 1 ? ROD_HASH : 0);
+                  (closed ? ROD_CLOSED : 0) | (opt->broad_phase == 1 ? ROD_HASH : 0) |
+                  (has_strands ? ROD_STRANDS : 0);
         R.ngrip = ng;
         R.excl = std::max(1, (int)std::ceil(2.0 * r / lmin));
         set_moduli(R, m, ns, opt->dt);

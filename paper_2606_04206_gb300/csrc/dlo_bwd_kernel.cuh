@@ -547,9 +547,14 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         add3(lphif, q, m0 + m1);
     }
     // ---- B8: per edge, reverse of the new reference-frame base and stretching second order
+    const bool strands = R.flags & ROD_STRANDS;
     for (int j = g.tid; j < ne; j += TPR) {
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
         const float4 ed = s.ED[j], et = s.ET[j];
+        if (strands && !(et.w > 0.f)) {   // a break edge kept its base frame: identity reverse
+            s.HB1[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         EdgeF<float> E;
         edge_forward(E, f3(s.X0[j]), f3(s.X0[j1]), f3(et), f3(ed), ed.w);
         V3<float> gtb, gd1b;
@@ -579,6 +584,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         const int ea = (i == 0) ? ne - 1 : i - 1, eb = i;
         const int im = (i == 0) ? nv - 1 : i - 1, ip = (i + 1 == nv) ? 0 : i + 1;
         const float4 EDa = s.ED[ea], EDb = s.ED[eb], ETa = s.ET[ea], ETb = s.ET[eb], hg = s.HG[i];
+        if (strands && !(ETa.w > 0.f && ETb.w > 0.f)) continue;   // inactive: at an end of a break edge
         const float lbar = 0.5f * (ETa.w + ETb.w), il = 1.f / lbar;
         // second order of the elastic force: tangents = cotangents of the gradient
         HingeF<dualf> Hd;

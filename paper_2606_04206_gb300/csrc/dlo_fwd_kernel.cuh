@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
                         const double ex = (double)s.X[j1].x - (double)s.X[j].x;
                         const double ey = (double)s.X[j1].y - (double)s.X[j].y;
                         const double ez = (double)s.X[j1].z - (double)s.X[j].z;
-                        r += fabs(sqrt(ex * ex + ey * ey + ez * ez) - (double)s.ET[j].w);
+                        if (s.ET[j].w > 0.f)   // not a break edge
+                            r += fabs(sqrt(ex * ex + ey * ey + ez * ez) - (double)s.ET[j].w);
                     }
                     r = grp_sum<TPR>(r, g);
                     if (g.tid == 0) P.residual[rod] = r;

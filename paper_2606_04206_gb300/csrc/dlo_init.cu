@@ -6,7 +6,9 @@
 // hinge, measured about t^0) is spread as phi^j = -psi_H j / N_e and each (d1, d2) rotated by
 // phi^j ("Loop Topology").  The reference twist of each hinge is the signed angle from the
 // transported d1 of the previous edge to d1 of the next; in rest mode it becomes the rest
-// twist, so the rest state stores no twist energy.
+// twist, so the rest state stores no twist energy.  A record of several strands (ROD_STRANDS)
+// starts each strand like edge 0; a break edge between two strands gets tangent z and d1 = x,
+// and the hinges at its two ends a reference (and rest) twist of 0.
 #include "dlo_kernels.h"
 #include "dlo_physics.cuh"
 
@@ -24,10 +26,16 @@ __global__ void init_kernel(InitParams P) {
     const bool closed = R.flags & ROD_CLOSED;
     auto X = [&](int i) { return ld(P.xin[v0 + i]); };
     auto T = [&](int j) { return unit_d(X(j + 1 == nv ? 0 : j + 1) - X(j)); };
+    // the first frame of an open rod or strand: the projection of a fixed axis
+    auto first_d1 = [](V3<double> t) {
+        V3<double> ax = fabs(t.z) < 0.9 ? V3<double>{0.0, 0.0, 1.0} : V3<double>{1.0, 0.0, 0.0};
+        return adapt_d(ax, t);
+    };
+    const bool strands = R.flags & ROD_STRANDS;
+    auto brk = [&](int j) { return strands && !(P.ES[e0 + j].x > 0.f); };
     // edge 0
     V3<double> t0 = T(0);
-    V3<double> a = fabs(t0.z) < 0.9 ? V3<double>{0.0, 0.0, 1.0} : V3<double>{1.0, 0.0, 0.0};
-    V3<double> d = adapt_d(a, t0);
+    V3<double> d = first_d1(t0);
     double psi = 0.0;
     if (closed) {   // first pass: holonomy of the space-parallel transport around the loop
         V3<double> tp = t0, dd = d;
@@ -42,8 +50,10 @@ __global__ void init_kernel(InitParams P) {
     // second pass: frames (with the holonomy correction) and reference twists
     V3<double> tp = t0, dp = d, d1p = d, tfirst = t0, d1first = d;
     for (int j = 0; j < ne; ++j) {
-        V3<double> tj = T(j);
-        V3<double> dj = j == 0 ? d : adapt_d(transport_d(tp, tj, dp), tj);
+        const bool bj = brk(j), start = j > 0 && brk(j - 1);
+        V3<double> tj = bj ? V3<double>{0.0, 0.0, 1.0} : T(j);
+        V3<double> dj = bj ? V3<double>{1.0, 0.0, 0.0}
+                           : (j == 0 ? d : (start ? first_d1(tj) : adapt_d(transport_d(tp, tj, dp), tj)));
         dp = dj;
         V3<double> d1 = dj;
         if (closed) {
@@ -52,7 +62,7 @@ __global__ void init_kernel(InitParams P) {
         }
         if (j > 0) {   // hinge at vertex j between edges j-1 and j
             V3<double> u = transport_d(tp, tj, d1p);
-            double ang = atan2(dot(cross(u, d1), tj), dot(u, d1));
+            double ang = (bj || start) ? 0.0 : atan2(dot(cross(u, d1), tj), dot(u, d1));
             if (P.rest_mode) P.rest[v0 + j].z = (float)ang;
             else {
                 float4 rs = P.rest[v0 + j];

@@ -11,8 +11,17 @@ enum RodFlags : int {
     ROD_SLIMIT = 4,      // elastic stretching plus strain-limit projection
     ROD_SELF = 8,        // self-contact on
     ROD_CLOSED = 16,
-    ROD_HASH = 32        // self-contact candidates through the per-rod spatial hash
+    ROD_HASH = 32,       // self-contact candidates through the per-rod spatial hash
+    ROD_STRANDS = 64     // several DLOs of one environment back to back; the edge between two
+                         // of them ("break") has rest length 0 and carries no force (see below)
 };
+
+// An environment of several DLOs is one record whose vertices are the DLOs' vertices back to
+// back ("strands", open only).  The edge that joins the last vertex of one strand to the
+// first of the next is no part of the model: its rest length (ES.x, ET.w) is 0, its inverse
+// axial inertia 0, it keeps the frame it was given (tangent z, d1 = x), it is no segment for
+// self-contact, and the hinges at its two ends are inactive.  Everything else, self-contact
+// between strands included, is the single-rod code path.
 
 // One rod: offsets into the packed arrays and its per-rod constants (64 bytes).
 struct RodInfo {

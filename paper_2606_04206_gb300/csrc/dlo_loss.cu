@@ -309,8 +309,13 @@ extern "C" dlo_status dlo_loss(dlo_ctx* c, int kind, const float* x, const float
     float4* GX = reinterpret_cast<float4*>(dL_dx);
     if (!x || ((uintptr_t)x & 15u) || (dL_dx && ((uintptr_t)dL_dx & 15u)) || (aux && ((uintptr_t)aux & 15u)))
         return set_err(c, DLO_ERR_INVALID_ARG, "x, aux and dL_dx must be non-null device float4 arrays (16-byte aligned)");
-    for (const auto& R : c->rods_h)
+    for (const auto& R : c->rods_h) {
         if (R.nv > kMaxV) return set_err(c, DLO_ERR_INVALID_ARG, "rod too long for the loss kernels");
+        // the losses over a rod's edges take single DLOs: nothing joins the strands of a record
+        if ((R.flags & ROD_STRANDS) &&
+            (kind == DLO_LOSS_WINDING || kind == DLO_LOSS_CROSSING || kind == DLO_LOSS_REPULSION))
+            return set_err(c, DLO_ERR_INVALID_ARG, "edge-based losses need rods without strands");
+    }
     switch (kind) {
         case DLO_LOSS_TARGET:
             if (!aux) return set_err(c, DLO_ERR_INVALID_ARG, "the target loss needs target positions");

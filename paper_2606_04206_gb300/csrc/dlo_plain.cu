@@ -65,22 +65,30 @@ __global__ void pl_pose_advance(const RodInfo* rods, int B, float* GP, const flo
 
 // candidates of one frame: every edge pair of a rod outside the exclusion window whose
 // segments are closer than the candidate distance (one thread per first edge)
-__global__ void pl_broad(const RodInfo* rods, const int* erod, long long Et, const float4* X, const int* poff,
-                         int* npair, uint32_t* pairs, unsigned* status) {
+__global__ void pl_broad(const RodInfo* rods, const int* erod, long long Et, const float2* ES, const float4* X,
+                         const int* poff, int* npair, uint32_t* pairs, unsigned* status) {
     const long long ge = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (ge >= Et) return;
     const int b = erod[ge];
     const RodInfo R = rods[b];
     if (!(R.flags & ROD_SELF)) return;
-    const bool closed = R.flags & ROD_CLOSED;
+    const bool closed = R.flags & ROD_CLOSED, strands = R.flags & ROD_STRANDS;
     const int a = (int)(ge - R.e0), nv = R.nv, ne = R.ne;
+    // break edges (between the strands of one record) are no segments
+    auto real = [&](int j) { return !strands || ES[R.e0 + j].x > 0.f; };
+    if (!real(a)) return;
     const int a1 = (a + 1 == nv) ? 0 : a + 1;
     const V3<float> pa0 = f3(X[R.v0 + a]), pa1 = f3(X[R.v0 + a1]);
     bool ovf = false;
     for (int c = a + 1; c < ne; ++c) {
+        if (!real(c)) continue;
         int sep = c - a;
         if (closed) sep = min(sep, ne - sep);
-        if (sep <= R.excl) continue;
+        if (sep <= R.excl) {   // the window applies within one strand
+            bool other = false;
+            for (int k = a + 1; strands && k < c; ++k) other |= !real(k);
+            if (!other) continue;
+        }
         const int c1 = (c + 1 == nv) ? 0 : c + 1;
         const V3<float> pb0 = f3(X[R.v0 + c]), pb1 = f3(X[R.v0 + c1]);
         float su, uu;
@@ -112,6 +120,11 @@ __global__ void pl_hinge(const RodInfo* rods, const int* vrod, long long V, cons
     const int im = (i == 0) ? nv - 1 : i - 1;
     const int ip = (i + 1 == nv) ? 0 : i + 1;
     const float4 EDa = ED[R.e0 + a], EDb = ED[R.e0 + b], ETa = ET[R.e0 + a], ETb = ET[R.e0 + b];
+    const bool strands = R.flags & ROD_STRANDS;
+    if (strands && !(ETa.w > 0.f && ETb.w > 0.f)) {   // a hinge at an end of a break edge
+        HB0[gv] = HB1[gv] = HB2[gv] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     float4 hg = HG[gv];
     HingeF<float> H;
     hinge_forward(H, f3(X[R.v0 + im]), f3(X[gv]), f3(X[R.v0 + ip]), f3(ETa), f3(EDa), f3(ETb), f3(EDb), EDa.w,
@@ -129,7 +142,8 @@ __global__ void pl_hinge(const RodInfo* rods, const int* vrod, long long V, cons
     HB1[gv] = f4(gxi, gtb);
     HB2[gv] = f4(gxp, 0.f);
     NDR[R.e0 + b] = f4(H.b.d1r, 0.f);
-    if (!closed && i == 1) NDR[R.e0] = f4(H.a.d1r, 0.f);
+    // the first edge of an open rod or strand gets its frame from its only hinge
+    if (!closed && (i == 1 || (strands && !(ET[R.e0 + a - 1].w > 0.f)))) NDR[R.e0 + a] = f4(H.a.d1r, 0.f);
     HG[gv] = make_float4(hg.x, hg.y, hg.z, H.mref);
 }
 
@@ -168,7 +182,9 @@ __global__ void pl_vertex(SceneDev sc, const RodInfo* rods, const int* vrod, lon
     }
     if ((closed || i >= 2) && has_h(im)) g += f3(HB2[v0 + im]);
     V3<float> t_i = zf3();
-    if (has_e) {
+    const bool strands = R.flags & ROD_STRANDS;
+    const bool brk = strands && has_e && !(ES[e0 + i].x > 0.f);   // a break edge starts here
+    if (has_e && !brk) {
         const V3<float> e = f3(X[v0 + ip]) - xi;
         const float ell_i = sqrtf(dot(e, e));
         t_i = e / ell_i;
@@ -177,7 +193,7 @@ __global__ void pl_vertex(SceneDev sc, const RodInfo* rods, const int* vrod, lon
             g -= (R.kA * (ell_i / eb - 1.f)) * t_i;
         }
     }
-    if (R.kA > 0.f && (closed || i >= 1)) {
+    if (R.kA > 0.f && (closed || i >= 1) && !(strands && !(ES[e0 + im].x > 0.f))) {
         const V3<float> e = xi - f3(X[v0 + im]);
         const float ell = sqrtf(dot(e, e));
         const float eb = ES[e0 + im].x;
@@ -211,14 +227,21 @@ __global__ void pl_vertex(SceneDev sc, const RodInfo* rods, const int* vrod, lon
         const float invI = ES[e0 + i].y;
         om1 = vi.w + h * (-gth * invI - R.cd * vi.w);
         const float4 ed = ED[e0 + i];
-        V3<float> d1r = nh > 0 ? f3(NDR[e0 + i]) : zf3();
-        if (nh == 0) {
-            EdgeF<float> E;
-            edge_forward(E, xi, f3(X[v0 + ip]), f3(ET[e0 + i]), f3(ed), ed.w);
-            d1r = E.d1r;
+        if (brk) {
+            ED[e0 + i] = make_float4(ed.x, ed.y, ed.z, ed.w + h * om1);
+        } else {
+            const int ne = R.ne;
+            const bool solo = nh == 0 || (strands && (i == 0 || !(ES[e0 + i - 1].x > 0.f)) &&
+                                          (i + 1 >= ne || !(ES[e0 + i + 1].x > 0.f)));
+            V3<float> d1r = solo ? zf3() : f3(NDR[e0 + i]);
+            if (solo) {
+                EdgeF<float> E;
+                edge_forward(E, xi, f3(X[v0 + ip]), f3(ET[e0 + i]), f3(ed), ed.w);
+                d1r = E.d1r;
+            }
+            ED[e0 + i] = f4(d1r, ed.w + h * om1);
+            ET[e0 + i] = f4(t_i, ES[e0 + i].x);
         }
-        ED[e0 + i] = f4(d1r, ed.w + h * om1);
-        ET[e0 + i] = f4(t_i, ES[e0 + i].x);
     }
     TGT[gv] = tgt4;
     D[gv] = f4(d, xi4.w);
@@ -254,7 +277,7 @@ __global__ void pl_inext(const RodInfo* rods, const int* erod, long long Et, con
         target = ell > hi ? hi : lo;
     }
     const float ws = A.w + B.w;
-    if (!active || !(ws > 0.f)) {
+    if (!active || !(ws > 0.f) || !(eb > 0.f)) {   // eb = 0: the edge between two strands
         if (PBDout) PBDout[ge] = make_float4(0.f, 0.f, 0.f, 1.f);
         return;
     }
@@ -481,7 +504,8 @@ cudaError_t plain_frame(dlo_ctx* c, const PlainWs& w, const PlainState& S, const
     cudaError_t e = cudaSuccess;
     if (contact) {
         e = cudaMemsetAsync(w.npair, 0, 4 * (size_t)B, sm);
-        pl_broad<<<blocks(Et, T), T, 0, sm>>>(c->d_rods, w.erod, Et, S.X, w.poff, w.npair, w.pairs, c->d_status);
+        pl_broad<<<blocks(Et, T), T, 0, sm>>>(c->d_rods, w.erod, Et, c->d_es, S.X, w.poff, w.npair, w.pairs,
+                                              c->d_status);
         c->launches++;
     }
     for (int s = 0; s < nsub_max && e == cudaSuccess; ++s) {
@@ -972,6 +996,10 @@ __global__ void prb_b8(const RodInfo* rods, const int* erod, long long Et, const
     const int nv = R.nv, j = (int)(ge - R.e0);
     const long long a = R.v0 + j, b = R.v0 + ((j + 1 == nv) ? 0 : j + 1);
     const float4 ed = ED[ge], et = ET[ge];
+    if ((R.flags & ROD_STRANDS) && !(et.w > 0.f)) {   // a break edge kept its base frame: identity reverse
+        A.HBE[ge] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     EdgeF<float> E;
     edge_forward(E, f3(X0[a]), f3(X0[b]), f3(et), f3(ed), ed.w);
     V3<float> gtb, gd1b;
@@ -1017,6 +1045,7 @@ __global__ void prb_b7(const RodInfo* rods, const int* vrod, long long V, const 
     const long long ea = R.e0 + ((i == 0) ? ne - 1 : i - 1), eb = R.e0 + i;
     const long long im = R.v0 + ((i == 0) ? nv - 1 : i - 1), ip = R.v0 + ((i + 1 == nv) ? 0 : i + 1);
     const float4 EDa = ED[ea], EDb = ED[eb], ETa = ET[ea], ETb = ET[eb], hg = HG[gv];
+    if ((R.flags & ROD_STRANDS) && !(ETa.w > 0.f && ETb.w > 0.f)) return;   // at an end of a break edge
     const float lbar = 0.5f * (ETa.w + ETb.w), il = 1.f / lbar;
     HingeF<dualf> Hd;
     const float4 gm_ = A.LG[im], gi_ = A.LG[gv], gp_ = A.LG[ip];

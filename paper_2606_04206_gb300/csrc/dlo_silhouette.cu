@@ -191,8 +191,11 @@ extern "C" dlo_status dlo_loss_silhouette(dlo_ctx* c, const float* x, const floa
     if (n_cams < 1 || height < 1 || width < 1 || (long long)height * width > (1LL << 24))
         return set_err(c, DLO_ERR_INVALID_ARG, "need 1 or more cameras and 1..2^24 pixels per image");
     if (!(tau > 0.f)) return set_err(c, DLO_ERR_INVALID_ARG, "tau must be positive");
-    for (const auto& R : c->rods_h)
+    for (const auto& R : c->rods_h) {
         if (R.nv > kSilMaxV) return set_err(c, DLO_ERR_INVALID_ARG, "rod too long for the silhouette kernel");
+        if (R.flags & ROD_STRANDS)   // its edges are drawn as capsules; nothing joins two strands
+            return set_err(c, DLO_ERR_INVALID_ARG, "the silhouette loss needs rods without strands");
+    }
     const size_t need = (size_t)c->B * height * width * sizeof(float);
     if (need > c->sil_bytes) {
         dev_free(c, c->sil_mem);

@@ -243,17 +243,27 @@ struct Smem {
 // rejects almost all pairs before the exact closest-point distance, and the found pairs are
 // appended with one shared-memory atomic per warp.  Groups are whole warps and both loops
 // are uniform across the group, so the warp-wide ballot sees all 32 lanes.
+// Whether an edge strictly between edges a < b is a break edge (rest length 0): a and b then
+// lie on different strands, and the exclusion window does not apply to them.
+__device__ __forceinline__ bool break_between(const float4* ET, int a, int b) {
+    for (int k = a + 1; k < b; ++k)
+        if (!(ET[k].w > 0.f)) return true;
+    return false;
+}
+
 template <int NV, bool CONTACT, int TPR>
 __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, bool closed, bool& overflow) {
     static_assert(TPR % 32 == 0, "rod groups are whole warps");
-    float4* mid = s.HB0;                          // midpoint, half length of each edge
+    float4* mid = s.HB0;                          // midpoint, half length of each edge (-1: a break edge)
     int* cnt = reinterpret_cast<int*>(s.HB1);     // pairs found
     const int ne = R.ne, nv = R.nv;
+    const bool strands = R.flags & ROD_STRANDS;
     for (int j = g.tid; j < ne; j += TPR) {
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
         const V3<float> p0 = f3(s.X[j]), p1 = f3(s.X[j1]);
         const V3<float> e = p1 - p0;
-        mid[j] = f4(0.5f * (p0 + p1), 0.5f * sqrtf(dot(e, e)));
+        mid[j] = (strands && !(s.ET[j].w > 0.f)) ? make_float4(0.f, 0.f, 0.f, -1.f)
+                                                 : f4(0.5f * (p0 + p1), 0.5f * sqrtf(dot(e, e)));
     }
     if (g.tid == 0) *cnt = 0;
     g.sync();
@@ -262,18 +272,19 @@ __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR
     bool ovf = false;
     for (int a0 = 0; a0 < ne; a0 += TPR) {
         const int a = a0 + g.tid;
-        const bool va = a < ne;
-        const float4 ma = va ? mid[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ma = a < ne ? mid[a] : make_float4(0.f, 0.f, 0.f, -1.f);
+        const bool va = ma.w >= 0.f;
         const int a1 = (a + 1 == nv) ? 0 : a + 1;
         for (int b = 0; b < ne; ++b) {
             const float4 mb = mid[b];
             bool hit = false;
-            if (va && b > a) {
+            if (va && b > a && mb.w >= 0.f) {
                 const float dx = ma.x - mb.x, dy = ma.y - mb.y, dz = ma.z - mb.z;
                 const float rr = (cd + ma.w + mb.w) * 1.00001f;
                 int sep = b - a;
                 if (closed) sep = min(sep, ne - sep);
-                if (dx * dx + dy * dy + dz * dz < rr * rr && sep > R.excl) {
+                if (dx * dx + dy * dy + dz * dz < rr * rr &&
+                    (sep > R.excl || (strands && break_between(s.ET, a, b)))) {
                     const int b1 = (b + 1 == nv) ? 0 : b + 1;
                     const V3<float> pa0 = f3(s.X[a]), pa1 = f3(s.X[a1]), pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
                     float su, uu;
@@ -324,8 +335,11 @@ __device__ int broad_phase_hash(const RodInfo& R, Smem<NV, CONTACT>& s, const Gr
     int* cnt = keys + NV;            // TBL bucket counters, then the pair counter
     int* sorted = cnt + TBL + 1;
     const int ne = R.ne, nv = R.nv;
+    const bool strands = R.flags & ROD_STRANDS;
+    auto real = [&](int j) { return !strands || s.ET[j].w > 0.f; };   // break edges are no segments
     float lmax = 0.f;
     for (int j = g.tid; j < ne; j += TPR) {
+        if (!real(j)) continue;
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
         const V3<float> e = f3(s.X[j1]) - f3(s.X[j]);
         lmax = fmaxf(lmax, sqrtf(dot(e, e)));
@@ -335,6 +349,7 @@ __device__ int broad_phase_hash(const RodInfo& R, Smem<NV, CONTACT>& s, const Gr
     const float inv_cell = 1.f / (R.contact_d + lmax);
     const V3<float> org = f3(s.X[0]);
     for (int j = g.tid; j < ne; j += TPR) {
+        if (!real(j)) continue;
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
         const V3<float> m = 0.5f * (f3(s.X[j]) + f3(s.X[j1])) - org;
         const int ix = min(max(__float2int_rd(m.x * inv_cell), -510), 510) + 512;
@@ -362,6 +377,7 @@ __device__ int broad_phase_hash(const RodInfo& R, Smem<NV, CONTACT>& s, const Gr
     }
     g.sync();
     for (int j = g.tid; j < ne; j += TPR) {
+        if (!real(j)) continue;
         const int key = keys[j];
         const int pos = atomicAdd(&cnt[cell_hash(key >> 20, (key >> 10) & 1023, key & 1023, TBL - 1)], 1);
         sorted[pos] = j;
@@ -372,6 +388,7 @@ __device__ int broad_phase_hash(const RodInfo& R, Smem<NV, CONTACT>& s, const Gr
     const float cd = R.contact_d;
     bool ovf = false;
     for (int a = g.tid; a < ne; a += TPR) {
+        if (!real(a)) continue;
         const int key = keys[a];
         const int ix = key >> 20, iy = (key >> 10) & 1023, iz = key & 1023;
         const int a1 = (a + 1 == nv) ? 0 : a + 1;
@@ -388,7 +405,7 @@ __device__ int broad_phase_hash(const RodInfo& R, Smem<NV, CONTACT>& s, const Gr
                         if (b <= a || keys[b] != nk) continue;
                         int sep = b - a;
                         if (closed) sep = min(sep, ne - sep);
-                        if (sep <= R.excl) continue;
+                        if (sep <= R.excl && !(strands && break_between(s.ET, a, b))) continue;
                         const int b1 = (b + 1 == nv) ? 0 : b + 1;
                         const V3<float> pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
                         float su, uu;
@@ -450,7 +467,7 @@ __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* 
             target = ell > hi ? hi : lo;
         }
         float ws = A.w + B.w;
-        if (!active || !(ws > 0.f)) {
+        if (!active || !(ws > 0.f) || !(eb > 0.f)) {   // eb = 0: the edge between two strands
             if (prec) prec[j] = make_float4(0.f, 0.f, 0.f, 1.f);
             continue;
         }
@@ -563,6 +580,7 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
     const int nv = R.nv, ne = R.ne, v0 = R.v0, e0 = R.e0;
     const bool closed = R.flags & ROD_CLOSED;
     const int nh = closed ? nv : nv - 2;
+    const bool strands = R.flags & ROD_STRANDS;
     // --- hinge phase
     for (int k = g.tid; k < nh; k += TPR) {
         const int i = closed ? k : k + 1;
@@ -571,6 +589,10 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
         const int im = (i == 0) ? nv - 1 : i - 1;
         const int ip = (i + 1 == nv) ? 0 : i + 1;
         float4 EDa = s.ED[a], EDb = s.ED[b], ETa = s.ET[a], ETb = s.ET[b], hg = s.HG[i];
+        if (strands && !(ETa.w > 0.f && ETb.w > 0.f)) {   // a hinge at an end of a break edge
+            s.HB0[i] = s.HB1[i] = s.HB2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         HingeF<float> H;
         hinge_forward(H, f3(s.X0[im]), f3(s.X0[i]), f3(s.X0[ip]), f3(ETa), f3(EDa), f3(ETb), f3(EDb), EDa.w,
                       EDb.w, hg.w);
@@ -587,7 +609,8 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
         s.HB1[i] = f4(gxi, gtb);
         s.HB2[i] = f4(gxp, 0.f);
         s.ND[b] = f4(H.b.d1r, 0.f);
-        if (!closed && i == 1) s.ND[0] = f4(H.a.d1r, 0.f);
+        // the first edge of an open rod or strand gets its frame from its only hinge
+        if (!closed && (i == 1 || (strands && !(s.ET[a - 1].w > 0.f)))) s.ND[a] = f4(H.a.d1r, 0.f);
         s.HG[i] = make_float4(hg.x, hg.y, hg.z, H.mref);
     }
     g.sync();
@@ -614,7 +637,9 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
         if ((closed || i >= 2) && has_h(im)) g += f3(s.HB2[im]);
         V3<float> t_i = zf3();
         float ell_i = 0.f;
-        if (has_e) {
+        // a break edge (between two strands) starts here: no tangent, no force, frame kept
+        const bool brk = strands && has_e && !(ES[e0 + i].x > 0.f);
+        if (has_e && !brk) {
             V3<float> e = f3(s.X0[ip]) - xi;
             ell_i = sqrtf(dot(e, e));
             t_i = e / ell_i;
@@ -623,7 +648,7 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
                 g -= (R.kA * (ell_i / eb - 1.f)) * t_i;
             }
         }
-        if (R.kA > 0.f && (closed || i >= 1)) {
+        if (R.kA > 0.f && (closed || i >= 1) && !(strands && !(ES[e0 + im].x > 0.f))) {
             const int j = im;   // edge i-1 ends here
             V3<float> e = xi - f3(s.X0[j]);
             float ell = sqrtf(dot(e, e));
@@ -660,14 +685,22 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
             const float invI = ES[e0 + i].y;
             om1 = vi.w + h * (-gth * invI - R.cd * vi.w);
             float4 ed = s.ED[i];
-            V3<float> d1r = nh > 0 ? f3(s.ND[i]) : zf3();
-            if (nh == 0) {   // a single open edge has no hinge: transport its frame here
-                EdgeF<float> E;
-                edge_forward(E, xi, f3(s.X0[ip]), f3(s.ET[i]), f3(ed), ed.w);
-                d1r = E.d1r;
+            if (brk) {
+                s.ED[i] = make_float4(ed.x, ed.y, ed.z, ed.w + h * om1);
+            } else {
+                // an edge with no hinge (a single open edge, a strand of two vertices):
+                // transport its frame here
+                const bool solo = nh == 0 || (strands && (i == 0 || !(ES[e0 + i - 1].x > 0.f)) &&
+                                              (i + 1 >= ne || !(ES[e0 + i + 1].x > 0.f)));
+                V3<float> d1r = solo ? zf3() : f3(s.ND[i]);
+                if (solo) {
+                    EdgeF<float> E;
+                    edge_forward(E, xi, f3(s.X0[ip]), f3(s.ET[i]), f3(ed), ed.w);
+                    d1r = E.d1r;
+                }
+                s.ED[i] = f4(d1r, ed.w + h * om1);
+                s.ET[i] = f4(t_i, ES[e0 + i].x);
             }
-            s.ED[i] = f4(d1r, ed.w + h * om1);
-            s.ET[i] = f4(t_i, ES[e0 + i].x);
         }
         s.ND[i] = nd_out;
         s.X[i] = f4(d, xi4.w);

@@ -44,7 +44,7 @@ class Scene(C.Structure):
     _fields_ = [("n_planes", C.c_int), ("planes", C.POINTER(C.c_float)), ("n_boxes", C.c_int),
                 ("boxes", C.POINTER(C.c_float)), ("n_grippers", C.POINTER(C.c_int)),
                 ("grip_pose", C.POINTER(C.c_float)), ("grip_radius", C.c_float), ("grip_half_len", C.c_float),
-                ("pinned", C.POINTER(C.c_ubyte))]
+                ("pinned", C.POINTER(C.c_ubyte)), ("strand_start", C.POINTER(C.c_ubyte))]
 
 
 class Options(C.Structure):
@@ -175,11 +175,14 @@ class DloSim:
         pose[..., :3] = prob.grip_pos
         pose[..., 3:] = np.asarray(prob.grip_rot).reshape(B, 2, 9)
         pinned = np.ascontiguousarray(prob.pinned, np.uint8)
-        self._keep += [mats, nv, xr, planes, boxes, ng, pose, pinned]
+        st = getattr(prob, "strand_start", None)
+        starts = None if st is None or not np.any(st) else np.ascontiguousarray(st, np.uint8)
+        self._keep += [mats, nv, xr, planes, boxes, ng, pose, pinned, starts]
         scene = Scene(len(prob.planes), _fptr(planes) if len(planes) else None, len(prob.boxes),
                       _fptr(boxes) if len(boxes) else None, ng.ctypes.data_as(C.POINTER(C.c_int)),
                       _fptr(pose), prob.grip_radius, prob.grip_half_len,
-                      pinned.ctypes.data_as(C.POINTER(C.c_ubyte)))
+                      pinned.ctypes.data_as(C.POINTER(C.c_ubyte)),
+                      None if starts is None else starts.ctypes.data_as(C.POINTER(C.c_ubyte)))
         self.options = options_from(prob, **opt)
         alloc = None
         if allocator is not None:

@@ -473,8 +473,8 @@ def separation(n_envs: int = 4096, frames: int = 2000, seed: int = 6000, n: int 
     vertices each (Separation rows: inextensible, E = 5e3 Pa, G = 1e3 Pa), stored as one
     record of two strands, on the table.  Gripper 0 holds the first rope and gripper 1 the
     second, each at the vertex of its half where the ropes are furthest apart; they follow
-    smooth random 6-DoF trajectories plus a drift that pulls the ropes apart sideways (0.15 m
-    over the episode) and lifts them by 3 cm.  Self-contact on, which is what couples the
+    smooth random 6-DoF trajectories (3 cm, 0.1 rad) plus a drift that pulls the ropes apart
+    sideways (0.15 m over the episode) and lifts them by 3 cm.  Self-contact on, which is what couples the
     two ropes."""
     rng = np.random.default_rng(seed)
     recs, gp, gr, drift = [], np.zeros((n_envs, 2, 3)), np.tile(np.eye(3), (n_envs, 2, 1, 1)), []
@@ -492,7 +492,7 @@ def separation(n_envs: int = 4096, frames: int = 2000, seed: int = 6000, n: int 
         out[2] = 0.0
         out /= max(np.linalg.norm(out), 1e-9)
         drift.append(out)
-    acts = _smooth_actions(rng, frames, n_envs, 1e-3)
+    acts = _smooth_actions(rng, frames, n_envs, 1e-3, amp_pos=0.03, amp_rot=0.1)
     dirs = np.stack(drift)
     acts[:, :, 0, :3] += (0.15 / frames) * dirs[None]
     acts[:, :, 1, :3] -= (0.15 / frames) * dirs[None]
