@@ -681,7 +681,9 @@ __global__ void __launch_bounds__(kFwdMaxThreads) rec_kernel(BwdParams P) {
         const int k = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (k >= P.n_items) break;
         const int rod = P.order[P.item0 + k];
-        const RodInfo R = P.rods[rod];
+        // with self-contact read from memory where used: a register copy spills the
+        // contact variant of the kernel (its broad phase and sweeps) past the launch bound
+        RodRef<CONTACT> R = P.rods[rod];
         const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
         const float h = sc.dt / (float)nsub;
         const int seg = P.fa / P.ck_every, f0 = seg * P.ck_every;

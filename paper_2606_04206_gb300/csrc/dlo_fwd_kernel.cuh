@@ -39,7 +39,9 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
         const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (item >= P.n_order) break;
         const int rod = P.order[item];
-        const RodInfo R = P.rods[rod];
+        // with self-contact read from memory where used: a register copy spills the
+        // contact variant of the kernel (its broad phase and sweeps) past the launch bound
+        RodRef<CONTACT> R = P.rods[rod];
         const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
         const float h = P.scene.dt / (float)nsub;
         for (int i = g.tid; i < R.nv; i += TPR) {

@@ -12,11 +12,17 @@
 // Per frame: self-contact candidates (every edge pair behind a bounding-sphere filter),
 // gripper pose update.
 #pragma once
+#include <type_traits>
 #include "dlo_internal.h"
 #include "dlo_kernels.h"
 #include "dlo_physics.cuh"
 
 namespace dlo {
+
+// The per-rod constants as the persistent kernels hold them: a copy in registers, or (C) a
+// reference to the record in global memory, read where used.
+template <bool C>
+using RodRef = typename std::conditional<C, const RodInfo&, const RodInfo>::type;
 
 // A rod is stepped by a group of TPR threads (one or more whole warps); elements are spread
 // over the group with stride TPR and phases are separated by the group's barrier (the warp's
@@ -235,14 +241,6 @@ struct Smem {
 };
 
 // ------------------------------------------------------------------ broad phase
-// Candidates of one rod: the edge pairs outside the exclusion window whose segments are
-// closer than R.contact_d.  A rod has at most 256 edges, so every pair is tested: the edge
-// midpoints and half lengths sit in shared memory, every thread of the group walks all
-// edges in the same order (each read is one broadcast), a bounding-sphere test
-// (|m_a - m_b| < contact_d + h_a + h_b, implied by a segment distance below contact_d)
-// rejects almost all pairs before the exact closest-point distance, and the found pairs are
-// appended with one shared-memory atomic per warp.  Groups are whole warps and both loops
-// are uniform across the group, so the warp-wide ballot sees all 32 lanes.
 // Whether an edge strictly between edges a < b is a break edge (rest length 0): a and b then
 // lie on different strands, and the exclusion window does not apply to them.
 __device__ __forceinline__ bool break_between(const float4* ET, int a, int b) {
@@ -251,11 +249,28 @@ __device__ __forceinline__ bool break_between(const float4* ET, int a, int b) {
     return false;
 }
 
+constexpr int kBpBlock = 8;   // edges per block of the broad phase's first level
+
+// Candidates of one rod: the edge pairs outside the exclusion window whose segments are
+// closer than R.contact_d.  A rod has at most 256 edges, so every pair is considered, in two
+// levels of exact bounding-sphere tests before the closest-point distance:
+//   - each block of kBpBlock consecutive edges lies in the sphere around the centre of its
+//     vertices' bounding box, with the distance to its farthest vertex as radius;
+//   - each edge's segment lies in the sphere around its midpoint with its half length.
+// A segment distance below contact_d implies both sphere distances are below contact_d plus
+// the radii.  Level 1 tests every pair of blocks (one pair per thread) and lists the near
+// ones; level 2 spreads the edge pairs of the listed block pairs over the group, one edge
+// pair per thread, and runs the edge-sphere test, the exclusion window and the exact
+// distance.  Found pairs are appended with a shared-memory atomic (rare), so their order
+// varies; every use of the list (the Jacobi projection and friction, summed in fixed point,
+// the records of the backward's recompute, the pair-list query) is independent of it.
 template <int NV, bool CONTACT, int TPR>
 __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR>& g, bool closed, bool& overflow) {
-    static_assert(TPR % 32 == 0, "rod groups are whole warps");
     float4* mid = s.HB0;                          // midpoint, half length of each edge (-1: a break edge)
-    int* cnt = reinterpret_cast<int*>(s.HB1);     // pairs found
+    int* cnt = reinterpret_cast<int*>(s.HB1);     // [0] pairs found, [1] near block pairs
+    uint32_t* nearb = reinterpret_cast<uint32_t*>(s.HB1) + 4;   // near block pairs kA | kB << 16, kA <= kB
+    float4* blk = s.HB2;                          // centre, radius of each block of edges
+    static_assert((NV / kBpBlock + 1) * (NV / kBpBlock + 2) / 2 + 4 <= 4 * NV, "block pairs fit in HB1");
     const int ne = R.ne, nv = R.nv;
     const bool strands = R.flags & ROD_STRANDS;
     for (int j = g.tid; j < ne; j += TPR) {
@@ -265,53 +280,72 @@ __device__ int broad_phase(const RodInfo& R, Smem<NV, CONTACT>& s, const Grp<TPR
         mid[j] = (strands && !(s.ET[j].w > 0.f)) ? make_float4(0.f, 0.f, 0.f, -1.f)
                                                  : f4(0.5f * (p0 + p1), 0.5f * sqrtf(dot(e, e)));
     }
-    if (g.tid == 0) *cnt = 0;
-    g.sync();
-    const int cap = R.pair_cap, lane = threadIdx.x & 31;
-    const float cd = R.contact_d;
-    bool ovf = false;
-    for (int a0 = 0; a0 < ne; a0 += TPR) {
-        const int a = a0 + g.tid;
-        const float4 ma = a < ne ? mid[a] : make_float4(0.f, 0.f, 0.f, -1.f);
-        const bool va = ma.w >= 0.f;
-        const int a1 = (a + 1 == nv) ? 0 : a + 1;
-        for (int b = 0; b < ne; ++b) {
-            const float4 mb = mid[b];
-            bool hit = false;
-            if (va && b > a && mb.w >= 0.f) {
-                const float dx = ma.x - mb.x, dy = ma.y - mb.y, dz = ma.z - mb.z;
-                const float rr = (cd + ma.w + mb.w) * 1.00001f;
-                int sep = b - a;
-                if (closed) sep = min(sep, ne - sep);
-                if (dx * dx + dy * dy + dz * dz < rr * rr &&
-                    (sep > R.excl || (strands && break_between(s.ET, a, b)))) {
-                    const int b1 = (b + 1 == nv) ? 0 : b + 1;
-                    const V3<float> pa0 = f3(s.X[a]), pa1 = f3(s.X[a1]), pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
-                    float su, uu;
-                    closest_params(pa0, pa1, pb0, pb1, su, uu);
-                    const V3<float> dd = (pa0 + su * (pa1 - pa0)) - (pb0 + uu * (pb1 - pb0));
-                    hit = sqrtf(dot(dd, dd)) < cd;
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(cnt, __popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                if (hit) {
-                    const int idx = base + __popc(m & ((1u << lane) - 1u));
-                    if (idx < cap)
-                        s.pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
-                    else
-                        ovf = true;
-                }
-            }
+    const int nblk = (ne + kBpBlock - 1) / kBpBlock;
+    for (int k = g.tid; k < nblk; k += TPR) {
+        // the vertices of edges k*B .. min(ne, (k+1)*B) - 1 (a loop's last edge ends at vertex 0)
+        const int v0 = k * kBpBlock, v1 = min(ne, v0 + kBpBlock);
+        V3<float> lo = f3(s.X[v0]), hi = lo;
+        for (int v = v0 + 1; v <= v1; ++v) {
+            const V3<float> x = f3(s.X[v == nv ? 0 : v]);
+            lo = f3(fminf(lo.x, x.x), fminf(lo.y, x.y), fminf(lo.z, x.z));
+            hi = f3(fmaxf(hi.x, x.x), fmaxf(hi.y, x.y), fmaxf(hi.z, x.z));
         }
+        const V3<float> c = 0.5f * (lo + hi);
+        float r2 = 0.f;
+        for (int v = v0; v <= v1; ++v) {
+            const V3<float> d = f3(s.X[v == nv ? 0 : v]) - c;
+            r2 = fmaxf(r2, dot(d, d));
+        }
+        blk[k] = f4(c, sqrtf(r2));
+    }
+    if (g.tid == 0) {
+        cnt[0] = 0;
+        cnt[1] = 0;
+    }
+    g.sync();
+    const float cd = R.contact_d;
+    // level 1: pairs of blocks
+    for (int q = g.tid; q < nblk * nblk; q += TPR) {
+        const int ka = q / nblk, kb = q - ka * nblk;
+        if (kb < ka) continue;
+        const float4 A = blk[ka], B = blk[kb];
+        const float dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+        const float rr = (cd + A.w + B.w) * 1.0001f;
+        if (dx * dx + dy * dy + dz * dz < rr * rr) nearb[atomicAdd(&cnt[1], 1)] = (uint32_t)ka | ((uint32_t)kb << 16);
+    }
+    g.sync();
+    // level 2: the edge pairs of the near block pairs
+    const int nn = cnt[1], cap = R.pair_cap;
+    bool ovf = false;
+    constexpr int BB = kBpBlock * kBpBlock;
+    for (int t = g.tid; t < nn * BB; t += TPR) {
+        const uint32_t bp = nearb[t / BB];
+        const int a = (int)(bp & 0xffffu) * kBpBlock + (t % BB) / kBpBlock;
+        const int b = (int)(bp >> 16) * kBpBlock + t % kBpBlock;
+        if (b <= a || b >= ne) continue;
+        const float4 ma = mid[a], mb = mid[b];
+        if (!(ma.w >= 0.f && mb.w >= 0.f)) continue;
+        const float dx = ma.x - mb.x, dy = ma.y - mb.y, dz = ma.z - mb.z;
+        const float rr = (cd + ma.w + mb.w) * 1.00001f;
+        if (!(dx * dx + dy * dy + dz * dz < rr * rr)) continue;
+        int sep = b - a;
+        if (closed) sep = min(sep, ne - sep);
+        if (!(sep > R.excl || (strands && break_between(s.ET, a, b)))) continue;
+        const int a1 = (a + 1 == nv) ? 0 : a + 1, b1 = (b + 1 == nv) ? 0 : b + 1;
+        const V3<float> pa0 = f3(s.X[a]), pa1 = f3(s.X[a1]), pb0 = f3(s.X[b]), pb1 = f3(s.X[b1]);
+        float su, uu;
+        closest_params(pa0, pa1, pb0, pb1, su, uu);
+        const V3<float> dd = (pa0 + su * (pa1 - pa0)) - (pb0 + uu * (pb1 - pb0));
+        if (!(sqrtf(dot(dd, dd)) < cd)) continue;
+        const int idx = atomicAdd(&cnt[0], 1);
+        if (idx < cap)
+            s.pairs[idx] = (uint32_t)a | ((uint32_t)b << 16);
+        else
+            ovf = true;
     }
     g.sync();
     overflow = grp_any<TPR>(ovf, g);
-    const int np = *cnt;
+    const int np = cnt[0];
     g.sync();
     return min(np, cap);
 }
