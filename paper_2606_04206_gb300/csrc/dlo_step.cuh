@@ -606,6 +606,26 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
     g.sync();
 }
 
+// The contact sweep and friction as out-of-line calls.  They run only on frames with
+// candidates; kept out of the substep's inlined code they add no registers, and no code, to
+// the path every substep takes.  The rod's shared-memory view is rebuilt from its base
+// inside (a view passed by reference would be read from memory at every use).
+template <int NV, bool CONTACT, int TPR>
+__device__ __noinline__ void contact_sweep_call(const RodInfo* R, float4* base, int gtid, int gbar, int np,
+                                                bool first) {
+    Smem<NV, CONTACT> s(base);
+    const Grp<TPR> g{gtid, gbar, s.red};
+    contact_sweep<NV, CONTACT, TPR>(*R, s, g, np, first);
+}
+
+template <int NV, bool CONTACT, int TPR>
+__device__ __noinline__ void self_friction_call(const RodInfo* R, float4* base, int gtid, int gbar, int np,
+                                                float h, float mu) {
+    Smem<NV, CONTACT> s(base);
+    const Grp<TPR> g{gtid, gbar, s.red};
+    self_friction<NV, CONTACT, TPR>(*R, s, g, np, h, mu);
+}
+
 // ------------------------------------------------------------------ one substep
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
@@ -755,7 +775,7 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
                 // accumulators before its own barrier
                 if (rec)
                     for (int i = g.tid; i < nv; i += TPR) rec->csnap[(size_t)it * rec->nvmax + i] = s.X[i];
-                contact_sweep<NV, CONTACT, TPR>(R, s, g, np, it == 0);
+                contact_sweep_call<NV, CONTACT, TPR>(&R, s.X, g.tid, g.bar, np, it == 0);
             }
         }
     }
@@ -772,7 +792,7 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
             rec->fr0[p] = s.fr0[p];
             rec->fr1[p] = s.fr1[p];
         }
-    if (CONTACT && np > 0) self_friction<NV, CONTACT, TPR>(R, s, g, np, h, sc.mu_self);
+    if (CONTACT && np > 0) self_friction_call<NV, CONTACT, TPR>(&R, s.X, g.tid, g.bar, np, h, sc.mu_self);
     float dm2 = 0.f;   // the largest squared displacement of this thread's vertices
     for (int i = g.tid; i < nv; i += TPR) {
         float4 x0 = s.X0[i], d = s.X[i], nd = s.ND[i];
