@@ -52,7 +52,9 @@ typedef enum {
     DLO_ERR_NONFINITE = 4,     /* a rod's state became NaN/Inf; dlo_last_error names the rod */
     DLO_ERR_CAPACITY = 5,      /* self-contact pair list or checkpoint ring too small */
     DLO_ERR_TIMEOUT = 6,       /* reserved: no device-side wait exists in this library */
-    DLO_ERR_STATE = 7          /* call out of order, e.g. dlo_backward without a rollout */
+    DLO_ERR_STATE = 7,         /* call out of order, e.g. dlo_backward without a rollout */
+    DLO_ERR_BOUNDS = 8         /* debug builds only (-DDLO_DEBUG_BOUNDS): an index a kernel took
+                                  from data failed its bounds check; dlo_last_error names the rod */
 } dlo_status;
 
 /* Per-rod material (App. A.1 energies; App. B Table "sim_params" gives the task values). */
@@ -338,7 +340,8 @@ enum {
                                 state, 2 pair-list overflow (both errors), 4 a warning: some vertex
                                 moved, within one frame, at least half of the candidate margin
                                 (contact_margin x radius), so the candidates found at the frame's
-                                start may miss a pair that came into contact during it */
+                                start may miss a pair that came into contact during it; 8 (debug
+                                builds) an index failed its bounds check (an error) */
     DLO_Q_BYTES = 3,         /* size_t: device bytes held by the context */
     DLO_Q_CONFIG = 4,        /* int [4]: warps per CTA, checkpoint interval, CTAs, smem/CTA */
     DLO_Q_RESIDUAL = 5,      /* double [B]: sum |C_j| of the inextensibility constraints
@@ -366,6 +369,10 @@ dlo_status dlo_query(dlo_ctx* ctx, int what, void* out);
  * Synchronises the stream; allocates and frees a few bytes of device memory.
  * Errors: DLO_ERR_INVALID_ARG for a NULL result or seconds out of range; DLO_ERR_CUDA. */
 dlo_status dlo_measure_fp32_peak(double seconds, void* cuda_stream, double* tflops);
+
+/* How this library was built: bit 1 set when the kernels check every index they take from data
+ * (compiled with -DDLO_DEBUG_BOUNDS; a failed check gives DLO_ERR_BOUNDS).  No device work. */
+int dlo_build_flags(void);
 
 const char* dlo_status_string(dlo_status s);
 const char* dlo_last_error(const dlo_ctx* ctx);

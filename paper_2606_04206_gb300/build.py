@@ -2,6 +2,12 @@
 
 Each CUDA translation unit is compiled in parallel, then linked into
 ``paper_2606_04206_gb300/_lib/libdlo.so``.  No CMake, no torch extension machinery.
+
+``build(debug_bounds=True)`` builds the same sources with ``-DDLO_DEBUG_BOUNDS`` into
+``_lib_debug/libdlo.so``: every index the kernels take from data (candidate pairs, kinematic
+kinds, work-queue items, recorded pair counts) is checked before use, a failed check sets
+status bit 8 of its rod and skips the access, and the next synchronising call returns
+DLO_ERR_BOUNDS.
 """
 from __future__ import annotations
 
@@ -17,6 +23,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libdlo.so")
+LIBDIR_DEBUG = os.path.join(PKG, "_lib_debug")
+LIB_DEBUG = os.path.join(LIBDIR_DEBUG, "libdlo.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -45,18 +53,20 @@ def _newer(src_list, target):
     return any(os.path.getmtime(s) > t for s in deps)
 
 
-def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libdlo.so; returns its path."""
-    os.makedirs(LIBDIR, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False, debug_bounds: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libdlo.so (or the bounds-checking debug library);
+    returns its path."""
+    libdir, lib = (LIBDIR_DEBUG, LIB_DEBUG) if debug_bounds else (LIBDIR, LIB)
+    os.makedirs(libdir, exist_ok=True)
     srcs = sources()
-    if not force and not ptxas_info and not _newer(srcs, LIB):
-        return LIB
+    if not force and not ptxas_info and not _newer(srcs, lib):
+        return lib
     cc = nvcc()
     objs = []
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DDLO_DEBUG_BOUNDS"] if debug_bounds else [])
 
     def one(src):
-        obj = os.path.join(LIBDIR, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(libdir, os.path.basename(src).replace(".cu", ".o"))
         cmd = [cc, *flags(extra), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,11 +78,11 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
             objs.append(obj)
             if verbose or ptxas_info:
                 sys.stderr.write(log)
-    cmd = [cc, ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    cmd = [cc, ARCH, "-shared", "-o", lib, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -338,6 +338,7 @@ BwdParams backward_common(dlo_ctx* c, int force, const float* dL_dx_T, const flo
     P.gth0 = dL_dtheta0;
     P.gtb0 = gtb0;
     P.gd1b0 = gd1b0;
+    P.status = c->d_status;
     P.scene = c->scene;
     return P;
 }

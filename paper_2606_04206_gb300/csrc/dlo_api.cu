@@ -20,7 +20,8 @@ using namespace dlo;
 
 // ------------------------------------------------------------------ helpers
 static const char* kStatusNames[] = {"ok", "invalid argument", "CUDA error", "out of memory",
-                                     "non-finite state", "capacity exceeded", "timeout", "call out of order"};
+                                     "non-finite state", "capacity exceeded", "timeout", "call out of order",
+                                     "index out of bounds (debug build)"};
 
 dlo_status set_err(dlo_ctx* c, dlo_status s, const std::string& msg) {
     if (c) c->err = msg;
@@ -341,9 +342,17 @@ extern "C" void dlo_destroy(dlo_ctx* c) {
     delete c;
 }
 
+extern "C" int dlo_build_flags(void) {
+#ifdef DLO_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 extern "C" const char* dlo_status_string(dlo_status s) {
     int i = (int)s;
-    if (i < 0 || i > 7) return "unknown status";
+    if (i < 0 || i > 8) return "unknown status";
     return kStatusNames[i];
 }
 
@@ -414,6 +423,8 @@ dlo_status check_status(dlo_ctx* c) {
         if (s[b] & 1u) return set_err(c, DLO_ERR_NONFINITE, "rod " + std::to_string(b) + " has a non-finite state");
         if (s[b] & 2u)
             return set_err(c, DLO_ERR_CAPACITY, "rod " + std::to_string(b) + " overflowed its self-contact pair list");
+        if (s[b] & 8u)
+            return set_err(c, DLO_ERR_BOUNDS, "rod " + std::to_string(b) + ": an index failed a bounds check (debug build)");
     }
     return DLO_OK;
 }

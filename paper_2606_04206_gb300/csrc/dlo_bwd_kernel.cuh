@@ -236,7 +236,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         const float4 kin = P.KIN[v0 + i];
         const int kind = (int)kin.w;
         float4 lx = a.LX[i];
-        if (kind >= 2) {
+        if (kind >= 2 && in_bounds(kind - 2 < R.ngrip, s.red)) {
             const int q = kind - 2;
             V3<float> y1 = mul_rm(s.sp + 32 * q + 15, f3(kin));
             add3(pa.ps1, q, f3(lx));
@@ -259,6 +259,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             if (!(s.fr1[p].w > 0.f)) continue;
             uint32_t pr = s.pairs[p];
             const int a0 = pr & 0xffff, q0 = pr >> 16;
+            if (!in_bounds(a0 < nv && q0 < nv, s.red)) continue;
             const int idx[4] = {a0, (a0 + 1 == nv) ? 0 : a0 + 1, q0, (q0 + 1 == nv) ? 0 : q0 + 1};
             const V3<float> o = f3(s.X0[a0]);
             V3<float> Pf[4], Vf[4], lo[4];
@@ -326,6 +327,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                 for (int p = g.tid; p < np; p += TPR) {
                     uint32_t pr = s.pairs[p];
                     const int a0 = pr & 0xffff, q0 = pr >> 16;
+                    if (!in_bounds(a0 < nv && q0 < nv, s.red)) continue;
                     const int idx[4] = {a0, (a0 + 1 == nv) ? 0 : a0 + 1, q0, (q0 + 1 == nv) ? 0 : q0 + 1};
                     const V3<float> o = f3(s.X0[a0]);
                     V3<float> Pf[4], lo[4];
@@ -497,7 +499,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             lg = f4((-h * wi) * lam, 0.f);
             gm[4] += (double)(-h * dot(f3(vn), lam));
             a.LX[i] = f4(f3(a.LX[i]) + lx_acc, 0.f);
-        } else if (kind >= 2) {
+        } else if (kind >= 2 && in_bounds(kind - 2 < R.ngrip, s.red)) {
             // d = target(pose at the substep end) - x0
             const int q = kind - 2;
             add3(pa.ps1, q, ld0);
@@ -681,6 +683,12 @@ __global__ void __launch_bounds__(kFwdMaxThreads) rec_kernel(BwdParams P) {
         const int k = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (k >= P.n_items) break;
         const int rod = P.order[P.item0 + k];
+        bounds_begin<TPR>(g);
+        if (!in_bounds(rod >= 0 && rod < P.B && P.rods[rod].nv <= NV, s.red)) {
+            g.sync();
+            bounds_end<TPR>(g, P.status, (rod >= 0 && rod < P.B) ? rod : 0);
+            continue;
+        }
         // with self-contact read from memory where used: a register copy spills the
         // contact variant of the kernel (its broad phase and sweeps) past the launch bound
         RodRef<CONTACT> R = P.rods[rod];
@@ -757,6 +765,7 @@ __global__ void __launch_bounds__(kFwdMaxThreads) rec_kernel(BwdParams P) {
             }
         }
         g.sync();
+        bounds_end<TPR>(g, P.status, rod);
     }
 }
 
@@ -782,6 +791,12 @@ __global__ void __launch_bounds__(kBwdMaxThreads) rev_kernel(BwdParams P) {
         const int k = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (k >= P.n_items) break;
         const int rod = P.order[P.item0 + k];
+        bounds_begin<TPR>(g);
+        if (!in_bounds(rod >= 0 && rod < P.B && P.rods[rod].nv <= NV, s.red)) {
+            g.sync();
+            bounds_end<TPR>(g, P.status, (rod >= 0 && rod < P.B) ? rod : 0);
+            continue;
+        }
         const RodInfo R = P.rods[rod];
         const int nsub = P.force_nsub > 0 ? P.force_nsub : R.nsub;
         const float h = sc.dt / (float)nsub;
@@ -832,6 +847,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads) rev_kernel(BwdParams P) {
             int np = 0;
             if (CONTACT) {
                 np = reinterpret_cast<const int*>(fb)[24];
+                if (!in_bounds(np >= 0 && np <= R.pair_cap, s.red)) np = 0;
                 const uint32_t* pl = reinterpret_cast<const uint32_t*>(fb + kFrameHead);
                 for (int p = g.tid; p < np; p += TPR) s.pairs[p] = pl[p];
             }
@@ -936,6 +952,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads) rev_kernel(BwdParams P) {
             }
         }
         g.sync();
+        bounds_end<TPR>(g, P.status, rod);
     }
 }
 

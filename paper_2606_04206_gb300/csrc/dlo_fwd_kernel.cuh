@@ -39,6 +39,13 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
         const int item = grp_bcast0<TPR>(g.tid == 0 ? atomicAdd(P.counter, 1) : 0, g);
         if (item >= P.n_order) break;
         const int rod = P.order[item];
+        bounds_begin<TPR>(g);
+        if (!in_bounds(rod >= 0 && rod < P.B && P.rods[rod].nv <= NV &&
+                           P.rods[rod].v0 + P.rods[rod].nv <= P.nvert_total, s.red)) {
+            g.sync();
+            bounds_end<TPR>(g, P.status, (rod >= 0 && rod < P.B) ? rod : 0);
+            continue;
+        }
         // with self-contact read from memory where used: a register copy spills the
         // contact variant of the kernel (its broad phase and sweeps) past the launch bound
         RodRef<CONTACT> R = P.rods[rod];
@@ -114,6 +121,7 @@ __global__ void __launch_bounds__(kFwdMaxThreads) fwd_kernel(FwdParams P) {
         write_state<TPR>(P.S, 0, 0, 0, R, rod, g, s.X, s.V, s.ED, s.ET, s.HG, s.fp);
         if (g.tid == 0 && bad) atomicOr(&P.status[rod], bad);
         g.sync();
+        bounds_end<TPR>(g, P.status, rod);
     }
 }
 

@@ -112,6 +112,7 @@ struct BwdParams {
     float* gth0;              // [Etot] or null
     float4* gtb0;             // [Etot] cotangent of the initial base tangents
     float4* gd1b0;            // [Etot] cotangent of the initial base d1
+    unsigned* status;         // [B] status bits (debug builds: bit 8, a failed bounds check)
     SceneDev scene;
 };
 

@@ -290,9 +290,26 @@ __global__ void pl_inext(const RodInfo* rods, const int* erod, long long Et, con
 }
 
 // one Jacobi sweep of the self-collision projection (one thread per pair slot)
+// Debug builds (-DDLO_DEBUG_BOUNDS): a pair index outside its rod sets status bit 8 of the rod
+// and the pair is skipped.  Release builds compile the check away.
+__device__ __forceinline__ bool pair_ok(int a0, int c0, int nv, unsigned* status, int b) {
+#ifdef DLO_DEBUG_BOUNDS
+    if (a0 < nv && c0 < nv) return true;
+    atomicOr(&status[b], kStatusBounds);
+    return false;
+#else
+    (void)a0;
+    (void)c0;
+    (void)nv;
+    (void)status;
+    (void)b;
+    return true;
+#endif
+}
+
 __global__ void pl_contact(const RodInfo* rods, const int* prod, long long P, const int* poff, const int* npair,
                            const uint32_t* pairs, const float4* X, const float4* D, int4* ACC, float4* FR0,
-                           float4* FR1, int first, int s, int force) {
+                           float4* FR1, int first, int s, int force, unsigned* status) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int b = prod[p];
@@ -301,6 +318,7 @@ __global__ void pl_contact(const RodInfo* rods, const int* prod, long long P, co
     const int nv = R.nv, v0 = R.v0;
     const uint32_t pr = pairs[p];
     const int a0 = pr & 0xffff, c0 = pr >> 16;
+    if (!pair_ok(a0, c0, R.nv, status, b)) return;
     const int a1 = (a0 + 1 == nv) ? 0 : a0 + 1, c1 = (c0 + 1 == nv) ? 0 : c0 + 1;
     const V3<float> o = f3(X[v0 + a0]);
     const float4 A0 = D[v0 + a0], A1 = D[v0 + a1], C0 = D[v0 + c0], C1 = D[v0 + c1];
@@ -354,7 +372,7 @@ __global__ void pl_velocity(SceneDev sc, const RodInfo* rods, const int* vrod, l
 // self-contact friction from the first iteration's contact set (one thread per pair slot)
 __global__ void pl_friction(SceneDev sc, const RodInfo* rods, const int* prod, long long P, const int* poff,
                             const int* npair, const uint32_t* pairs, const float4* X, const float4* Vl,
-                            const float4* FR0, const float4* FR1, int4* ACC, int s, int force) {
+                            const float4* FR0, const float4* FR1, int4* ACC, int s, int force, unsigned* status) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int b = prod[p];
@@ -368,6 +386,7 @@ __global__ void pl_friction(SceneDev sc, const RodInfo* rods, const int* prod, l
     const int nv = R.nv, v0 = R.v0;
     const uint32_t pr = pairs[p];
     const int a0 = pr & 0xffff, c0 = pr >> 16;
+    if (!pair_ok(a0, c0, R.nv, status, b)) return;
     const int a1 = (a0 + 1 == nv) ? 0 : a0 + 1, c1 = (c0 + 1 == nv) ? 0 : c0 + 1;
     const float su = F1.x, uu = F1.y, W = F1.z;
     const V3<float> nn = f3(F0);
@@ -534,7 +553,8 @@ cudaError_t plain_frame(dlo_ctx* c, const PlainWs& w, const PlainState& S, const
                                         cudaMemcpyDeviceToDevice, sm);
                 pl_contact<<<blocks(P, T), T, 0, sm>>>(c->d_rods, w.prod, P, w.poff, w.npair, w.pairs, S.X, w.D, w.ACC,
                                                        rec ? rec->FR0 + s * rec->sP : w.FR0,
-                                                       rec ? rec->FR1 + s * rec->sP : w.FR1, it == 0, s, substeps);
+                                                       rec ? rec->FR1 + s * rec->sP : w.FR1, it == 0, s, substeps,
+                                                       c->d_status);
                 pl_apply<<<blocks(V, T), T, 0, sm>>>(V, w.ACC, w.D, kFixPos);
                 c->launches += 2;
             }
@@ -545,7 +565,8 @@ cudaError_t plain_frame(dlo_ctx* c, const PlainWs& w, const PlainState& S, const
         if (contact) {
             pl_friction<<<blocks(P, T), T, 0, sm>>>(c->scene, c->d_rods, w.prod, P, w.poff, w.npair, w.pairs, S.X,
                                                     S.Vl, rec ? rec->FR0 + s * rec->sP : w.FR0,
-                                                    rec ? rec->FR1 + s * rec->sP : w.FR1, w.ACC, s, substeps);
+                                                    rec ? rec->FR1 + s * rec->sP : w.FR1, w.ACC, s, substeps,
+                                                    c->d_status);
             pl_apply<<<blocks(V, T), T, 0, sm>>>(V, w.ACC, S.Vl, kFixVel);
             c->launches += 2;
         }
@@ -669,7 +690,7 @@ __global__ void prb_b1(const RodInfo* rods, const int* vrod, long long V, const 
 // B2: self-contact friction (per pair slot), into LP0 (positions) and LTMP (velocities)
 __global__ void prb_b2(SceneDev sc, const RodInfo* rods, const int* prod, long long P, const int* poff,
                        const int* npair, const uint32_t* pairs, const float4* X0, const float4* T0, const float4* DF,
-                       const float4* FR1, int s, int force, PlainAdj A) {
+                       const float4* FR1, int s, int force, PlainAdj A, unsigned* status) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int b = prod[p];
@@ -681,6 +702,7 @@ __global__ void prb_b2(SceneDev sc, const RodInfo* rods, const int* prod, long l
     const int nv = R.nv, v0 = R.v0;
     const uint32_t pr = pairs[p];
     const int a0 = pr & 0xffff, q0 = pr >> 16;
+    if (!pair_ok(a0, q0, R.nv, status, b)) return;
     const int idx[4] = {v0 + a0, v0 + ((a0 + 1 == nv) ? 0 : a0 + 1), v0 + q0, v0 + ((q0 + 1 == nv) ? 0 : q0 + 1)};
     const V3<float> o = f3(X0[idx[0]]);
     V3<float> Pf[4], Vf[4], lo[4];
@@ -734,7 +756,8 @@ __global__ void prb_b3(SceneDev sc, const RodInfo* rods, const int* vrod, long l
 
 // B4, contact sweep of iteration it (per pair slot), into LTMP
 __global__ void prb_b4c(const RodInfo* rods, const int* prod, long long P, const int* poff, const int* npair,
-                        const uint32_t* pairs, const float4* X0, const float4* Dc, int s, int force, PlainAdj A) {
+                        const uint32_t* pairs, const float4* X0, const float4* Dc, int s, int force, PlainAdj A,
+                        unsigned* status) {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int b = prod[p];
@@ -743,6 +766,7 @@ __global__ void prb_b4c(const RodInfo* rods, const int* prod, long long P, const
     const int nv = R.nv, v0 = R.v0;
     const uint32_t pr = pairs[p];
     const int a0 = pr & 0xffff, q0 = pr >> 16;
+    if (!pair_ok(a0, q0, R.nv, status, b)) return;
     const int idx[4] = {v0 + a0, v0 + ((a0 + 1 == nv) ? 0 : a0 + 1), v0 + q0, v0 + ((q0 + 1 == nv) ? 0 : q0 + 1)};
     const V3<float> o = f3(X0[idx[0]]);
     V3<float> Pf[4], lo[4];
@@ -1318,7 +1342,7 @@ extern "C" dlo_status dlo_backward_plain(dlo_ctx* c, const float* dL_dx_T, const
                 e = cudaMemsetAsync(A.LP0, 0, 16 * nV, sm);
                 if (e == cudaSuccess) e = cudaMemsetAsync(A.LTMP, 0, 16 * nV, sm);
                 prb_b2<<<blocks(P, T), T, 0, sm>>>(c->scene, c->d_rods, w.prod, P, w.poff, w.npair, w.pairs, X0, CSN, DF,
-                                                   FR1, s, force, A);
+                                                   FR1, s, force, A, c->d_status);
                 c->launches++;
             }
             prb_b3<<<blocks(V, T), T, 0, sm>>>(c->scene, c->d_rods, w.vrod, V, s, force, contact ? 1 : 0, A);
@@ -1327,7 +1351,7 @@ extern "C" dlo_status dlo_backward_plain(dlo_ctx* c, const float* dL_dx_T, const
                 if (contact) {
                     e = cudaMemsetAsync(A.LTMP, 0, 16 * nV, sm);
                     prb_b4c<<<blocks(P, T), T, 0, sm>>>(c->d_rods, w.prod, P, w.poff, w.npair, w.pairs, X0,
-                                                        CSN + (size_t)it * nV, s, force, A);
+                                                        CSN + (size_t)it * nV, s, force, A, c->d_status);
                     prb_b4a<<<blocks(V, T), T, 0, sm>>>(c->d_rods, w.vrod, V, s, force, it == 0 ? 1 : 0, A);
                     c->launches += 2;
                 }

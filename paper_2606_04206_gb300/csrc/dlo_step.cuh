@@ -105,6 +105,49 @@ __device__ __forceinline__ float grp_max_nonneg(float v, const Grp<TPR>& g) {
     return __uint_as_float(m);
 }
 
+// Status bit of a failed bounds check.  Debug builds (-DDLO_DEBUG_BOUNDS) check every index
+// the kernels take from data (candidate pairs, kinematic kinds, recorded pair counts, work-
+// queue items) before using it: a failed check sets the bit in the rod's flag word (slot 40
+// of its reduction scratch, folded into the rod's status when its work ends) and the access
+// is skipped.  Release builds compile the checks away.
+constexpr unsigned kStatusBounds = 8u;
+
+__device__ __forceinline__ bool in_bounds(bool ok, float* red) {
+#ifdef DLO_DEBUG_BOUNDS
+    if (!ok) atomicOr(reinterpret_cast<unsigned*>(red) + 40, kStatusBounds);
+    return ok;
+#else
+    (void)ok;
+    (void)red;
+    return true;
+#endif
+}
+
+// Start of a rod's work: clear its flag word (debug builds).
+template <int TPR>
+__device__ __forceinline__ void bounds_begin(const Grp<TPR>& g) {
+#ifdef DLO_DEBUG_BOUNDS
+    if (g.tid == 0) reinterpret_cast<unsigned*>(g.red)[40] = 0u;
+#else
+    (void)g;
+#endif
+}
+
+// End of a rod's work, after a group barrier: fold its flag word into status[rod].
+template <int TPR>
+__device__ __forceinline__ void bounds_end(const Grp<TPR>& g, unsigned* status, int rod) {
+#ifdef DLO_DEBUG_BOUNDS
+    if (g.tid == 0 && status) {
+        const unsigned f = reinterpret_cast<unsigned*>(g.red)[40];
+        if (f) atomicOr(&status[rod], f);
+    }
+#else
+    (void)g;
+    (void)status;
+    (void)rod;
+#endif
+}
+
 // Value held by thread 0 of the group.
 template <int TPR>
 __device__ __forceinline__ int grp_bcast0(int v, const Grp<TPR>& g) {
@@ -529,6 +572,7 @@ __device__ __forceinline__ void contact_sweep(const RodInfo& R, Smem<NV, CONTACT
     for (int p = g.tid; p < np; p += TPR) {
         uint32_t pr = s.pairs[p];
         int a0 = pr & 0xffff, c0 = pr >> 16;
+        if (!in_bounds(a0 < nv && c0 < nv && p < R.pair_cap, s.red)) continue;
         int a1 = (a0 + 1 == nv) ? 0 : a0 + 1, c1 = (c0 + 1 == nv) ? 0 : c0 + 1;
         // current positions in coordinates local to the start position of vertex a0
         const V3<float> o = f3(s.X0[a0]);
@@ -575,6 +619,7 @@ __device__ __forceinline__ void self_friction(const RodInfo& R, Smem<NV, CONTACT
         float4 F0 = s.fr0[p];
         uint32_t pr = s.pairs[p];
         int a0 = pr & 0xffff, c0 = pr >> 16;
+        if (!in_bounds(a0 < nv && c0 < nv && p < R.pair_cap, s.red)) continue;
         int a1 = (a0 + 1 == nv) ? 0 : a0 + 1, c1 = (c0 + 1 == nv) ? 0 : c0 + 1;
         float su = F1.x, uu = F1.y, W = F1.z;
         V3<float> n = f3(F0);
@@ -723,7 +768,7 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
             if (rec) rec->v1[i] = f4(v1, 0.f);
             v2 = rigid_contact(sc, R, xi, v1, s.sp, imp ? imp + 4 * i : nullptr, 1.f / xi4.w);
             d = h * v2;
-        } else if (kind >= 2) {
+        } else if (kind >= 2 && in_bounds(kind - 2 < R.ngrip, s.red)) {
             const float* o = s.sp + 32 * (kind - 2);
             const V3<float> off = f3(kin);
             const V3<float> p1 = f3(o[3], o[4], o[5]);

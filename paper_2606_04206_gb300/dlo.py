@@ -15,13 +15,14 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libdlo.so")
+LIB_DEBUG_PATH = os.path.join(_PKG, "_lib_debug", "libdlo.so")   # build(debug_bounds=True)
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "dlo.h")
 
 STATUS = {0: "DLO_OK", 1: "DLO_ERR_INVALID_ARG", 2: "DLO_ERR_CUDA", 3: "DLO_ERR_OOM", 4: "DLO_ERR_NONFINITE",
           5: "DLO_ERR_CAPACITY", 6: "DLO_ERR_TIMEOUT", 7: "DLO_ERR_STATE"}
 Q_SUBSTEPS, Q_STATUS, Q_BYTES, Q_CONFIG, Q_RESIDUAL, Q_PAIRS, Q_LAUNCHES, Q_MASS, Q_PAIR_LIST = range(1, 10)
 PAIR_LIST_STRIDE = 1024   # candidates per rod row of Q_PAIR_LIST (4 per vertex of 256 vertices)
-STATUS_NONFINITE, STATUS_PAIR_OVERFLOW, STATUS_MOVED_PAST_MARGIN = 1, 2, 4
+STATUS_NONFINITE, STATUS_PAIR_OVERFLOW, STATUS_MOVED_PAST_MARGIN, STATUS_BOUNDS = 1, 2, 4, 8
 MATERIAL_KEYS = ("K", "E", "G", "yield_curv", "damping")
 LOSS_TARGET, LOSS_CHAMFER, LOSS_WINDING, LOSS_CROSSING, LOSS_MINDIST, LOSS_REPULSION = range(1, 7)
 N_MAT_GRAD = 5      # K_stretch, E_bend, G_twist, yield_curv, damping
@@ -63,15 +64,14 @@ class Allocator(C.Structure):
     _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
 
 
-_lib = None
+_libs = {}
 
 
 def load(path: str | None = None):
     """Load libdlo.so (built by ``paper_2606_04206_gb300.build``); raises if it is missing."""
-    global _lib
-    if _lib is not None:
-        return _lib
     p = path or LIB_PATH
+    if p in _libs:
+        return _libs[p]
     if not os.path.exists(p):
         raise RuntimeError(f"libdlo.so not found at {p}: run paper_2606_04206_gb300.build.build() first")
     lib = C.CDLL(p)
@@ -79,6 +79,8 @@ def load(path: str | None = None):
     lib.dlo_create.argtypes = [C.POINTER(vp), ip, C.POINTER(C.c_int), C.POINTER(Material), fp, C.POINTER(Scene),
                                C.POINTER(Options), C.POINTER(Allocator), vp]
     lib.dlo_create.restype = st
+    lib.dlo_build_flags.argtypes = []
+    lib.dlo_build_flags.restype = C.c_int
     lib.dlo_set_material.argtypes = [vp, C.POINTER(Material)]
     lib.dlo_set_material.restype = st
     lib.dlo_set_state.argtypes = [vp, vp, vp, vp]
@@ -115,7 +117,7 @@ def load(path: str | None = None):
     lib.dlo_last_error.restype = C.c_char_p
     lib.dlo_destroy.argtypes = [vp]
     lib.dlo_destroy.restype = None
-    _lib = lib
+    _libs[p] = lib
     return lib
 
 
@@ -151,10 +153,10 @@ class DloSim:
     callables (alloc(nbytes) -> device address or None, free(address)) handed to the
     library as its dlo_allocator."""
 
-    def __init__(self, prob, torch_alloc: bool = True, allocator=None, **opt):
+    def __init__(self, prob, torch_alloc: bool = True, allocator=None, debug_bounds: bool = False, **opt):
         import torch
         self.torch = torch
-        self.lib = load()
+        self.lib = load(LIB_DEBUG_PATH if debug_bounds else None)
         self.p = prob
         self.B = prob.batch
         self.V = int(prob.vert_off[-1])

@@ -24,7 +24,9 @@ def test_every_declared_function_is_exported(lib):
 def test_status_strings(lib):
     assert lib.dlo_status_string(0) == b"ok"
     assert lib.dlo_status_string(1) == b"invalid argument"
+    assert lib.dlo_status_string(8) == b"index out of bounds (debug build)"
     assert lib.dlo_status_string(99) == b"unknown status"
+    assert lib.dlo_build_flags() == 0          # the release library has no bounds checks
     assert lib.dlo_last_error(None) == b"null context"
 
 
