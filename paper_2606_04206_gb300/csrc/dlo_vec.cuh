@@ -25,9 +25,19 @@ DLO_HD float dof(dualf a) { return a.d; }
 DLO_HD dualf operator+(dualf a, dualf b) { return {a.v + b.v, a.d + b.d}; }
 DLO_HD dualf operator-(dualf a, dualf b) { return {a.v - b.v, a.d - b.d}; }
 DLO_HD dualf operator*(dualf a, dualf b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+// Quotient of a derivative part.  The value parts keep IEEE division, so that a dual
+// evaluation's values (and the branches taken on them) are those of the float evaluation;
+// a derivative tolerates the fast quotient's 2 ulp and then needs no IEEE slow path.
+DLO_HD float ddiv(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
 DLO_HD dualf operator/(dualf a, dualf b) {
     float q = a.v / b.v;
-    return {q, (a.d - q * b.d) / b.v};
+    return {q, ddiv(a.d - q * b.d, b.v)};
 }
 DLO_HD dualf operator-(dualf a) { return {-a.v, -a.d}; }
 DLO_HD dualf operator+(dualf a, float b) { return {a.v + b, a.d}; }
@@ -36,10 +46,10 @@ DLO_HD dualf operator-(dualf a, float b) { return {a.v - b, a.d}; }
 DLO_HD dualf operator-(float a, dualf b) { return {a - b.v, -b.d}; }
 DLO_HD dualf operator*(dualf a, float b) { return {a.v * b, a.d * b}; }
 DLO_HD dualf operator*(float a, dualf b) { return {a * b.v, a * b.d}; }
-DLO_HD dualf operator/(dualf a, float b) { return {a.v / b, a.d / b}; }
+DLO_HD dualf operator/(dualf a, float b) { return {a.v / b, ddiv(a.d, b)}; }
 DLO_HD dualf operator/(float a, dualf b) {
     float q = a / b.v;
-    return {q, -q * b.d / b.v};
+    return {q, -ddiv(q * b.d, b.v)};
 }
 DLO_HD dualf& operator+=(dualf& a, dualf b) { a = a + b; return a; }
 DLO_HD dualf& operator-=(dualf& a, dualf b) { a = a - b; return a; }
@@ -48,7 +58,7 @@ DLO_HD dualf& operator*=(dualf& a, dualf b) { a = a * b; return a; }
 DLO_HD float dsqrt(float a) { return sqrtf(a); }
 DLO_HD dualf dsqrt(dualf a) {
     float s = sqrtf(a.v);
-    return {s, s > 0.f ? 0.5f * a.d / s : 0.f};
+    return {s, s > 0.f ? ddiv(0.5f * a.d, s) : 0.f};
 }
 DLO_HD float dsin(float a) { return sinf(a); }
 DLO_HD float dcos(float a) { return cosf(a); }
@@ -62,7 +72,7 @@ DLO_HD dualf dexp(dualf a) {
 DLO_HD float datan2(float y, float x) { return atan2f(y, x); }
 DLO_HD dualf datan2(dualf y, dualf x) {
     float r2 = x.v * x.v + y.v * y.v;
-    return {atan2f(y.v, x.v), (x.v * y.d - y.v * x.d) / r2};
+    return {atan2f(y.v, x.v), ddiv(x.v * y.d - y.v * x.d, r2)};
 }
 template <class T> DLO_HD T cst(float a);
 template <> DLO_HD float cst<float>(float a) { return a; }
@@ -98,7 +108,11 @@ template <class T> DLO_HD V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a
 template <class T> DLO_HD V3<T> operator*(V3<T> a, T s) { return {s * a.x, s * a.y, s * a.z}; }
 DLO_HD V3<dualf> operator*(float s, V3<dualf> a) { return {s * a.x, s * a.y, s * a.z}; }
 DLO_HD V3<dualf> operator*(dualf s, V3<float> a) { return {s * a.x, s * a.y, s * a.z}; }
-template <class T> DLO_HD V3<T> operator/(V3<T> a, T s) { return {a.x / s, a.y / s, a.z / s}; }
+// one reciprocal and three products (float and dual alike, so their values agree)
+template <class T> DLO_HD V3<T> operator/(V3<T> a, T s) {
+    const T r = 1.f / s;
+    return {a.x * r, a.y * r, a.z * r};
+}
 template <class T> DLO_HD V3<T>& operator+=(V3<T>& a, V3<T> b) { a = a + b; return a; }
 template <class T> DLO_HD V3<T>& operator-=(V3<T>& a, V3<T> b) { a = a - b; return a; }
 template <class T> DLO_HD T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }

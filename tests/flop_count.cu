@@ -80,6 +80,10 @@ inline DC datan2(DC y, DC x) {
     return {datan2(y.v, x.v), (x.v * y.d - y.v * x.d) / r2};
 }
 template <> inline DC cst<DC>(float a) { return {{a}, {0.f}}; }
+// a vector over a scalar is three quotients, however the kernels form them (one reciprocal
+// and three products)
+inline V3<CountF> operator/(V3<CountF> a, CountF s) { return {a.x / s, a.y / s, a.z / s}; }
+inline V3<DC> operator/(V3<DC> a, DC s) { return {a.x / s, a.y / s, a.z / s}; }
 }  // namespace dlo
 
 #include "dlo_physics.cuh"
