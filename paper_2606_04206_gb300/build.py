@@ -35,9 +35,16 @@ def nvcc() -> str:
     return p
 
 
+# Single-precision division and square root as the hardware's approximations (at most 2 ulp),
+# without the IEEE-rounded versions' correction steps and slow-path branches; the elastic
+# and contact kernels take several dozen of each per vertex and substep.  The transcendental
+# functions keep their accurate versions.
+FAST_DIV_SQRT = ["-prec-div=false", "-prec-sqrt=false"]
+
+
 def flags(extra=()):
     return [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-            "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
+            *FAST_DIV_SQRT, "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
 
 def sources():
