@@ -23,7 +23,10 @@
 
 namespace dlo {
 
-constexpr int kBwdMaxThreads = 256;   // per CTA (register budget of the backward kernel)
+// Threads per CTA the reverse kernel is compiled for (its register budget).  Rods of up to 128
+// vertices take at most 62.5 KB of shared memory each, so three fit an SM: 384 threads at 168
+// registers.  Larger rods fit two per SM (one at 256 vertices), and keep 255 registers.
+__host__ __device__ constexpr int rev_max_threads(int NV) { return NV <= 128 ? 384 : 256; }
 
 __host__ __device__ constexpr size_t bwd_smem_bytes(int NV, bool contact) {
     return rod_smem_bytes(NV, contact) + (size_t)(10 * NV + 20) * 16;
@@ -230,6 +233,9 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
     const float rsum = 2.f * R.radius;
     PoseAdj pa;
     pa.zero();
+    // this substep's material terms, in registers (gm is the caller's memory), added to gm at
+    // the end
+    double gl[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = g.tid; i < nv; i += TPR) a.LP0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     // ---- B1: positions at the substep end
     for (int i = g.tid; i < nv; i += TPR) {
@@ -497,7 +503,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float wi = x4.w;
             lvn = f4((1.f - h * R.cd) * lam, 0.f);
             lg = f4((-h * wi) * lam, 0.f);
-            gm[4] += (double)(-h * dot(f3(vn), lam));
+            gl[4] += (double)(-h * dot(f3(vn), lam));
             a.LX[i] = f4(f3(a.LX[i]) + lx_acc, 0.f);
         } else if (kind >= 2 && in_bounds(kind - 2 < R.ngrip, s.red)) {
             // d = target(pose at the substep end) - x0
@@ -512,7 +518,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float invI = P.ES[e0 + i].y;
             lvn.w = (1.f - h * R.cd) * lw1;
             lg.w = -h * invI * lw1;
-            gm[4] += (double)(-h * vn.w * lw1);
+            gl[4] += (double)(-h * vn.w * lw1);
         }
         a.LV[i] = lvn;
         a.LG[i] = lg;
@@ -566,7 +572,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float eb = P.ES[e0 + j].x;
             const float tl = dot(E.t, les);
             le += R.kA * ((tl / eb) * E.t + (E.ell / eb - 1.f) / E.ell * (les - tl * E.t));
-            gm[0] += (double)((E.ell / eb - 1.f) * tl);
+            gl[0] += (double)((E.ell / eb - 1.f) * tl);
         }
         s.HB1[j] = f4(le, 0.f);
         a.LT[j] = f4(gtb, 0.f);
@@ -601,8 +607,8 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         dualf e0d = Hd.k0 - kb0, e1d = Hd.k1 - kb1, emd = Hd.m - hg.z;
         dualf gk0 = (R.Bm * il) * e0d, gk1 = (R.Bm * il) * e1d, gmt = (R.beta * il) * emd;
         // each term in float, added to the FP64 sums (the cancellation is across terms)
-        gm[1] += (double)(il * (e0d.v * e0d.d + e1d.v * e1d.d));
-        gm[2] += (double)(il * emd.v * emd.d);
+        gl[1] += (double)(il * (e0d.v * e0d.d + e1d.v * e1d.d));
+        gl[2] += (double)(il * emd.v * emd.d);
         // rest curvature: cotangent of the one used (-d gk / d .) plus the carried one
         float lk0 = a.LK[i].x - gk0.d, lk1 = a.LK[i].y - gk1.d;
         if (yielded) {
@@ -611,7 +617,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const float g = R.rc * (n - thr) / n;
             const float kk = R.rc * thr / (n * n * n) * (el0 * lk0 + el1 * lk1);
             const float le0 = g * lk0 + kk * el0, le1 = g * lk1 + kk * el1;     // cotangent of kappa_el
-            gm[3] += (double)(-R.rc * lbar * (el0 * lk0 + el1 * lk1) / n);
+            gl[3] += (double)(-R.rc * lbar * (el0 * lk0 + el1 * lk1) / n);
             // The first-order reverse of kappa from seeds (le0, le1) is needed too.  The hinge
             // reverse is linear in its seeds, so adding them to the derivative part of the
             // dual seeds makes the reverse below return J^T le on top of the Hessian term.
@@ -635,6 +641,8 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         atomic_add3(&a.LE[eb], ders(gd1bb));
         a.LK[i] = make_float4(lk0, lk1, 0.f, 0.f);
     }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) gm[c] += gl[c];
     g.sync();
 }
 
@@ -776,7 +784,7 @@ __global__ void __launch_bounds__(kFwdMaxThreads) rec_kernel(BwdParams P) {
 // state) on the first chunk (fb = F), else from the previous chunk's launch (CS); those at fa
 // go to CS, or to the outputs on the last chunk (fa = 0).
 template <int NV, bool CONTACT>
-__global__ void __launch_bounds__(kBwdMaxThreads) rev_kernel(BwdParams P) {
+__global__ void __launch_bounds__(rev_max_threads(NV)) rev_kernel(BwdParams P) {
     constexpr int TPR = threads_per_rod(NV);
     extern __shared__ float4 dyn_smem[];
     const int rs = threadIdx.x / TPR;
@@ -959,7 +967,7 @@ __global__ void __launch_bounds__(kBwdMaxThreads) rev_kernel(BwdParams P) {
 // ------------------------------------------------------------------ launch helpers
 template <int NV, bool C>
 static int rev_occ_t(int rpc) {
-    if (rpc < 1 || rpc * threads_per_rod(NV) > kBwdMaxThreads) return 0;
+    if (rpc < 1 || rpc * threads_per_rod(NV) > rev_max_threads(NV)) return 0;
     size_t smem = bwd_smem_bytes(NV, C) * rpc;
     auto k = rev_kernel<NV, C>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
