@@ -211,6 +211,81 @@ __device__ __forceinline__ V3<float> mul_rm(const float* o, V3<float> v) {
               o[6] * v.x + o[7] * v.y + o[8] * v.z);
 }
 
+// The dual-number frames of a rod's edges (7 float4 per edge) and the seeds the hinges send
+// back to each edge (3 float4 per edge, accumulated with shared-memory atomics), kept in ten
+// per-edge arrays that the substep's reverse no longer uses when it reaches its hinges.
+struct EdgeDual {
+    float4 *tv, *td, *wv, *wd, *rv, *rd, *cs;   // t | ell, w0 | n1, d1r | c (values, derivatives); s
+    float4 *s0, *s1, *s2;                       // seeds: gt.v | gd1r.x.v, gt.d | gd1r.x.d, gd1r.yz (v, d)
+    __device__ __forceinline__ void store(int j, const EdgeF<dualf>& E) const {
+        tv[j] = make_float4(E.t.x.v, E.t.y.v, E.t.z.v, E.ell.v);
+        td[j] = make_float4(E.t.x.d, E.t.y.d, E.t.z.d, E.ell.d);
+        wv[j] = make_float4(E.w0.x.v, E.w0.y.v, E.w0.z.v, E.n1.v);
+        wd[j] = make_float4(E.w0.x.d, E.w0.y.d, E.w0.z.d, E.n1.d);
+        rv[j] = make_float4(E.d1r.x.v, E.d1r.y.v, E.d1r.z.v, E.c.v);
+        rd[j] = make_float4(E.d1r.x.d, E.d1r.y.d, E.d1r.z.d, E.c.d);
+        cs[j] = make_float4(E.s.v, E.s.d, 0.f, 0.f);
+    }
+    // what the hinge needs: t, d1r, d2r = t x d1r, the material frame (d1, d2) and (c, s)
+    __device__ __forceinline__ void load_frame(int j, EdgeF<dualf>& E) const {
+        const float4 a = tv[j], b = td[j], c = rv[j], d = rd[j], e = cs[j];
+        E.t = mk3(mkd(a.x, b.x), mkd(a.y, b.y), mkd(a.z, b.z));
+        E.d1r = mk3(mkd(c.x, d.x), mkd(c.y, d.y), mkd(c.z, d.z));
+        E.c = mkd(c.w, d.w);
+        E.s = mkd(e.x, e.y);
+        E.d2r = cross(E.t, E.d1r);
+        E.d1 = E.c * E.d1r + E.s * E.d2r;
+        E.d2 = E.c * E.d2r - E.s * E.d1r;
+    }
+    // what edge_reverse needs: t, w0, d1r, n1, ell
+    __device__ __forceinline__ void load_rev(int j, EdgeF<dualf>& E) const {
+        const float4 a = tv[j], b = td[j], c = wv[j], d = wd[j], e = rv[j], f = rd[j];
+        E.t = mk3(mkd(a.x, b.x), mkd(a.y, b.y), mkd(a.z, b.z));
+        E.ell = mkd(a.w, b.w);
+        E.w0 = mk3(mkd(c.x, d.x), mkd(c.y, d.y), mkd(c.z, d.z));
+        E.n1 = mkd(c.w, d.w);
+        E.d1r = mk3(mkd(e.x, f.x), mkd(e.y, f.y), mkd(e.z, f.z));
+    }
+    __device__ __forceinline__ void zero_seeds(int j) const {
+        s0[j] = s1[j] = s2[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __device__ __forceinline__ void add_seeds(int j, V3<dualf> gt, V3<dualf> gr) const {
+        atomicAdd(&s0[j].x, gt.x.v);
+        atomicAdd(&s0[j].y, gt.y.v);
+        atomicAdd(&s0[j].z, gt.z.v);
+        atomicAdd(&s0[j].w, gr.x.v);
+        atomicAdd(&s1[j].x, gt.x.d);
+        atomicAdd(&s1[j].y, gt.y.d);
+        atomicAdd(&s1[j].z, gt.z.d);
+        atomicAdd(&s1[j].w, gr.x.d);
+        atomicAdd(&s2[j].x, gr.y.v);
+        atomicAdd(&s2[j].y, gr.z.v);
+        atomicAdd(&s2[j].z, gr.y.d);
+        atomicAdd(&s2[j].w, gr.z.d);
+    }
+    __device__ __forceinline__ void load_seeds(int j, V3<dualf>& gt, V3<dualf>& gr) const {
+        const float4 a = s0[j], b = s1[j], c = s2[j];
+        gt = mk3(mkd(a.x, b.x), mkd(a.y, b.y), mkd(a.z, b.z));
+        gr = mk3(mkd(a.w, b.w), mkd(c.x, c.z), mkd(c.y, c.w));
+    }
+};
+
+// The values of a dual-number edge frame.
+__device__ __forceinline__ EdgeF<float> edge_vals(const EdgeF<dualf>& D) {
+    EdgeF<float> E;
+    E.t = vals(D.t);
+    E.w0 = vals(D.w0);
+    E.d1r = vals(D.d1r);
+    E.d2r = vals(D.d2r);
+    E.d1 = vals(D.d1);
+    E.d2 = vals(D.d2);
+    E.ell = D.ell.v;
+    E.n1 = D.n1.v;
+    E.c = D.c.v;
+    E.s = D.s.v;
+    return E;
+}
+
 // ------------------------------------------------------------------ reverse of one substep
 // On entry the shared state holds S_n (the substep's start), the recorded intermediates and,
 // for a self-contact rod, the frame's pair list and the projection data of the first
@@ -554,52 +629,52 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                                 pm[11] * ph1.x + pm[14] * ph1.y + pm[17] * ph1.z);
         add3(lphif, q, m0 + m1);
     }
-    // ---- B8: per edge, reverse of the new reference-frame base and stretching second order
+    // ---- B8: per edge, the reverse of the new reference-frame base and the stretching second
+    // order; and the edge's frame as dual numbers in the direction of the force cotangents LG,
+    // once per edge, for the hinge phase (B7).  Arrays dead after B5 hold the dual frames
+    // (EdgeDual) and the seeds the two hinges of an edge send back to it (zeroed here).
     const bool strands = R.flags & ROD_STRANDS;
+    const EdgeDual ES{a.LD, a.LP0, a.V1, a.DF, s.X, s.V, s.HB0, s.HB1, s.HB2, s.ND};
     for (int j = g.tid; j < ne; j += TPR) {
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
         const float4 ed = s.ED[j], et = s.ET[j];
-        if (strands && !(et.w > 0.f)) {   // a break edge kept its base frame: identity reverse
-            s.HB1[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
-        EdgeF<float> E;
-        edge_forward(E, f3(s.X0[j]), f3(s.X0[j1]), f3(et), f3(ed), ed.w);
+        ES.zero_seeds(j);
+        if (strands && !(et.w > 0.f)) continue;   // a break edge kept its base frame: identity reverse
+        const float4 lga = a.LG[j], lgb = a.LG[j1];
+        EdgeF<dualf> Ed;
+        edge_forward(Ed, lift(f3(s.X0[j]), f3(lga)), lift(f3(s.X0[j1]), f3(lgb)), lift(f3(et)), lift(f3(ed)),
+                     mkd(ed.w, lga.w));
+        ES.store(j, Ed);
+        const EdgeF<float> E = edge_vals(Ed);
         V3<float> gtb, gd1b;
         V3<float> le = edge_reverse<float, true>(E, f3(et), f3(ed), f3(a.LT[j]), f3(a.LE[j]), 0.f, &gtb, &gd1b);
         if (R.kA > 0.f) {
-            const V3<float> les = f3(a.LG[j1]) - f3(a.LG[j]);
+            const V3<float> les = f3(lgb) - f3(lga);
             const float eb = P.ES[e0 + j].x;
             const float tl = dot(E.t, les);
             le += R.kA * ((tl / eb) * E.t + (E.ell / eb - 1.f) / E.ell * (les - tl * E.t));
             gl[0] += (double)((E.ell / eb - 1.f) * tl);
         }
-        s.HB1[j] = f4(le, 0.f);
+        atomic_add3(&a.LX[j], -le);
+        atomic_add3(&a.LX[j1], le);
         a.LT[j] = f4(gtb, 0.f);
         a.LE[j] = f4(gd1b, a.LE[j].w);
     }
     g.sync();
-    for (int i = g.tid; i < nv; i += TPR) {
-        V3<float> l = f3(a.LX[i]);
-        if (closed || i < nv - 1) l -= f3(s.HB1[i]);
-        if (closed || i > 0) l += f3(s.HB1[i == 0 ? ne - 1 : i - 1]);
-        a.LX[i] = f4(l, 0.f);
-    }
-    g.sync();
-    // ---- B7: hinges: force second order (dual numbers), plasticity, its first-order reverse
+    // ---- B7: hinges: force second order (dual numbers), plasticity, its first-order reverse.
+    // The hinge's own part runs here; the reverse through its edges' frames runs per edge below
+    // on the sum of the seeds of both hinges of the edge (the reverse is linear in them).
     for (int k = g.tid; k < nh; k += TPR) {
         const int i = closed ? k : k + 1;
         const int ea = (i == 0) ? ne - 1 : i - 1, eb = i;
-        const int im = (i == 0) ? nv - 1 : i - 1, ip = (i + 1 == nv) ? 0 : i + 1;
-        const float4 EDa = s.ED[ea], EDb = s.ED[eb], ETa = s.ET[ea], ETb = s.ET[eb], hg = s.HG[i];
+        const float4 ETa = s.ET[ea], ETb = s.ET[eb], hg = s.HG[i];
         if (strands && !(ETa.w > 0.f && ETb.w > 0.f)) continue;   // inactive: at an end of a break edge
         const float lbar = 0.5f * (ETa.w + ETb.w), il = 1.f / lbar;
         // second order of the elastic force: tangents = cotangents of the gradient
         HingeF<dualf> Hd;
-        const float4 gm_ = a.LG[im], gi_ = a.LG[i], gp_ = a.LG[ip];
-        hinge_forward(Hd, lift(f3(s.X0[im]), f3(gm_)), lift(f3(s.X0[i]), f3(gi_)), lift(f3(s.X0[ip]), f3(gp_)),
-                      lift(f3(ETa)), lift(f3(EDa)), lift(f3(ETb)), lift(f3(EDb)), mkd(EDa.w, a.LG[ea].w),
-                      mkd(EDb.w, a.LG[eb].w), mkd(hg.w));
+        ES.load_frame(ea, Hd.a);
+        ES.load_frame(eb, Hd.b);
+        hinge_core_forward(Hd, mkd(s.ED[ea].w, a.LG[ea].w), mkd(s.ED[eb].w, a.LG[eb].w), mkd(hg.w));
         const float hk0 = Hd.k0.v, hk1 = Hd.k1.v;   // the hinge's material curvature (for plasticity)
         float kb0 = hg.x, kb1 = hg.y;
         const bool plastic = R.flags & ROD_PLASTIC;
@@ -626,20 +701,33 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             lk0 -= le0;
             lk1 -= le1;
         }
-        V3<dualf> gxm, gxi, gxp, gtba, gd1ba, gtbb, gd1bb;
-        dualf gta, gtb;
-        hinge_reverse<dualf, true>(Hd, lift(f3(ETa)), lift(f3(EDa)), lift(f3(ETb)), lift(f3(EDb)), gk0, gk1, gmt,
-                                   mkd(0.f), gxm, gxi, gxp, gta, gtb, &gtba, &gd1ba, &gtbb, &gd1bb);
-        atomic_add3(&a.LX[im], ders(gxm));
-        atomic_add3(&a.LX[i], ders(gxi));
-        atomic_add3(&a.LX[ip], ders(gxp));
-        atomicAdd(&a.LE[ea].w, gta.d);
-        atomicAdd(&a.LE[eb].w, gtb.d);
-        atomic_add3(&a.LT[ea], ders(gtba));
-        atomic_add3(&a.LE[ea], ders(gd1ba));
-        atomic_add3(&a.LT[eb], ders(gtbb));
-        atomic_add3(&a.LE[eb], ders(gd1bb));
+        V3<dualf> gta, gd1ra, gtb, gd1rb;
+        dualf ghta, ghtb;
+        hinge_core_reverse(Hd, gk0, gk1, gmt, mkd(0.f), gta, gd1ra, gtb, gd1rb, ghta, ghtb);
+        ES.add_seeds(ea, gta, gd1ra);
+        ES.add_seeds(eb, gtb, gd1rb);
+        atomicAdd(&a.LE[ea].w, ghta.d);
+        atomicAdd(&a.LE[eb].w, ghtb.d);
         a.LK[i] = make_float4(lk0, lk1, 0.f, 0.f);
+    }
+    g.sync();
+    // ---- B7, per edge: the reverse through the edge's frame (vertices and base frame)
+    for (int j = g.tid; j < ne; j += TPR) {
+        const float4 et = s.ET[j];
+        if (strands && !(et.w > 0.f)) continue;
+        V3<dualf> gt, gd1r;
+        ES.load_seeds(j, gt, gd1r);
+        EdgeF<dualf> Ed;
+        ES.load_rev(j, Ed);
+        V3<dualf> gtbd, gd1bd;
+        const V3<float> ge = ders(edge_reverse<dualf, true>(Ed, lift(f3(et)), lift(f3(s.ED[j])), gt, gd1r,
+                                                            mkd(0.f), &gtbd, &gd1bd));
+        const int j1 = (j + 1 == nv) ? 0 : j + 1;
+        atomic_add3(&a.LX[j], -ge);
+        atomic_add3(&a.LX[j1], ge);
+        const float4 lt = a.LT[j], le = a.LE[j];
+        a.LT[j] = f4(f3(lt) + ders(gtbd), 0.f);
+        a.LE[j] = f4(f3(le) + ders(gd1bd), le.w);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) gm[c] += gl[c];

@@ -92,11 +92,9 @@ struct HingeF {
     T cc, y, xq, mref, m, k0, k1;
 };
 
+// The hinge's own part, from its two edges' frames (H.a, H.b: t, d1r, d2r, d1, d2 set).
 template <class T>
-DLO_HD void hinge_forward(HingeF<T>& H, V3<T> xm, V3<T> xi, V3<T> xp, V3<T> tba, V3<T> d1ba,
-                          V3<T> tbb, V3<T> d1bb, T tha, T thb, T mprev) {
-    edge_forward(H.a, xm, xi, tba, d1ba, tha);
-    edge_forward(H.b, xi, xp, tbb, d1bb, thb);
+DLO_HD void hinge_core_forward(HingeF<T>& H, T tha, T thb, T mprev) {
     H.cc = 1.f + dot(H.a.t, H.b.t);
     H.X = cross(H.a.t, H.b.t);
     H.kb = (2.f / H.cc) * H.X;
@@ -112,14 +110,21 @@ DLO_HD void hinge_forward(HingeF<T>& H, V3<T> xm, V3<T> xi, V3<T> xp, V3<T> tba,
     H.m = thb - tha + H.mref;
 }
 
-// Reverse of hinge_forward from seeds on kappa (gk0, gk1), on the total twist m (gmt, flows
-// to theta and the reference twist) and on the reference twist alone (gmr).  Returns the
-// adjoints of the three vertices and the two twist angles; with BASE also of both base frames.
-template <class T, bool BASE>
-DLO_HD void hinge_reverse(const HingeF<T>& H, V3<T> tba, V3<T> d1ba, V3<T> tbb, V3<T> d1bb,
-                          T gk0, T gk1, T gmt, T gmr, V3<T>& gxm, V3<T>& gxi, V3<T>& gxp,
-                          T& gtha, T& gthb, V3<T>* gtba, V3<T>* gd1ba, V3<T>* gtbb,
-                          V3<T>* gd1bb) {
+template <class T>
+DLO_HD void hinge_forward(HingeF<T>& H, V3<T> xm, V3<T> xi, V3<T> xp, V3<T> tba, V3<T> d1ba,
+                          V3<T> tbb, V3<T> d1bb, T tha, T thb, T mprev) {
+    edge_forward(H.a, xm, xi, tba, d1ba, tha);
+    edge_forward(H.b, xi, xp, tbb, d1bb, thb);
+    hinge_core_forward(H, tha, thb, mprev);
+}
+
+// Reverse of hinge_core_forward from seeds on kappa (gk0, gk1), on the total twist m (gmt,
+// flows to theta and the reference twist) and on the reference twist alone (gmr): the adjoints
+// of both edges' tangents and reference directors (gta, gd1ra, gtb, gd1rb) and of the two
+// twist angles.
+template <class T>
+DLO_HD void hinge_core_reverse(const HingeF<T>& H, T gk0, T gk1, T gmt, T gmr, V3<T>& gta, V3<T>& gd1ra,
+                               V3<T>& gtb_, V3<T>& gd1rb, T& gtha, T& gthb) {
     const EdgeF<T>& A = H.a;
     const EdgeF<T>& B = H.b;
     T hk0 = 0.5f * gk0, hk1 = 0.5f * gk1;
@@ -136,14 +141,14 @@ DLO_HD void hinge_reverse(const HingeF<T>& H, V3<T> tba, V3<T> d1ba, V3<T> tbb, 
     T gy = gang * H.xq / r2;
     T gxq = -(gang * H.y) / r2;
     V3<T> gu = gy * cross(B.d1r, B.t) + gxq * B.d1r;
-    V3<T> gd1rb = gy * cross(B.t, H.u) + gxq * H.u;
-    V3<T> gtb_ = gy * cross(H.u, B.d1r);
+    gd1rb = gy * cross(B.t, H.u) + gxq * H.u;
+    gtb_ = gy * cross(H.u, B.d1r);
     T Xd = dot(H.X, A.d1r);
     T gux = dot(gu, H.X);
     gcc += dot(gu, A.d1r) - Xd * gux / (H.cc * H.cc);
-    V3<T> gd1ra = (H.cc - 1.f) * gu + cross(gu, H.X) + (gux / H.cc) * H.X;
+    gd1ra = (H.cc - 1.f) * gu + cross(gu, H.X) + (gux / H.cc) * H.X;
     gX += cross(A.d1r, gu) + (Xd / H.cc) * gu + (gux / H.cc) * A.d1r;
-    V3<T> gta = gcc * B.t + cross(B.t, gX);
+    gta = gcc * B.t + cross(B.t, gX);
     gtb_ += gcc * A.t + cross(gX, A.t);
     // material frames -> reference frames and twist angles
     {
@@ -160,6 +165,19 @@ DLO_HD void hinge_reverse(const HingeF<T>& H, V3<T> tba, V3<T> d1ba, V3<T> tbb, 
         gtb_ += cross(B.d1r, gd2r);
         gd1rb += cross(gd2r, B.t);
     }
+}
+
+// Reverse of hinge_forward: the adjoints of the three vertices and the two twist angles; with
+// BASE also of both base frames.
+template <class T, bool BASE>
+DLO_HD void hinge_reverse(const HingeF<T>& H, V3<T> tba, V3<T> d1ba, V3<T> tbb, V3<T> d1bb,
+                          T gk0, T gk1, T gmt, T gmr, V3<T>& gxm, V3<T>& gxi, V3<T>& gxp,
+                          T& gtha, T& gthb, V3<T>* gtba, V3<T>* gd1ba, V3<T>* gtbb,
+                          V3<T>* gd1bb) {
+    V3<T> gta, gd1ra, gtb_, gd1rb;
+    hinge_core_reverse(H, gk0, gk1, gmt, gmr, gta, gd1ra, gtb_, gd1rb, gtha, gthb);
+    const EdgeF<T>& A = H.a;
+    const EdgeF<T>& B = H.b;
     T zero = cst<T>(0.f);
     V3<T> gea = edge_reverse<T, BASE>(A, tba, d1ba, gta, gd1ra, zero, gtba, gd1ba);
     V3<T> geb = edge_reverse<T, BASE>(B, tbb, d1bb, gtb_, gd1rb, zero, gtbb, gd1bb);
