@@ -671,6 +671,30 @@ __device__ __noinline__ void self_friction_call(const RodInfo* R, float4* base, 
     self_friction<NV, CONTACT, TPR>(*R, s, g, np, h, mu);
 }
 
+// An edge's frame for the hinge phase from its stored (t, |e|), (d1r, cos theta) and
+// sin theta: d2r = t x d1r and the material frame, as edge_forward forms them.
+__device__ __forceinline__ void load_frame(EdgeF<float>& E, float4 ta, float4 rc, float sn) {
+    E.t = f3(ta);
+    E.d1r = f3(rc);
+    E.c = rc.w;
+    E.s = sn;
+    E.d2r = cross(E.t, E.d1r);
+    E.d1 = E.c * E.d1r + E.s * E.d2r;
+    E.d2 = E.c * E.d2r - E.s * E.d1r;
+}
+
+// A hinge's gradient seeds for one of its edges, added to the edge's sums (the other hinge of
+// the edge adds to the same sums).
+__device__ __forceinline__ void add_seeds(float4* sg, float4* sr, V3<float> gt, V3<float> gd1r, float gth) {
+    atomicAdd(&sg->x, gt.x);
+    atomicAdd(&sg->y, gt.y);
+    atomicAdd(&sg->z, gt.z);
+    atomicAdd(&sg->w, gth);
+    atomicAdd(&sr->x, gd1r.x);
+    atomicAdd(&sr->y, gd1r.y);
+    atomicAdd(&sr->z, gd1r.z);
+}
+
 // ------------------------------------------------------------------ one substep
 template <int NV, bool CONTACT, int TPR>
 __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* __restrict__ KIN, const float2* __restrict__ ES,
@@ -680,37 +704,67 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
     const bool closed = R.flags & ROD_CLOSED;
     const int nh = closed ? nv : nv - 2;
     const bool strands = R.flags & ROD_STRANDS;
-    // --- hinge phase
+    // --- edge frames, once per edge: (t, |e|) in EA, (w0, n1) in EW, (d1r, cos theta) in ND
+    // (the vertex phase takes the new reference director from there), and per edge the seeds
+    // its two hinges send back: (dU/dt, dU/dtheta) in SG, (dU/dd1r, sin theta) in SR.  The
+    // displacement array SR = X is rewritten by the vertex phase before it is read.
+    float4* const EA = s.HB0;
+    float4* const EW = s.HB1;
+    float4* const SG = s.HB2;
+    float4* const SR = s.X;
+    for (int j = g.tid; j < ne; j += TPR) {
+        const int j1 = (j + 1 == nv) ? 0 : j + 1;
+        const float4 ed = s.ED[j], et = s.ET[j];
+        SG[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (strands && !(et.w > 0.f)) continue;   // a break edge: no frame, no hinge
+        EdgeF<float> E;
+        edge_forward(E, f3(s.X0[j]), f3(s.X0[j1]), f3(et), f3(ed), ed.w);
+        EA[j] = f4(E.t, E.ell);
+        EW[j] = f4(E.w0, E.n1);
+        s.ND[j] = f4(E.d1r, E.c);
+        SR[j] = make_float4(0.f, 0.f, 0.f, E.s);
+    }
+    g.sync();
+    // --- hinge phase: the hinge's own part, from its edges' frames
     for (int k = g.tid; k < nh; k += TPR) {
         const int i = closed ? k : k + 1;
         const int a = (i == 0) ? ne - 1 : i - 1;
         const int b = i;
-        const int im = (i == 0) ? nv - 1 : i - 1;
-        const int ip = (i + 1 == nv) ? 0 : i + 1;
-        float4 EDa = s.ED[a], EDb = s.ED[b], ETa = s.ET[a], ETb = s.ET[b], hg = s.HG[i];
-        if (strands && !(ETa.w > 0.f && ETb.w > 0.f)) {   // a hinge at an end of a break edge
-            s.HB0[i] = s.HB1[i] = s.HB2[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
+        const float4 ETa = s.ET[a], ETb = s.ET[b];
+        float4 hg = s.HG[i];
+        if (strands && !(ETa.w > 0.f && ETb.w > 0.f)) continue;   // a hinge at an end of a break edge
         HingeF<float> H;
-        hinge_forward(H, f3(s.X0[im]), f3(s.X0[i]), f3(s.X0[ip]), f3(ETa), f3(EDa), f3(ETb), f3(EDb), EDa.w,
-                      EDb.w, hg.w);
+        load_frame(H.a, EA[a], s.ND[a], SR[a].w);
+        load_frame(H.b, EA[b], s.ND[b], SR[b].w);
+        hinge_core_forward(H, s.ED[a].w, s.ED[b].w, hg.w);
         const float lbar = 0.5f * (ETa.w + ETb.w);
         if (R.flags & ROD_PLASTIC) plastic_update(H.k0, H.k1, hg.x, hg.y, R.sy * lbar, R.rc);
         const float il = 1.f / lbar;
         const float gk0 = R.Bm * il * (H.k0 - hg.x), gk1 = R.Bm * il * (H.k1 - hg.y);
         const float gm = R.beta * il * (H.m - hg.z);
-        V3<float> gxm, gxi, gxp;
-        float gta, gtb;
-        hinge_reverse<float, false>(H, f3(ETa), f3(EDa), f3(ETb), f3(EDb), gk0, gk1, gm, 0.f, gxm, gxi, gxp, gta,
-                                    gtb, nullptr, nullptr, nullptr, nullptr);
-        s.HB0[i] = f4(gxm, gta);
-        s.HB1[i] = f4(gxi, gtb);
-        s.HB2[i] = f4(gxp, 0.f);
-        s.ND[b] = f4(H.b.d1r, 0.f);
-        // the first edge of an open rod or strand gets its frame from its only hinge
-        if (!closed && (i == 1 || (strands && !(s.ET[a - 1].w > 0.f)))) s.ND[a] = f4(H.a.d1r, 0.f);
+        V3<float> gta, gd1ra, gtb, gd1rb;
+        float ghta, ghtb;
+        hinge_core_reverse(H, gk0, gk1, gm, 0.f, gta, gd1ra, gtb, gd1rb, ghta, ghtb);
+        add_seeds(SG + a, SR + a, gta, gd1ra, ghta);
+        add_seeds(SG + b, SR + b, gtb, gd1rb, ghtb);
         s.HG[i] = make_float4(hg.x, hg.y, hg.z, H.mref);
+    }
+    g.sync();
+    // --- per edge, the reverse through its frame: the gradient on the edge vector (in SG, with
+    // the edge's twist gradient; zero for a break edge)
+    for (int j = g.tid; j < ne; j += TPR) {
+        const float4 et = s.ET[j], sg = SG[j];
+        if (strands && !(et.w > 0.f)) continue;   // SG[j] stays zero
+        const float4 ea = EA[j], ew = EW[j], nd = s.ND[j];
+        EdgeF<float> E;
+        E.t = f3(ea);
+        E.ell = ea.w;
+        E.w0 = f3(ew);
+        E.n1 = ew.w;
+        E.d1r = f3(nd);
+        const V3<float> ge =
+            edge_reverse<float, false>(E, f3(et), f3(s.ED[j]), f3(sg), f3(SR[j]), 0.f, nullptr, nullptr);
+        SG[j] = f4(ge, sg.w);
     }
     g.sync();
     // --- vertex phase
@@ -718,41 +772,33 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
         const float4 xi4 = s.X0[i];
         const V3<float> xi = f3(xi4);
         V3<float> g = zf3();
-        auto has_h = [&](int j) { return closed || (j >= 1 && j <= nv - 2); };
-        const int ip = (i + 1 == nv) ? 0 : i + 1;
         const int im = (i == 0) ? nv - 1 : i - 1;
         float gth = 0.f;
         const bool has_e = closed || i < nv - 1;          // edge i starts here
-        if (has_h(i)) {
-            float4 q = s.HB1[i];
-            g += f3(q);
-            gth += q.w;
+        const bool has_em = closed || i >= 1;             // edge i-1 ends here
+        // bending and twisting: the gradients on the edge vectors of the edges at this vertex
+        if (has_e) {
+            const float4 q = SG[i];
+            g -= f3(q);
+            gth = q.w;
         }
-        if ((closed || i + 1 <= nv - 2) && has_h(ip) && (closed || i + 1 < nv)) {
-            float4 q = s.HB0[ip];
-            g += f3(q);
-            if (has_e) gth += q.w;
-        }
-        if ((closed || i >= 2) && has_h(im)) g += f3(s.HB2[im]);
+        if (has_em) g += f3(SG[im]);
         V3<float> t_i = zf3();
         float ell_i = 0.f;
         // a break edge (between two strands) starts here: no tangent, no force, frame kept
         const bool brk = strands && has_e && !(ES[e0 + i].x > 0.f);
         if (has_e && !brk) {
-            V3<float> e = f3(s.X0[ip]) - xi;
-            ell_i = sqrtf(dot(e, e));
-            t_i = e / ell_i;
+            const float4 q = EA[i];
+            ell_i = q.w;
+            t_i = f3(q);
             if (R.kA > 0.f) {
                 float eb = ES[e0 + i].x;
                 g -= (R.kA * (ell_i / eb - 1.f)) * t_i;
             }
         }
-        if (R.kA > 0.f && (closed || i >= 1) && !(strands && !(ES[e0 + im].x > 0.f))) {
-            const int j = im;   // edge i-1 ends here
-            V3<float> e = xi - f3(s.X0[j]);
-            float ell = sqrtf(dot(e, e));
-            float eb = ES[e0 + j].x;
-            g += (R.kA * (ell / eb - 1.f) / ell) * e;
+        if (R.kA > 0.f && has_em && !(strands && !(ES[e0 + im].x > 0.f))) {
+            const float4 q = EA[im];   // edge i-1 ends here
+            g += (R.kA * (q.w / ES[e0 + im].x - 1.f)) * f3(q);
         }
         float4 vi = s.V[i];
         const float4 kin = KIN[v0 + i];
@@ -787,17 +833,7 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
             if (brk) {
                 s.ED[i] = make_float4(ed.x, ed.y, ed.z, ed.w + h * om1);
             } else {
-                // an edge with no hinge (a single open edge, a strand of two vertices):
-                // transport its frame here
-                const bool solo = nh == 0 || (strands && (i == 0 || !(ES[e0 + i - 1].x > 0.f)) &&
-                                              (i + 1 >= ne || !(ES[e0 + i + 1].x > 0.f)));
-                V3<float> d1r = solo ? zf3() : f3(s.ND[i]);
-                if (solo) {
-                    EdgeF<float> E;
-                    edge_forward(E, xi, f3(s.X0[ip]), f3(s.ET[i]), f3(ed), ed.w);
-                    d1r = E.d1r;
-                }
-                s.ED[i] = f4(d1r, ed.w + h * om1);
+                s.ED[i] = f4(f3(s.ND[i]), ed.w + h * om1);   // the edge's new reference director
                 s.ET[i] = f4(t_i, ES[e0 + i].x);
             }
         }
