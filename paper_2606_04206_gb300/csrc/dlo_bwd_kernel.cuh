@@ -106,6 +106,10 @@ __device__ __forceinline__ V3<T> prim_respond(int k, const SceneDev& sc, const R
         sdf = sdf_box(x, f3(sc.box_c[b]), f3(sc.box_h[b]), n);
     } else {
         V3<T> a = gp - sc.grip_hl * gax, bb = gp + sc.grip_hl * gax;
+        if (capsule_far(vals(x), vals(a), vals(bb), sc.grip_r + R.radius + kContactReach * R.eps)) {
+            act = false;
+            return v;
+        }
         sdf = sdf_capsule(x, a, bb, sc.grip_r, n);
         vrig = vp + cross(w, x - gp);
     }

@@ -36,6 +36,17 @@ DLO_HD V3<double> transport_d(V3<double> a, V3<double> b, V3<double> d) {
     return c * d + cross(k, d) + (dot(k, d) / (1.0 + c)) * k;
 }
 
+// Length of e and its inverse from one reciprocal square root.
+DLO_HD void len_inv(V3<float> e, float& ell, float& inv) {
+    const float e2 = dot(e, e);
+#ifdef __CUDA_ARCH__
+    inv = rsqrtf(e2);
+#else
+    inv = 1.f / sqrtf(e2);
+#endif
+    ell = e2 * inv;
+}
+
 // ------------------------------------------------------------------ edge frames
 template <class T>
 struct EdgeF {
@@ -240,6 +251,18 @@ DLO_HD T sdf_capsule(V3<T> x, V3<T> a, V3<T> b, float rc, V3<T>& n) {
 }
 
 constexpr float kContactReach = 2.31f;   // -ln(0.1) = 2.3026 plus a margin
+
+// Whether x lies farther than reach from the segment ab, by squared distances (no square root
+// or quotient for the many vertices far from a gripper); a margin of 1e-3 reach keeps every
+// point the exact test would take.
+DLO_HD bool capsule_far(V3<float> x, V3<float> a, V3<float> b, float reach) {
+    const V3<float> ab = b - a, xa = x - a;
+    const float L2 = dot(ab, ab), q = dot(xa, ab);
+    const float s = q <= 0.f ? 0.f : (q >= L2 ? 1.f : q / L2);
+    const V3<float> dv = xa - s * ab;
+    const float lim = 1.001f * reach;
+    return dot(dv, dv) > lim * lim;
+}
 
 // Soft coupling (Sec. 3.2): d = r - SDF, f = min(exp(d / eps_s), 1); if f > 0.1 the relative
 // velocity's normal part gets restitution and its tangential part Coulomb friction, and the

@@ -264,7 +264,8 @@ __global__ void pl_inext(const RodInfo* rods, const int* erod, long long Et, con
     const int j1 = (j + 1 == nv) ? 0 : j + 1;
     const float4 A = D[R.v0 + j], B = D[R.v0 + j1];
     const V3<float> e = (f3(X[R.v0 + j1]) - f3(X[R.v0 + j])) + (f3(B) - f3(A));
-    const float ell = sqrtf(dot(e, e));
+    float ell, ie;
+    len_inv(e, ell, ie);
     const float eb = ET[R.e0 + j].w;
     float target;
     bool active;
@@ -282,8 +283,8 @@ __global__ void pl_inext(const RodInfo* rods, const int* erod, long long Et, con
         return;
     }
     const float lam = (ell - target) / ws;
-    const V3<float> t = e / ell;
-    if (PBDout) PBDout[ge] = f4(t, target / ell);
+    const V3<float> t = ie * e;
+    if (PBDout) PBDout[ge] = f4(t, target * ie);
     const V3<float> da = (lam * A.w) * t, db = (lam * B.w) * t;
     D[R.v0 + j] = make_float4(A.x + da.x, A.y + da.y, A.z + da.z, A.w);
     D[R.v0 + j1] = make_float4(B.x - db.x, B.y - db.y, B.z - db.z, B.w);

@@ -235,6 +235,7 @@ __device__ __forceinline__ V3<float> rigid_contact(const SceneDev& sc, const Rod
         V3<float> p = f3(o[0], o[1], o[2]);
         V3<float> ax = f3(o[8], o[11], o[14]);   // column 2 of R0: the capsule axis
         V3<float> a = p - sc.grip_hl * ax, b = p + sc.grip_hl * ax, n;
+        if (capsule_far(x, a, b, sc.grip_r + R.radius + kContactReach * R.eps)) continue;
         float sdf = sdf_capsule(x, a, b, sc.grip_r, n);
         if (sdf > R.radius + kContactReach * R.eps) continue;
         V3<float> vp = f3(o[24], o[25], o[26]);
@@ -531,7 +532,8 @@ __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* 
         int j1 = (j + 1 == nv) ? 0 : j + 1;
         float4 A = D[j], B = D[j1];              // displacements (w = inverse mass)
         V3<float> e = (f3(X0[j1]) - f3(X0[j])) + (f3(B) - f3(A));
-        float ell = sqrtf(dot(e, e));
+        float ell, ie;
+        len_inv(e, ell, ie);
         float eb = ET[j].w;
         float target;
         bool active;
@@ -549,8 +551,8 @@ __device__ __forceinline__ void inext_color_arr(const RodInfo& R, const float4* 
             continue;
         }
         float lam = (ell - target) / ws;
-        V3<float> t = e / ell;
-        if (prec) prec[j] = f4(t, target / ell);
+        V3<float> t = ie * e;
+        if (prec) prec[j] = f4(t, target * ie);
         V3<float> da = (lam * A.w) * t, db = (lam * B.w) * t;
         D[j] = make_float4(A.x + da.x, A.y + da.y, A.z + da.z, A.w);
         D[j1] = make_float4(B.x - db.x, B.y - db.y, B.z - db.z, B.w);
