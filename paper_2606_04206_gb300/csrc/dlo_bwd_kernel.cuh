@@ -116,27 +116,6 @@ __device__ __forceinline__ V3<T> prim_respond(int k, const SceneDev& sc, const R
     return contact_respond(v, sdf, n, vrig, R.radius, R.eps, sc.mu_rigid, sc.restitution, act);
 }
 
-// Friction of one pair (App. A.1), as a function of the four positions at the first
-// projection and the four rebuilt velocities; returns whether the pair acts.
-template <class T>
-__device__ __forceinline__ bool fric_pair(const V3<T>* P, const V3<T>* Vv, const float* w, float rsum, float mu,
-                                          float h, V3<T>* dv) {
-    T s, u, d, W;
-    V3<T> n, dx[4];
-    if (!pair_correction(P[0], P[1], P[2], P[3], w[0], w[1], w[2], w[3], rsum, dx, s, u, n, d, W)) return false;
-    V3<T> vrel = (1.f - s) * Vv[0] + s * Vv[1] - (1.f - u) * Vv[2] - u * Vv[3];
-    V3<T> vt = vrel - dot(vrel, n) * n;
-    T vt2 = dot(vt, vt);
-    if (!(vof(vt2) > 1e-24f)) return false;
-    T coef = dmin(mu * d / (h * dsqrt(vt2)), cst<T>(1.f));
-    V3<T> dd = (-(coef / W)) * vt;
-    dv[0] = (w[0] * (1.f - s)) * dd;
-    dv[1] = (w[1] * s) * dd;
-    dv[2] = (-(w[2] * (1.f - u))) * dd;
-    dv[3] = (-(w[3] * u)) * dd;
-    return true;
-}
-
 template <int NV, bool CONTACT>
 struct AdjArrays {
     float4 *LX, *LD, *LV, *LE, *LT, *LK, *LP0, *LG, *V1, *DF;
@@ -356,29 +335,13 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                 w[k] = s.X0[idx[k]].w;
                 lo[k] = f3(a.LV[idx[k]]);
             }
-            float lin[24];
-#pragma unroll 1
-            for (int d = 0; d < 24; ++d) {
-                V3<dualf> Pd[4], Vd[4], dv[4];
+            V3<float> pb[4], vb[4];
+            if (fric_pair_vjp(Pf, Vf, w, rsum, sc.mu_self, h, lo, pb, vb))
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    V3<float> ep = zf3(), ev = zf3();
-                    if (d / 3 == k) (d % 3 == 0 ? ep.x : d % 3 == 1 ? ep.y : ep.z) = 1.f;
-                    if (d / 3 == 4 + k) (d % 3 == 0 ? ev.x : d % 3 == 1 ? ev.y : ev.z) = 1.f;
-                    Pd[k] = lift(Pf[k], ep);
-                    Vd[k] = lift(Vf[k], ev);
+                    atomic_add3(&a.LP0[idx[k]], pb[k]);
+                    atomic_add3(&LTMP[idx[k]], vb[k]);
                 }
-                float acc = 0.f;
-                if (fric_pair(Pd, Vd, w, rsum, sc.mu_self, h, dv))
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) acc += dot(ders(dv[k]), lo[k]);
-                lin[d] = acc;
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                atomic_add3(&a.LP0[idx[k]], f3(lin[3 * k], lin[3 * k + 1], lin[3 * k + 2]));
-                atomic_add3(&LTMP[idx[k]], f3(lin[12 + 3 * k], lin[13 + 3 * k], lin[14 + 3 * k]));
-            }
         }
         g.sync();
         for (int i = g.tid; i < nv; i += TPR) {
@@ -423,33 +386,10 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                         w[k] = s.X0[idx[k]].w;
                         lo[k] = f3(a.LD[idx[k]]);
                     }
-                    {
-                        V3<float> dxf[4], nf;
-                        float su, uu, dd, W;
-                        if (!pair_correction(Pf[0], Pf[1], Pf[2], Pf[3], w[0], w[1], w[2], w[3], rsum, dxf, su, uu,
-                                             nf, dd, W))
-                            continue;
-                    }
-                    float lin[12];
-#pragma unroll 1
-                    for (int d = 0; d < 12; ++d) {
-                        V3<dualf> Pd[4], dx[4], n;
-                        dualf su, uu, dd, W;
+                    V3<float> pb[4];
+                    if (pair_correction_vjp(Pf, w, rsum, lo, pb))
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            V3<float> ep = zf3();
-                            if (d / 3 == k) (d % 3 == 0 ? ep.x : d % 3 == 1 ? ep.y : ep.z) = 1.f;
-                            Pd[k] = lift(Pf[k], ep);
-                        }
-                        float acc = 0.f;
-                        if (pair_correction(Pd[0], Pd[1], Pd[2], Pd[3], w[0], w[1], w[2], w[3], rsum, dx, su, uu, n,
-                                            dd, W))
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) acc += dot(ders(dx[k]), lo[k]);
-                        lin[d] = acc;
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) atomic_add3(&LTMP[idx[k]], f3(lin[3 * k], lin[3 * k + 1], lin[3 * k + 2]));
+                        for (int k = 0; k < 4; ++k) atomic_add3(&LTMP[idx[k]], pb[k]);
                 }
                 g.sync();
                 for (int i = g.tid; i < nv; i += TPR) {

@@ -432,4 +432,196 @@ DLO_HD bool pair_correction(V3<T> xa0, V3<T> xa1, V3<T> xb0, V3<T> xb1, float wa
     return true;
 }
 
+// Friction of one pair (App. A.1), as a function of the four positions at the first
+// projection and the four rebuilt velocities; returns whether the pair acts.
+template <class T>
+DLO_HD bool fric_pair(const V3<T>* P, const V3<T>* Vv, const float* w, float rsum, float mu, float h, V3<T>* dv) {
+    T s, u, d, W;
+    V3<T> n, dx[4];
+    if (!pair_correction(P[0], P[1], P[2], P[3], w[0], w[1], w[2], w[3], rsum, dx, s, u, n, d, W)) return false;
+    V3<T> vrel = (1.f - s) * Vv[0] + s * Vv[1] - (1.f - u) * Vv[2] - u * Vv[3];
+    V3<T> vt = vrel - dot(vrel, n) * n;
+    T vt2 = dot(vt, vt);
+    if (!(vof(vt2) > 1e-24f)) return false;
+    T coef = dmin(mu * d / (h * dsqrt(vt2)), cst<T>(1.f));
+    V3<T> dd = (-(coef / W)) * vt;
+    dv[0] = (w[0] * (1.f - s)) * dd;
+    dv[1] = (w[1] * s) * dd;
+    dv[2] = (-(w[2] * (1.f - u))) * dd;
+    dv[3] = (-(w[3] * u)) * dd;
+    return true;
+}
+
+// ------------------------------------------------------------------ closed-form pair reverses
+// The forward of pair_correction (segments P0P1 and P2P3) with what its reverse needs: the
+// closest-point solve's scalars and how s and u were formed (the branch taken), the normal,
+// depth and weight sum.  The expressions are those of closest_params and pair_correction.
+struct PairFwd {
+    V3<float> d1, d2, r, n;
+    float a, b, c, e, f, den, s0, s, u, dist, d, W;
+    int sb;   // s: 0 constant (parallel or clamped), 1 (b f - c e) / den, 2 -c / a, 3 (b - c) / a
+    bool uf;  // u = (b s0 + f) / e (else constant)
+};
+
+DLO_HD bool pair_fwd(const V3<float>* P, const float* w, float rsum, PairFwd& F) {
+    F.d1 = P[1] - P[0];
+    F.d2 = P[3] - P[2];
+    F.r = P[0] - P[2];
+    F.a = dot(F.d1, F.d1);
+    F.e = dot(F.d2, F.d2);
+    F.f = dot(F.d2, F.r);
+    F.c = dot(F.d1, F.r);
+    F.b = dot(F.d1, F.d2);
+    F.den = F.a * F.e - F.b * F.b;
+    float s = 0.f;
+    F.sb = 0;
+    if (!(F.den <= 1e-6f * F.a * F.e)) {
+        const float q = (F.b * F.f - F.c * F.e) / F.den;
+        s = q < 0.f ? 0.f : (q > 1.f ? 1.f : q);
+        F.sb = (q < 0.f || q > 1.f) ? 0 : 1;
+    }
+    F.s0 = s;
+    const float uu = (F.b * s + F.f) / F.e;
+    F.uf = false;
+    if (uu < 0.f) {
+        const float q = (-F.c) / F.a;
+        s = q < 0.f ? 0.f : (q > 1.f ? 1.f : q);
+        F.sb = (q < 0.f || q > 1.f) ? 0 : 2;
+        F.u = 0.f;
+    } else if (uu > 1.f) {
+        const float q = (F.b - F.c) / F.a;
+        s = q < 0.f ? 0.f : (q > 1.f ? 1.f : q);
+        F.sb = (q < 0.f || q > 1.f) ? 0 : 3;
+        F.u = 1.f;
+    } else {
+        F.u = uu;
+        F.uf = true;
+    }
+    F.s = s;
+    const float u = F.u;
+    const V3<float> ca = P[0] + s * (P[1] - P[0]);
+    const V3<float> cb = P[2] + u * (P[3] - P[2]);
+    const V3<float> dv = ca - cb;
+    const float d2 = dot(dv, dv);
+    const float os = 1.f - s, ou = 1.f - u;
+    F.W = w[0] * os * os + w[1] * s * s + w[2] * ou * ou + w[3] * u * u;
+    if (!(d2 > 1e-24f) || !(F.W > 0.f)) return false;
+    F.dist = dsqrt(d2);
+    F.d = rsum - F.dist;
+    if (!(F.d > 0.f)) return false;
+    F.n = dv / F.dist;
+    return true;
+}
+
+// Reverse of pair_fwd: from the cotangents of s, u, the normal, the depth and the weight sum,
+// the cotangents of the four points (Pb, overwritten).  Branches follow the forward's.
+DLO_HD void pair_fwd_rev(const PairFwd& F, const V3<float>* P, const float* w, float sb_, float ub_, V3<float> nb,
+                         float db, float Wb, V3<float>* Pb) {
+    const float s = F.s, u = F.u, os = 1.f - s, ou = 1.f - u;
+    sb_ += Wb * (2.f * w[1] * s - 2.f * w[0] * os);
+    ub_ += Wb * (2.f * w[3] * u - 2.f * w[2] * ou);
+    // n = dv / |dv|, d = rsum - |dv|
+    const V3<float> dvb = (nb - dot(nb, F.n) * F.n) / F.dist - db * F.n;
+    // dv = P0 + s (P1 - P0) - P2 - u (P3 - P2)
+    Pb[0] = os * dvb;
+    Pb[1] = s * dvb;
+    Pb[2] = (-ou) * dvb;
+    Pb[3] = (-u) * dvb;
+    sb_ += dot(dvb, P[1] - P[0]);
+    ub_ -= dot(dvb, P[3] - P[2]);
+    // the closest-point solve
+    float ab = 0.f, bb = 0.f, cb = 0.f, eb = 0.f, fb = 0.f;
+    if (F.uf) {   // u = (b s0 + f) / e with s = s0
+        bb += ub_ * F.s0 / F.e;
+        sb_ += ub_ * F.b / F.e;
+        fb += ub_ / F.e;
+        eb -= ub_ * u / F.e;
+    }
+    if (F.sb == 1) {   // s = (b f - c e) / den, den = a e - b^2
+        const float numb = sb_ / F.den, denb = -sb_ * s / F.den;
+        bb += numb * F.f - 2.f * F.b * denb;
+        fb += numb * F.b;
+        cb -= numb * F.e;
+        eb += denb * F.a - numb * F.c;
+        ab += denb * F.e;
+    } else if (F.sb == 2) {   // s = -c / a
+        cb -= sb_ / F.a;
+        ab -= sb_ * s / F.a;
+    } else if (F.sb == 3) {   // s = (b - c) / a
+        bb += sb_ / F.a;
+        cb -= sb_ / F.a;
+        ab -= sb_ * s / F.a;
+    }
+    const V3<float> d1b = (2.f * ab) * F.d1 + cb * F.r + bb * F.d2;
+    const V3<float> d2b = (2.f * eb) * F.d2 + fb * F.r + bb * F.d1;
+    const V3<float> rb = fb * F.d2 + cb * F.d1;
+    Pb[0] += rb - d1b;
+    Pb[1] += d1b;
+    Pb[2] -= rb + d2b;
+    Pb[3] += d2b;
+}
+
+// Vector-Jacobian product of the self-collision projection (pair_correction): with lo the
+// cotangents of the four corrections, the cotangents of the four points.  False where the pair
+// makes no correction (then Pb is untouched).
+DLO_HD bool pair_correction_vjp(const V3<float>* P, const float* w, float rsum, const V3<float>* lo, V3<float>* Pb) {
+    PairFwd F;
+    if (!pair_fwd(P, w, rsum, F)) return false;
+    const float s = F.s, u = F.u, os = 1.f - s, ou = 1.f - u;
+    const float k = F.d / F.W;
+    // sum_k lo_k . dx_k = k (n . Lam)
+    const V3<float> Lam = (w[0] * os) * lo[0] + (w[1] * s) * lo[1] - (w[2] * ou) * lo[2] - (w[3] * u) * lo[3];
+    const float m = dot(F.n, Lam);
+    const V3<float> Lamb = k * F.n;
+    const float sb_ = dot(Lamb, w[1] * lo[1] - w[0] * lo[0]);
+    const float ub_ = dot(Lamb, w[2] * lo[2] - w[3] * lo[3]);
+    pair_fwd_rev(F, P, w, sb_, ub_, k * Lam, m / F.W, -m * k / F.W, Pb);
+    return true;
+}
+
+// Vector-Jacobian product of one pair's self-contact friction (the velocity corrections of
+// fric_pair): with lo the cotangents of the four velocity corrections, the cotangents of the
+// four points (Pb) and velocities (Vb).  False where the pair makes no correction.
+DLO_HD bool fric_pair_vjp(const V3<float>* P, const V3<float>* Vv, const float* w, float rsum, float mu, float h,
+                          const V3<float>* lo, V3<float>* Pb, V3<float>* Vb) {
+    PairFwd F;
+    if (!pair_fwd(P, w, rsum, F)) return false;
+    const float s = F.s, u = F.u, os = 1.f - s, ou = 1.f - u;
+    const V3<float> vrel = os * Vv[0] + s * Vv[1] - ou * Vv[2] - u * Vv[3];
+    const float vn = dot(vrel, F.n);
+    const V3<float> vt = vrel - vn * F.n;
+    const float vt2 = dot(vt, vt);
+    if (!(vt2 > 1e-24f)) return false;
+    const float sv = dsqrt(vt2);
+    const float c0 = mu * F.d / (h * sv);
+    const bool free = c0 <= 1.f;
+    const float coef = free ? c0 : 1.f;
+    const float q = coef / F.W;
+    // sum_k lo_k . dv_k = -q (vt . Gam)
+    const V3<float> Gam = (w[0] * os) * lo[0] + (w[1] * s) * lo[1] - (w[2] * ou) * lo[2] - (w[3] * u) * lo[3];
+    const float m = dot(vt, Gam);
+    V3<float> vtb = (-q) * Gam;
+    const V3<float> Gamb = (-q) * vt;
+    float sb_ = dot(Gamb, w[1] * lo[1] - w[0] * lo[0]);
+    float ub_ = dot(Gamb, w[2] * lo[2] - w[3] * lo[3]);
+    const float coefb = -m / F.W, Wb = m * q / F.W;
+    float db = 0.f;
+    if (free) {   // coef = mu d / (h |vt|)
+        db = coefb * coef / F.d;
+        vtb += (-coefb * coef / (sv * sv)) * vt;
+    }
+    // vt = vrel - (vrel . n) n
+    const float vnb = -dot(vtb, F.n);
+    const V3<float> vrelb = vtb + vnb * F.n;
+    const V3<float> nb = vnb * vrel - vn * vtb;
+    Vb[0] = os * vrelb;
+    Vb[1] = s * vrelb;
+    Vb[2] = (-ou) * vrelb;
+    Vb[3] = (-u) * vrelb;
+    sb_ += dot(vrelb, Vv[1] - Vv[0]);
+    ub_ += dot(vrelb, Vv[2] - Vv[3]);
+    pair_fwd_rev(F, P, w, sb_, ub_, nb, db, Wb, Pb);
+    return true;
+}
+
 }  // namespace dlo

@@ -714,24 +714,11 @@ __global__ void prb_b2(SceneDev sc, const RodInfo* rods, const int* prod, long l
         w[k] = X0[idx[k]].w;
         lo[k] = f3(A.LV[idx[k]]);
     }
-    float lin[24];
-    for (int d = 0; d < 24; ++d) {
-        V3<dualf> Pd[4], Vd[4], dv[4];
-        for (int k = 0; k < 4; ++k) {
-            V3<float> ep = zf3(), ev = zf3();
-            if (d / 3 == k) (d % 3 == 0 ? ep.x : d % 3 == 1 ? ep.y : ep.z) = 1.f;
-            if (d / 3 == 4 + k) (d % 3 == 0 ? ev.x : d % 3 == 1 ? ev.y : ev.z) = 1.f;
-            Pd[k] = lift(Pf[k], ep);
-            Vd[k] = lift(Vf[k], ev);
-        }
-        float acc = 0.f;
-        if (fric_pair(Pd, Vd, w, 2.f * R.radius, sc.mu_self, h, dv))
-            for (int k = 0; k < 4; ++k) acc += dot(ders(dv[k]), lo[k]);
-        lin[d] = acc;
-    }
+    V3<float> pb[4], vb[4];
+    if (!fric_pair_vjp(Pf, Vf, w, 2.f * R.radius, sc.mu_self, h, lo, pb, vb)) return;
     for (int k = 0; k < 4; ++k) {
-        atomic_add3(&A.LP0[idx[k]], f3(lin[3 * k], lin[3 * k + 1], lin[3 * k + 2]));
-        atomic_add3(&A.LTMP[idx[k]], f3(lin[12 + 3 * k], lin[13 + 3 * k], lin[14 + 3 * k]));
+        atomic_add3(&A.LP0[idx[k]], pb[k]);
+        atomic_add3(&A.LTMP[idx[k]], vb[k]);
     }
 }
 
@@ -777,27 +764,9 @@ __global__ void prb_b4c(const RodInfo* rods, const int* prod, long long P, const
         w[k] = X0[idx[k]].w;
         lo[k] = f3(A.LD[idx[k]]);
     }
-    const float rsum = 2.f * R.radius;
-    {
-        V3<float> dxf[4], nf;
-        float su, uu, dd, W;
-        if (!pair_correction(Pf[0], Pf[1], Pf[2], Pf[3], w[0], w[1], w[2], w[3], rsum, dxf, su, uu, nf, dd, W)) return;
-    }
-    float lin[12];
-    for (int d = 0; d < 12; ++d) {
-        V3<dualf> Pd[4], dx[4], nn;
-        dualf su, uu, dd, W;
-        for (int k = 0; k < 4; ++k) {
-            V3<float> ep = zf3();
-            if (d / 3 == k) (d % 3 == 0 ? ep.x : d % 3 == 1 ? ep.y : ep.z) = 1.f;
-            Pd[k] = lift(Pf[k], ep);
-        }
-        float acc = 0.f;
-        if (pair_correction(Pd[0], Pd[1], Pd[2], Pd[3], w[0], w[1], w[2], w[3], rsum, dx, su, uu, nn, dd, W))
-            for (int k = 0; k < 4; ++k) acc += dot(ders(dx[k]), lo[k]);
-        lin[d] = acc;
-    }
-    for (int k = 0; k < 4; ++k) atomic_add3(&A.LTMP[idx[k]], f3(lin[3 * k], lin[3 * k + 1], lin[3 * k + 2]));
+    V3<float> pb[4];
+    if (!pair_correction_vjp(Pf, w, 2.f * R.radius, lo, pb)) return;
+    for (int k = 0; k < 4; ++k) atomic_add3(&A.LTMP[idx[k]], pb[k]);
 }
 
 // B4, the contact sweep's cotangents added (per vertex), plus the friction's on iteration 0

@@ -200,3 +200,60 @@ extern "C" void plane_rev_check(const float* in, float* out) {
         out[6 + d] = dot(ders(res), lo);
     }
 }
+
+// Self-contact projection and friction of one segment pair: closed-form vector-Jacobian products
+// against dual-number directional derivatives through the forward code.
+// in: P(12) V(12) w(4) rsum mu h lo_x(12) lo_v(12)  (55)
+// out: projection Pb (12) then dual (12); friction Pb (12), Vb (12) then dual (24); flags (2)
+extern "C" void pair_vjp_check(const float* in, float* out) {
+    V3<float> P[4], Vv[4], lx[4], lv[4];
+    float w[4];
+    for (int k = 0; k < 4; ++k) {
+        P[k] = ld3(in + 3 * k);
+        Vv[k] = ld3(in + 12 + 3 * k);
+        w[k] = in[24 + k];
+        lx[k] = ld3(in + 31 + 3 * k);
+        lv[k] = ld3(in + 43 + 3 * k);
+    }
+    const float rsum = in[28], mu = in[29], h = in[30];
+    for (int i = 0; i < 74; ++i) out[i] = 0.f;
+    V3<float> pb[4], vb[4];
+    const bool on = pair_correction_vjp(P, w, rsum, lx, pb);
+    out[72] = on ? 1.f : 0.f;
+    if (on)
+        for (int k = 0; k < 4; ++k) st3(out + 3 * k, pb[k]);
+    for (int d = 0; d < 12; ++d) {
+        V3<dualf> Pd[4], dx[4], n;
+        dualf s, u, dd, W;
+        for (int k = 0; k < 4; ++k) {
+            V3<float> e = zf3();
+            if (d / 3 == k) (d % 3 == 0 ? e.x : d % 3 == 1 ? e.y : e.z) = 1.f;
+            Pd[k] = lift(P[k], e);
+        }
+        float acc = 0.f;
+        if (pair_correction(Pd[0], Pd[1], Pd[2], Pd[3], w[0], w[1], w[2], w[3], rsum, dx, s, u, n, dd, W))
+            for (int k = 0; k < 4; ++k) acc += dot(ders(dx[k]), lx[k]);
+        out[12 + d] = acc;
+    }
+    const bool fon = fric_pair_vjp(P, Vv, w, rsum, mu, h, lv, pb, vb);
+    out[73] = fon ? 1.f : 0.f;
+    if (fon)
+        for (int k = 0; k < 4; ++k) {
+            st3(out + 24 + 3 * k, pb[k]);
+            st3(out + 36 + 3 * k, vb[k]);
+        }
+    for (int d = 0; d < 24; ++d) {
+        V3<dualf> Pd[4], Vd[4], dv[4];
+        for (int k = 0; k < 4; ++k) {
+            V3<float> ep = zf3(), ev = zf3();
+            if (d / 3 == k) (d % 3 == 0 ? ep.x : d % 3 == 1 ? ep.y : ep.z) = 1.f;
+            if (d / 3 == 4 + k) (d % 3 == 0 ? ev.x : d % 3 == 1 ? ev.y : ev.z) = 1.f;
+            Pd[k] = lift(P[k], ep);
+            Vd[k] = lift(Vv[k], ev);
+        }
+        float acc = 0.f;
+        if (fric_pair(Pd, Vd, w, rsum, mu, h, dv))
+            for (int k = 0; k < 4; ++k) acc += dot(ders(dv[k]), lv[k]);
+        out[48 + d] = acc;
+    }
+}

@@ -29,7 +29,7 @@ def H():
     assert r.returncode == 0, r.stderr
     lib = C.CDLL(out)
     for n in ("hinge_grad_host", "contact_host", "closest_host", "expmap_host", "capsule_rev_check",
-              "plane_rev_check"):
+              "plane_rev_check", "pair_vjp_check"):
         getattr(lib, n).argtypes = [C.c_void_p, C.c_void_p]
     lib.hinge_hvp_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hinge_fold_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -232,3 +232,50 @@ def test_closed_form_contact_reverses_match_dual_numbers(H):
         if out[12] == 0:
             continue
         np.testing.assert_allclose(out[:6], out[6:12], rtol=2e-3, atol=2e-3 * max(np.abs(out[6:12]).max(), 1e-6))
+
+
+def test_closed_form_pair_reverses_match_dual_numbers(H):
+    """The adjoint's closed-form vector-Jacobian products of the self-collision projection and of
+    the pair friction (App. A.1) equal the transpose-Jacobian products taken with dual numbers
+    through the forward code, in every branch of the clamped closest-point solve: interior
+    points, one or both parameters clamped at a segment end, and near-parallel segments."""
+    rng = np.random.default_rng(11)
+    r = 0.002
+    seen = {"proj": 0, "fric": 0, "end": 0, "parallel": 0}
+    for trial in range(3000):
+        kind = trial % 3
+        p0 = rng.normal(size=3) * 0.004
+        d1 = rng.normal(size=3)
+        d1 *= 0.01 / np.linalg.norm(d1)
+        if kind == 2:   # near-parallel second segment
+            d2 = d1 + rng.normal(size=3) * 1e-4
+        else:
+            d2 = rng.normal(size=3)
+            d2 *= 0.01 / np.linalg.norm(d2)
+        # second segment crossing near the first one at a random parameter (beyond its ends for
+        # kind 1), a random normal offset below the contact distance
+        t = rng.uniform(-0.4, 1.4) if kind == 1 else rng.uniform(0.0, 1.0)
+        off = rng.normal(size=3)
+        off *= rng.uniform(0.2, 1.0) * 2 * r / np.linalg.norm(off)
+        q0 = p0 + t * d1 + off - rng.uniform(0.0, 1.0) * d2
+        P = np.concatenate([p0, p0 + d1, q0, q0 + d2])
+        V = rng.normal(size=12) * 0.05
+        w = rng.uniform(0.5, 2.0, size=4)
+        w[rng.integers(0, 4)] *= rng.integers(0, 2)   # sometimes a kinematic end (w = 0)
+        inp = fl(np.concatenate([P, V, w, [2 * r, 0.3, 2e-4], rng.normal(size=12), rng.normal(size=12)]))
+        out = call(H.pair_vjp_check, inp, n_out=74)
+        if out[72]:
+            seen["proj"] += 1
+            seen["end"] += kind == 1
+            seen["parallel"] += kind == 2
+            ref = out[12:24]
+            np.testing.assert_allclose(out[:12], ref, rtol=2e-3, atol=2e-3 * max(np.abs(ref).max(), 1e-6))
+        else:
+            assert not np.any(out[12:24])
+        if out[73]:
+            seen["fric"] += 1
+            ref = out[48:72]
+            np.testing.assert_allclose(out[24:48], ref, rtol=2e-3, atol=2e-3 * max(np.abs(ref).max(), 1e-6))
+        else:
+            assert not np.any(out[48:72])
+    assert min(seen.values()) > 100, seen
