@@ -193,7 +193,7 @@ void best_shape(int nv, bool contact, bool rec, int& w, int& nb) {
 }  // namespace
 
 // Plan of the chunked backward for checkpoint interval K: frames per chunk C (the records of
-// one chunk of every rod within rec_budget, at most 16 frames), per-rod buffer sizes and the
+// one chunk of every rod within rec_budget, at most 64 frames), per-rod buffer sizes and the
 // workspace of all rods at once.
 dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out, size_t rec_budget) {
     const size_t nb_ = c->buckets.size();
@@ -222,7 +222,7 @@ dlo_status bwd_plan(dlo_ctx* c, int force, int K, BwdPlan& out, size_t rec_budge
         out.nsmax[k] = ns;
         per_frame += 16 * (size_t)bk.n * frame_rec_h(bk.nv_max, c->opt.n_iter_pbd, ns);
     }
-    int C = (int)std::max<size_t>(1, std::min<size_t>(16, rec_budget / std::max<size_t>(per_frame, 1)));
+    int C = (int)std::max<size_t>(1, std::min<size_t>(64, rec_budget / std::max<size_t>(per_frame, 1)));
     if (C >= K) C = (C / K) * K;   // chunks start at checkpoints
     size_t need = 0;
     for (size_t k = 0; k < nb_; ++k) {
@@ -355,7 +355,7 @@ extern "C" dlo_status dlo_backward(dlo_ctx* c, const float* dL_dx_T, const float
         return set_err(c, DLO_ERR_INVALID_ARG, "self-contact gradients need at least one projection iteration");
     const int force = c->rec_nsub > 0 ? c->rec_nsub : 0;
     BwdPlan plan;
-    dlo_status pst = bwd_plan(c, force, c->ck_every, plan);
+    dlo_status pst = bwd_plan(c, force, c->ck_every, plan, c->rec_budget);
     if (pst != DLO_OK) return pst;
     if (plan.bytes > c->bw_bytes) {
         dev_free(c, c->bw_mem);

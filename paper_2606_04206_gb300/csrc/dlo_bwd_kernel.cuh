@@ -579,7 +579,16 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
     // (EdgeDual) and the seeds the two hinges of an edge send back to it (zeroed here).
     const bool strands = R.flags & ROD_STRANDS;
     const EdgeDual ES{a.LD, a.LP0, a.V1, a.DF, s.X, s.V, s.HB0, s.HB1, s.HB2, s.ND};
-    for (int j = g.tid; j < ne; j += TPR) {
+    // Each thread keeps its edges' position cotangents (this phase's and B7's) in registers and
+    // adds them up per vertex in a fixed order at the end: no floating-point atomics, so the
+    // reverse of a substep without contact candidates is bitwise reproducible.
+    constexpr int EPT = (NV + TPR - 1) / TPR;   // edges per thread
+    V3<float> le_keep[EPT];
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) {
+        const int j = g.tid + m * TPR;
+        le_keep[m] = zf3();
+        if (j >= ne) continue;
         const int j1 = (j + 1 == nv) ? 0 : j + 1;
         const float4 ed = s.ED[j], et = s.ET[j];
         ES.zero_seeds(j);
@@ -599,8 +608,7 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             le += R.kA * ((tl / eb) * E.t + (E.ell / eb - 1.f) / E.ell * (les - tl * E.t));
             gl[0] += (double)((E.ell / eb - 1.f) * tl);
         }
-        atomic_add3(&a.LX[j], -le);
-        atomic_add3(&a.LX[j1], le);
+        le_keep[m] = le;
         a.LT[j] = f4(gtb, 0.f);
         a.LE[j] = f4(gd1b, a.LE[j].w);
     }
@@ -650,28 +658,39 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
         hinge_core_reverse(Hd, gk0, gk1, gmt, mkd(0.f), gta, gd1ra, gtb, gd1rb, ghta, ghtb);
         ES.add_seeds(ea, gta, gd1ra);
         ES.add_seeds(eb, gtb, gd1rb);
-        atomicAdd(&a.LE[ea].w, ghta.d);
-        atomicAdd(&a.LE[eb].w, ghtb.d);
+        atomicAdd(&ES.cs[ea].z, ghta.d);   // two terms per edge, added to zero: order-free
+        atomicAdd(&ES.cs[eb].z, ghtb.d);
         a.LK[i] = make_float4(lk0, lk1, 0.f, 0.f);
     }
     g.sync();
-    // ---- B7, per edge: the reverse through the edge's frame (vertices and base frame)
-    for (int j = g.tid; j < ne; j += TPR) {
+    // ---- B7, per edge: the reverse through the edge's frame (vertices and base frame); the
+    // edge's total position cotangent goes to s0 (its own slot, after its seeds are read)
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) {
+        const int j = g.tid + m * TPR;
+        if (j >= ne) continue;
         const float4 et = s.ET[j];
-        if (strands && !(et.w > 0.f)) continue;
-        V3<dualf> gt, gd1r;
-        ES.load_seeds(j, gt, gd1r);
-        EdgeF<dualf> Ed;
-        ES.load_rev(j, Ed);
-        V3<dualf> gtbd, gd1bd;
-        const V3<float> ge = ders(edge_reverse<dualf, true>(Ed, lift(f3(et)), lift(f3(s.ED[j])), gt, gd1r,
-                                                            mkd(0.f), &gtbd, &gd1bd));
-        const int j1 = (j + 1 == nv) ? 0 : j + 1;
-        atomic_add3(&a.LX[j], -ge);
-        atomic_add3(&a.LX[j1], ge);
-        const float4 lt = a.LT[j], le = a.LE[j];
-        a.LT[j] = f4(f3(lt) + ders(gtbd), 0.f);
-        a.LE[j] = f4(f3(le) + ders(gd1bd), le.w);
+        V3<float> tot = le_keep[m];
+        if (!(strands && !(et.w > 0.f))) {
+            V3<dualf> gt, gd1r;
+            ES.load_seeds(j, gt, gd1r);
+            EdgeF<dualf> Ed;
+            ES.load_rev(j, Ed);
+            V3<dualf> gtbd, gd1bd;
+            tot += ders(edge_reverse<dualf, true>(Ed, lift(f3(et)), lift(f3(s.ED[j])), gt, gd1r, mkd(0.f), &gtbd,
+                                                  &gd1bd));
+            const float4 lt = a.LT[j], le = a.LE[j];
+            a.LT[j] = f4(f3(lt) + ders(gtbd), 0.f);
+            a.LE[j] = f4(f3(le) + ders(gd1bd), le.w + ES.cs[j].z);
+        }
+        ES.s0[j] = f4(tot, 0.f);
+    }
+    g.sync();
+    for (int i = g.tid; i < nv; i += TPR) {
+        V3<float> l = f3(a.LX[i]);
+        if (closed || i < nv - 1) l -= f3(ES.s0[i]);                   // edge i starts here
+        if (closed || i > 0) l += f3(ES.s0[i == 0 ? ne - 1 : i - 1]);  // edge i-1 ends here
+        a.LX[i] = f4(l, 0.f);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) gm[c] += gl[c];

@@ -243,11 +243,11 @@ extern "C" dlo_status dlo_begin_rollout(dlo_ctx* c, int n_frames) {
     const size_t per = 16 * (3 * (size_t)c->V + 2 * (size_t)c->Et) + sizeof(float) * 24 * (size_t)c->B;
     const size_t abytes = sizeof(float) * 12 * (size_t)c->B * n_frames;
     int K = std::min(c->opt.checkpoint_every, n_frames);
+    const size_t budget = c->opt.hbm_budget ? c->opt.hbm_budget : ((size_t)80 << 30);
     if (K <= 0) {
         // autotune: the shortest interval (the least recomputation in the backward) whose
         // checkpoint ring, action record and backward workspace fit the HBM budget; the
         // backward reruns at most K - 1 frames per segment to rebuild the frame-start states
-        const size_t budget = c->opt.hbm_budget ? c->opt.hbm_budget : ((size_t)80 << 30);
         K = n_frames;
         for (int k = 1; k <= n_frames; ++k) {
             BwdPlan plan;
@@ -260,6 +260,15 @@ extern "C" dlo_status dlo_begin_rollout(dlo_ctx* c, int n_frames) {
         }
     }
     const int count = (n_frames + K - 1) / K;
+    // Frames per backward launch pair: the chunk records may take half of what the ring and the
+    // action record leave of the budget (at most 24 GiB), and never less than the default the
+    // interval was chosen with.  Longer chunks mean fewer launch pairs, each with its own tail.
+    {
+        const size_t used = per * (size_t)count + abytes;
+        const size_t spare = budget > used ? budget - used : 0;
+        const size_t dflt = std::min<size_t>((size_t)8 << 30, budget / 8);
+        c->rec_budget = std::max(dflt, std::min<size_t>((size_t)24 << 30, spare / 2));
+    }
     const size_t need = per * count + 256 * 8;
     if (need > c->ck_bytes) {
         dev_free(c, c->ck_mem);

@@ -63,6 +63,7 @@ struct dlo_ctx {
     bool rec_from_set = false;
     int rec_frames = 0, rec_done = 0, rec_nsub = 0;
     int ck_every = 0, ck_count = 0;
+    size_t rec_budget = 0;   // chunk-record bytes the backward may use (set by dlo_begin_rollout)
     dlo::StateRef ck{};
     void* ck_mem = nullptr;
     size_t ck_bytes = 0;

@@ -175,3 +175,18 @@ def test_backward_requires_a_recorded_rollout():
     with pytest.raises(DloError) as ei:
         sim.backward()
     assert ei.value.status == 7
+
+
+def test_backward_without_candidates_is_bitwise_reproducible():
+    """Without self-contact candidates the reverse adds every cotangent in a fixed order (no
+    floating-point atomics with more than two terms), so two backward passes of the same
+    rollout, on two contexts, agree bit for bit in every gradient group."""
+    p = inputs.trajopt(n_rods=6, frames=6, seed=17, n=48, self_contact=False)
+    wx, wv, wth = weights(p, seed=3)
+    outs = []
+    for _ in range(2):
+        sim = sim_for(p)
+        outs.append(device_gradients(sim, p, 6, wx, wv, wth))
+        sim.close()
+    for k in GROUPS:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
