@@ -63,7 +63,8 @@ typedef struct {
     float radius;         /* m (uniform along the rod) */
     float K_stretch;      /* stretching modulus K, Pa (k_s = K A); ignored if inextensible */
     float E_bend;         /* bending modulus E, Pa (B = E A r^2 / 4) */
-    float G_twist;        /* twisting modulus G, Pa (beta = G A r^2 / 2); 0 = no twist energy */
+    float G_twist;        /* twisting modulus G, Pa (beta = G A r^2 / 2); 0 = no twist energy
+                             and no twist dynamics (the twist angles keep their values) */
     int   inextensible;   /* 1: stretching energy off, edges projected to rest length */
     float strain_limit;   /* >0: elastic stretching plus projection back into [1-s, 1+s] */
     int   plastic;        /* 1: bending plasticity on */
@@ -152,8 +153,9 @@ dlo_status dlo_set_state(dlo_ctx* ctx, const float* x, const float* v, const flo
 /* Replace the per-rod material (host mat[B]) after create: the moduli K_stretch, E_bend and
  * G_twist, the yield curvature, the creep rate and the damping, with which the next dlo_step
  * runs.  Each rod's substep count is recomputed from the new moduli (as at dlo_create).
- * Density, radius, inextensibility, strain limit, plasticity and topology are fixed at
- * create (they set masses, inertias and the rod's constraints) and must be unchanged.  Ends
+ * Density, radius, inextensibility, strain limit, plasticity, topology and whether G_twist
+ * is zero are fixed at create (they set masses, inertias and the rod's constraints; a rod
+ * with G_twist = 0 has no twist dynamics) and must be unchanged.  Ends
  * any armed recording (a recorded rollout ran with the previous material).  Synchronises.
  * Defined by: the material parameters of the energies and the plasticity rule of App. A.1
  * (the quantities the system identification of Sec. 5 fits).

@@ -476,7 +476,10 @@ class OracleSim:
         ea, eb_ = hinge_sides(ebar, closed)
         mass = rho[:, None] * A[:, None] * lv                 # reading: lumped Voronoi mass
         inertia = 0.5 * rho[:, None] * A[:, None] * ebar * r[:, None] ** 2   # reading: solid-cylinder axial inertia
-        inertia = torch.where(G["ereal"], inertia, torch.full_like(inertia, math.inf))   # break edges: no twist dynamics
+        # break edges, and every edge of a rod with no twist stiffness (G = 0, the table's
+        # "Twisting -"; reading O41): no twist dynamics, the twist angle keeps its value
+        twist = (self.mat["G"][ids].detach() > 0)[:, None]
+        inertia = torch.where(G["ereal"] & twist, inertia, torch.full_like(inertia, math.inf))
         # kinematic vertices: pinned, or grasped by a gripper (Sec. 3.2)
         kind = np.zeros((len(ids), N), np.int64)
         off = np.zeros((len(ids), N, 3))
@@ -920,7 +923,7 @@ class OracleSim:
             R = G["R"]
             U = elastic_energy(S["x"], S["theta"], S["tb"], S["d1b"], S["mprev"], S["kbar"], R, G["closed"],
                                G["strands"])
-            Iw = torch.where(G["ereal"], R["inertia"] * S["omega"] ** 2, torch.zeros_like(S["omega"]))
+            Iw = torch.where(torch.isfinite(R["inertia"]), R["inertia"] * S["omega"] ** 2, torch.zeros_like(S["omega"]))
             ke = 0.5 * (R["mass"] * dot(S["v"], S["v"])).sum(1) + 0.5 * Iw.sum(1)
             pe = (R["mass"] * S["x"][..., 2]).sum(1) * self.p.gravity
             out[G["ids"]] = torch.stack([ke, U, pe], 1).detach().numpy()

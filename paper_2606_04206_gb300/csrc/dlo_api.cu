@@ -209,7 +209,12 @@ extern "C" dlo_status dlo_create(dlo_ctx** out, int batch, const int* n_verts, c
                 return DLO_ERR_INVALID_ARG;
             }
             lmin = std::min(lmin, eb[j]);
-            es[e0 + j] = make_float2((float)eb[j], (float)(1.0 / (0.5 * rho * A * eb[j] * r * r)));
+            // with no twist stiffness (G = 0) the twist angle has no dynamics: an edge without a
+            // restoring torque and with an axial inertia this small (1/2 rho A r^2 |e|) would
+            // spin up under the bending-twist coupling alone (reading O41 of the paper's
+            // "Twisting -" rows)
+            const double invI = m.G_twist > 0.f ? 1.0 / (0.5 * rho * A * eb[j] * r * r) : 0.0;
+            es[e0 + j] = make_float2((float)eb[j], (float)invI);
         }
         const bool inext = m.inextensible != 0;
         const int ns = substeps_for(opt->dt, opt->substeps_min, rho, r, m.K_stretch, m.E_bend, m.G_twist, inext, lmin);
@@ -394,11 +399,12 @@ extern "C" dlo_status dlo_set_material(dlo_ctx* c, const dlo_material* mat) {
         if (!material_ok(m))
             return set_err(c, DLO_ERR_INVALID_ARG, "rod " + std::to_string(b) + ": material value out of range");
         if (m.density != m0.density || m.radius != m0.radius || m.inextensible != m0.inextensible ||
-            m.strain_limit != m0.strain_limit || m.plastic != m0.plastic || m.closed != m0.closed)
+            m.strain_limit != m0.strain_limit || m.plastic != m0.plastic || m.closed != m0.closed ||
+            (m.G_twist > 0.f) != (m0.G_twist > 0.f))
             return set_err(c, DLO_ERR_INVALID_ARG,
                            "rod " + std::to_string(b) +
-                               ": density, radius, inextensibility, strain limit, plasticity and topology are fixed "
-                               "at dlo_create");
+                               ": density, radius, inextensibility, strain limit, plasticity, topology and whether "
+                               "the twist modulus is zero are fixed at dlo_create");
         nsub[b] = substeps_for(c->opt.dt, c->opt.substeps_min, m.density, m.radius, m.K_stretch, m.E_bend,
                                m.G_twist, m.inextensible != 0, c->lmin_h[b]);
         set_moduli(rods[b], m, nsub[b], c->opt.dt);

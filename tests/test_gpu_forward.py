@@ -258,3 +258,17 @@ def test_status_flags_motion_past_the_candidate_margin():
     sim.get_state()                               # a warning, not an error
     st = sim.query(Q_STATUS)
     assert not (st[0] & STATUS_MOVED_PAST_MARGIN) and (st[1] & STATUS_MOVED_PAST_MARGIN), st
+
+
+def test_rods_without_twist_stiffness_keep_their_twist_and_stay_finite():
+    """Reading O41 on the device: a rope with G = 0 has no twist dynamics, so its twist angles
+    and rates stay exactly zero.  The candidate checked is one of the CMA-ES population's
+    knotted ropes (the bench's Unknotting generation) that, with a dynamic twist angle of so
+    small an axial inertia, spun up its twist and became non-finite within 650 frames."""
+    p = inputs.cmaes(pop=400, frames=2000, seed=5000, n=128).subset([0, 220])
+    sim = sim_for(p)
+    sim.reset()
+    sim.step(actions_dev(p), 2000)
+    x, v, th = (t.cpu().numpy() for t in sim.get_state())
+    assert np.isfinite(x).all() and np.isfinite(v).all()
+    assert np.all(th == 0.0) and np.all(v[:, 3] == 0.0)

@@ -787,3 +787,24 @@ def test_damping_decays_velocity_and_twist_rate_geometrically():
         np.testing.assert_allclose(st["omega"], np.full(n - 1, q ** k * 3.0), rtol=1e-12)
         moved = h * v0 * q * (1.0 - q ** k) / (1.0 - q)
         np.testing.assert_allclose(st["x"] - p.x0, np.tile(moved, (n, 1)), rtol=1e-9, atol=1e-15)
+
+
+def test_no_twist_stiffness_means_no_twist_dynamics():
+    """Reading O41: a rod with G = 0 (the parameter table's "Twisting -" rows) has no twist
+    dynamics; its twist angles and rates keep their start values (here zero) while the rod
+    bends and swings in 3D.  With a twist modulus that is tiny but positive, the same rod's
+    twist angles move under the bending-twist coupling alone, so the pin is not trivially
+    satisfied by the frames."""
+    n = 16
+    s = np.linspace(0.0, 1.0, n)
+    x = np.stack([0.3 * s, 0.1 * np.sin(3 * s), 0.5 + 0.05 * np.cos(4 * s)], 1)   # curved, non-planar
+    out = {}
+    for G in (0.0, 1e-9):
+        p = inputs.custom([x], frames=20, K=1e5, E=1e4, G=G)
+        sim = OracleSim(p)
+        sim.set_state(p.x0, p.v0, p.theta0, p.omega0)
+        sim.step(p.actions, 20)
+        out[G] = sim.get_state()
+    assert np.all(out[0.0]["theta"] == 0.0) and np.all(out[0.0]["omega"] == 0.0)
+    assert np.abs(out[1e-9]["theta"]).max() > 1e-12      # exactly zero only without dynamics
+    assert np.abs(out[0.0]["x"] - x).max() > 1e-3        # the rod did move
