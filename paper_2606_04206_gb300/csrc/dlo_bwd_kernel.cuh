@@ -605,8 +605,9 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
             const V3<float> les = f3(lgb) - f3(lga);
             const float eb = P.ES[e0 + j].x;
             const float tl = dot(E.t, les);
-            le += R.kA * ((tl / eb) * E.t + (E.ell / eb - 1.f) / E.ell * (les - tl * E.t));
-            gl[0] += (double)((E.ell / eb - 1.f) * tl);
+            const float st = edge_strain(f3(s.X0[j1]) - f3(s.X0[j]), eb);
+            le += R.kA * ((tl / eb) * E.t + st / E.ell * (les - tl * E.t));
+            gl[0] += (double)(st * tl);
         }
         le_keep[m] = le;
         a.LT[j] = f4(gtb, 0.f);

@@ -47,6 +47,17 @@ DLO_HD void len_inv(V3<float> e, float& ell, float& inv) {
     ell = e2 * inv;
 }
 
+// Axial strain |e| / |ebar| - 1 with IEEE-rounded square root and quotient: the stretching
+// sensitivity sums strains of nearly inextensible edges, so it keeps what float32 positions
+// resolve rather than the approximate square root's extra ulps.
+DLO_HD float edge_strain(V3<float> e, float eb) {
+#ifdef __CUDA_ARCH__
+    return __fdiv_rn(__fsqrt_rn(dot(e, e)), eb) - 1.f;
+#else
+    return sqrtf(dot(e, e)) / eb - 1.f;
+#endif
+}
+
 // ------------------------------------------------------------------ edge frames
 template <class T>
 struct EdgeF {

@@ -188,16 +188,11 @@ __global__ void pl_vertex(SceneDev sc, const RodInfo* rods, const int* vrod, lon
         const V3<float> e = f3(X[v0 + ip]) - xi;
         const float ell_i = sqrtf(dot(e, e));
         t_i = e / ell_i;
-        if (R.kA > 0.f) {
-            const float eb = ES[e0 + i].x;
-            g -= (R.kA * (ell_i / eb - 1.f)) * t_i;
-        }
+        if (R.kA > 0.f) g -= (R.kA * edge_strain(e, ES[e0 + i].x)) * t_i;
     }
     if (R.kA > 0.f && (closed || i >= 1) && !(strands && !(ES[e0 + im].x > 0.f))) {
         const V3<float> e = xi - f3(X[v0 + im]);
-        const float ell = sqrtf(dot(e, e));
-        const float eb = ES[e0 + im].x;
-        g += (R.kA * (ell / eb - 1.f) / ell) * e;
+        g += (R.kA * edge_strain(e, ES[e0 + im].x)) * (e / sqrtf(dot(e, e)));
     }
     const float4 vi = Vl[gv];
     const float4 kin = KIN[gv];
@@ -1002,8 +997,9 @@ __global__ void prb_b8(const RodInfo* rods, const int* erod, long long Et, const
         const V3<float> les = f3(A.LG[b]) - f3(A.LG[a]);
         const float eb = ES[ge].x;
         const float tl = dot(E.t, les);
-        le += R.kA * ((tl / eb) * E.t + (E.ell / eb - 1.f) / E.ell * (les - tl * E.t));
-        atomicAdd(&A.GM[5 * rod + 0], (double)(E.ell / eb - 1.f) * (double)tl);
+        const float st = edge_strain(f3(X0[b]) - f3(X0[a]), eb);
+        le += R.kA * ((tl / eb) * E.t + st / E.ell * (les - tl * E.t));
+        atomicAdd(&A.GM[5 * rod + 0], (double)st * (double)tl);
     }
     A.HBE[ge] = f4(le, 0.f);
     A.LT[ge] = f4(gtb, 0.f);

@@ -789,19 +789,16 @@ __device__ __forceinline__ void substep_body(const SceneDev& sc, const float4* _
         float ell_i = 0.f;
         // a break edge (between two strands) starts here: no tangent, no force, frame kept
         const bool brk = strands && has_e && !(ES[e0 + i].x > 0.f);
+        // stretching: the strains with IEEE-rounded square roots and quotients (the strains of
+        // nearly inextensible ropes are ~1e-4, so a few ulps of the length matter to them)
         if (has_e && !brk) {
             const float4 q = EA[i];
             ell_i = q.w;
             t_i = f3(q);
-            if (R.kA > 0.f) {
-                float eb = ES[e0 + i].x;
-                g -= (R.kA * (ell_i / eb - 1.f)) * t_i;
-            }
+            if (R.kA > 0.f) g -= (R.kA * edge_strain(f3(s.X0[i + 1 == nv ? 0 : i + 1]) - xi, ES[e0 + i].x)) * t_i;
         }
-        if (R.kA > 0.f && has_em && !(strands && !(ES[e0 + im].x > 0.f))) {
-            const float4 q = EA[im];   // edge i-1 ends here
-            g += (R.kA * (q.w / ES[e0 + im].x - 1.f)) * f3(q);
-        }
+        if (R.kA > 0.f && has_em && !(strands && !(ES[e0 + im].x > 0.f)))   // edge i-1 ends here
+            g += (R.kA * edge_strain(xi - f3(s.X0[im]), ES[e0 + im].x)) * f3(EA[im]);
         float4 vi = s.V[i];
         const float4 kin = KIN[v0 + i];
         const int kind = (int)kin.w;

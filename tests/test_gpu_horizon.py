@@ -144,6 +144,12 @@ def test_200_frames_four_segments_against_oracle_and_central_differences():
     # context) while the device and the oracle's reverse mode run here
     pool = ProcessPoolExecutor(max_workers=max(2, min(16, os.cpu_count() or 2)), mp_context=mp.get_context("spawn"))
     futs = [pool.submit(oracle_fd.central_difference, job(*d)) for d in draws]
+    # the same differences at half and at twice the step: their spread estimates the
+    # differences' own error (FP64 rounding amplified by the rollout, truncation, and yield
+    # decisions close to the threshold within the step)
+    scaled = lambda d, m: job(*d)[:5] + (m * job(*d)[5],)
+    futs2 = [pool.submit(oracle_fd.central_difference, scaled(d, 0.5)) for d in draws]
+    futs3 = [pool.submit(oracle_fd.central_difference, scaled(d, 2.0)) for d in draws]
     try:
         got = device_target_gradients(p, frames, K)
         got1 = device_target_gradients(p, frames, 1)
@@ -154,8 +160,11 @@ def test_200_frames_four_segments_against_oracle_and_central_differences():
         r32 = oracle_target_gradients(p, frames, torch.float32)
         bars = conditioned_check(p, got, r64, r32, f"{frames} frames, K = {K}:")
         ok, flagged = [], []
-        for f, (name, idx, b) in zip(futs, draws):
+        for f, f2, f3, (name, idx, b) in zip(futs, futs2, futs3, draws):
             fd, same = f.result()
+            fd2, same2 = f2.result()
+            fd3, same3 = f3.result()
+            same = same and same2 and same3
             if name == "act":
                 key, dev, ora = "act", got["act"][idx], r64["act"][idx]
             elif name in ("x0", "v0"):
@@ -164,20 +173,24 @@ def test_200_frames_four_segments_against_oracle_and_central_differences():
                 c = {"E": 1, "yield_curv": 3}[name]
                 sc = float(np.asarray(getattr(p, name))[idx])       # material entries are p dL/dp
                 key, dev, ora = "material", got["material"][idx, c] / sc, r64["material"][idx, c] / sc
-            (ok if same else flagged).append((name, idx, b, key, dev, ora, fd))
+            (ok if same else flagged).append((name, idx, b, key, dev, ora, fd, max(abs(fd - fd2), abs(fd - fd3))))
     finally:
         pool.shutdown(wait=False, cancel_futures=True)
     print(f"central differences: {len(ok)} coordinates compared, {len(flagged)} set aside (branch flip between "
           f"+h and -h): {[(n, i) for n, i, *_ in flagged]}")
     assert len(ok) >= 16
-    for name, idx, b, key, dev, ora, fd in ok:
+    for name, idx, b, key, dev, ora, fd, efd in ok:
         big = np.abs(rod_slice(p, r64, b)[key]).max()
         if key == "material":
             big /= float(np.asarray(getattr(p, name))[idx])
-        print("central difference", name, idx, "oracle %.6e device %.6e fd %.6e (group scale %.2e)" % (ora, dev, fd, big))
+        print("central difference", name, idx, "oracle %.6e device %.6e fd %.6e (step spread %.1e, group scale "
+              "%.2e)" % (ora, dev, fd, efd, big))
         # the oracle's FP64 reverse mode is the derivative the differences estimate; the
         # differences carry FP64 rounding amplified by the rollout, ~1e-5 of the group's largest
-        # entry at this horizon, which bounds the comparison of small entries
-        assert ora == pytest.approx(fd, rel=1e-3, abs=1e-5 * big), (name, idx, ora, fd, big)
+        # entry at this horizon, which bounds the comparison of small entries, and their own
+        # error, estimated by their spread over the three steps: near a contact or yield kink
+        # within a few steps the differences converge to the derivative slower than h^2 (up to
+        # about 4x their spread was seen at 200 frames), hence 5 times the spread
+        assert ora == pytest.approx(fd, rel=1e-3, abs=max(1e-5 * big, 5.0 * efd)), (name, idx, ora, fd, big, efd)
         # the device, within the float32 bar of its group, relative to the group's scale
-        assert abs(dev - fd) <= bars.get((b, key), 1e-3) * max(abs(fd), 0.1 * big), (name, idx, dev, fd)
+        assert abs(dev - fd) <= bars.get((b, key), 1e-3) * max(abs(fd), 0.1 * big) + 5.0 * efd, (name, idx, dev, fd)
