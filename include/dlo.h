@@ -176,7 +176,9 @@ dlo_status dlo_get_internal(dlo_ctx* ctx, float* ref, float* tan, float* hinge, 
 /* Arm recording of the next n_frames frames: checkpoints every K frames into the HBM ring
  * and a copy of the actions, so that dlo_backward can differentiate the rollout.  K is
  * opt.checkpoint_every, or when that is 0 the shortest interval whose ring, action record
- * and backward workspace fit opt.hbm_budget (80 GiB by default).
+ * and backward workspace fit opt.hbm_budget (80 GiB by default).  It also sets how many
+ * frames the backward reverses per launch pair: its chunk records may take half of what the
+ * ring and the action record leave of the budget (at most 24 GiB).
  * Defined by: the gradient checkpointing of Sec. 3.3 (checkpoints kept in HBM here).
  * Errors: DLO_ERR_INVALID_ARG for n_frames <= 0; DLO_ERR_OOM when the ring cannot be
  * allocated. */
