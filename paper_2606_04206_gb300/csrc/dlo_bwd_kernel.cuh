@@ -495,7 +495,15 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                     lam = lv;
                     continue;
                 }
-                const int nin = q >= 0 ? 18 : 6;
+                if (q < 0) {   // box: closed-form reverse
+                    const int bi = k - sc.n_planes;
+                    V3<float> lv;
+                    lx_acc += box_contact_rev(x, vs[k], f3(sc.box_c[bi]), f3(sc.box_h[bi]), R.radius, R.eps,
+                                              sc.mu_rigid, sc.restitution, lam, lv);
+                    lam = lv;
+                    continue;
+                }
+                const int nin = 18;   // the degenerate on-axis gripper contact keeps dual numbers
                 float lin[18];
 #pragma unroll 1
                 for (int d = 0; d < nin; ++d) {
@@ -511,12 +519,10 @@ __device__ __noinline__ void reverse_substep(const BwdParams& P, const RodInfo& 
                 }
                 lx_acc += f3(lin[0], lin[1], lin[2]);
                 lam = f3(lin[3], lin[4], lin[5]);
-                if (q >= 0) {
-                    add3(pa.ps0, q, f3(lin[6], lin[7], lin[8]));
-                    add3(pa.phs0, q, f3(lin[9], lin[10], lin[11]));
-                    add3(pa.vp, q, f3(lin[12], lin[13], lin[14]));
-                    add3(pa.w, q, f3(lin[15], lin[16], lin[17]));
-                }
+                add3(pa.ps0, q, f3(lin[6], lin[7], lin[8]));
+                add3(pa.phs0, q, f3(lin[9], lin[10], lin[11]));
+                add3(pa.vp, q, f3(lin[12], lin[13], lin[14]));
+                add3(pa.w, q, f3(lin[15], lin[16], lin[17]));
             }
             // v1 = v + h (-w g + gravity - c_d v)
             const float wi = x4.w;

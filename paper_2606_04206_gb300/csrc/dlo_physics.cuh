@@ -353,6 +353,32 @@ DLO_HD void contact_respond_rev(V3<float> v, float sdf, V3<float> n, V3<float> v
     lsdf = f0 < 1.f ? -lf * f0 / eps_s : 0.f;
 }
 
+// Reverse of the soft contact of a vertex with a static box (centre c, half extents hl) on the
+// active branch: from the cotangent lo of the output velocity, the cotangents of the position
+// (returned) and of the velocity (lv).  Outside the box the SDF is |u|, u the offset from the
+// nearest surface point (u_i = p_i - sign(p_i) hl_i on the axes where |p_i| > hl_i, else 0),
+// and the normal u/|u| turns with x; inside, the SDF is the nearest face's |p_k| - hl_k and its
+// normal is constant.
+DLO_HD V3<float> box_contact_rev(V3<float> x, V3<float> v, V3<float> c, V3<float> hl, float r, float eps_s,
+                                 float mu, float rest, V3<float> lo, V3<float>& lv) {
+    V3<float> n;
+    const float sdf = sdf_box(x, c, hl, n);
+    V3<float> ln, lvr;
+    float lsdf;
+    contact_respond_rev(v, sdf, n, zf3(), r, eps_s, mu, rest, lo, lv, lsdf, ln, lvr);
+    V3<float> lx = lsdf * n;
+    const V3<float> p = x - c;
+    const float qx = (p.x >= 0.f ? p.x : -p.x) - hl.x, qy = (p.y >= 0.f ? p.y : -p.y) - hl.y,
+                qz = (p.z >= 0.f ? p.z : -p.z) - hl.z;
+    if (qx > 0.f || qy > 0.f || qz > 0.f) {
+        const V3<float> w = (ln - dot(ln, n) * n) / sdf;
+        lx.x += qx > 0.f ? w.x : 0.f;
+        lx.y += qy > 0.f ? w.y : 0.f;
+        lx.z += qz > 0.f ? w.z : 0.f;
+    }
+    return lx;
+}
+
 // Reverse of the soft contact of a vertex with a capsule gripper (segment p +- hl * ax, radius
 // rc, rigid velocity vp + w x (x - p)) on the active branch: from the cotangent lo of the output
 // velocity, the cotangents of x, v, the capsule position p, its axis rotation (as a world-frame

@@ -885,7 +885,15 @@ __global__ void prb_b5(SceneDev sc, const RodInfo* rods, const int* vrod, long l
                 lam = lv;
                 continue;
             }
-            const int nin = q >= 0 ? 18 : 6;
+            if (q < 0) {   // box: closed-form reverse
+                const int bi = k - sc.n_planes;
+                V3<float> lv;
+                lx_acc += box_contact_rev(x, vs[k], f3(sc.box_c[bi]), f3(sc.box_h[bi]), R.radius, R.eps, sc.mu_rigid,
+                                          sc.restitution, lam, lv);
+                lam = lv;
+                continue;
+            }
+            const int nin = 18;   // the degenerate on-axis gripper contact keeps dual numbers
             float lin[18];
             for (int d = 0; d < nin; ++d) {
                 V3<float> e = zf3();
@@ -900,12 +908,10 @@ __global__ void prb_b5(SceneDev sc, const RodInfo* rods, const int* vrod, long l
             }
             lx_acc += f3(lin[0], lin[1], lin[2]);
             lam = f3(lin[3], lin[4], lin[5]);
-            if (q >= 0) {
-                atomic_add3f(pa + 3 * q, f3(lin[6], lin[7], lin[8]));
-                atomic_add3f(pa + 6 + 3 * q, f3(lin[9], lin[10], lin[11]));
-                atomic_add3f(pa + 24 + 3 * q, f3(lin[12], lin[13], lin[14]));
-                atomic_add3f(pa + 30 + 3 * q, f3(lin[15], lin[16], lin[17]));
-            }
+            atomic_add3f(pa + 3 * q, f3(lin[6], lin[7], lin[8]));
+            atomic_add3f(pa + 6 + 3 * q, f3(lin[9], lin[10], lin[11]));
+            atomic_add3f(pa + 24 + 3 * q, f3(lin[12], lin[13], lin[14]));
+            atomic_add3f(pa + 30 + 3 * q, f3(lin[15], lin[16], lin[17]));
         }
         lvn = f4((1.f - h * R.cd) * lam, 0.f);
         lg = f4((-h * x4.w) * lam, 0.f);

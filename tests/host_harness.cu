@@ -257,3 +257,28 @@ extern "C" void pair_vjp_check(const float* in, float* out) {
         out[48 + d] = acc;
     }
 }
+
+// Box contact: closed-form reverse against dual numbers.  in: x(3) v(3) c(3) hl(3) r eps mu rest lo(3)
+// out: lx(3) lv(3) then the dual-number ones (12), active (1)
+extern "C" void box_rev_check(const float* in, float* out) {
+    V3<float> x = ld3(in), v = ld3(in + 3), c = ld3(in + 6), hl = ld3(in + 9), lo = ld3(in + 16);
+    float r = in[12], eps = in[13], mu = in[14], rest = in[15];
+    V3<float> n;
+    bool on;
+    contact_respond(v, sdf_box(x, c, hl, n), n, zf3(), r, eps, mu, rest, on);
+    out[12] = on ? 1.f : 0.f;
+    for (int i = 0; i < 12; ++i) out[i] = 0.f;
+    if (!on) return;
+    V3<float> lv;
+    st3(out, box_contact_rev(x, v, c, hl, r, eps, mu, rest, lo, lv));
+    st3(out + 3, lv);
+    for (int d = 0; d < 6; ++d) {
+        V3<float> e = zf3();
+        (d % 3 == 0 ? e.x : d % 3 == 1 ? e.y : e.z) = 1.f;
+        V3<dualf> xd = lift(x, d < 3 ? e : zf3()), vd = lift(v, d >= 3 ? e : zf3()), nd;
+        dualf sdf = sdf_box(xd, c, hl, nd);
+        bool act;
+        V3<dualf> res = contact_respond(vd, sdf, nd, lift(zf3()), r, eps, mu, rest, act);
+        out[6 + d] = dot(ders(res), lo);
+    }
+}

@@ -29,7 +29,7 @@ def H():
     assert r.returncode == 0, r.stderr
     lib = C.CDLL(out)
     for n in ("hinge_grad_host", "contact_host", "closest_host", "expmap_host", "capsule_rev_check",
-              "plane_rev_check", "pair_vjp_check"):
+              "plane_rev_check", "pair_vjp_check", "box_rev_check"):
         getattr(lib, n).argtypes = [C.c_void_p, C.c_void_p]
     lib.hinge_hvp_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hinge_fold_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -279,3 +279,32 @@ def test_closed_form_pair_reverses_match_dual_numbers(H):
         else:
             assert not np.any(out[48:72])
     assert min(seen.values()) > 100, seen
+
+
+def test_closed_form_box_contact_reverse_matches_dual_numbers(H):
+    """The adjoint's closed-form reverse of the soft contact with a box equals the transpose-
+    Jacobian products taken with dual numbers through the forward code: outside the box near a
+    face, an edge and a corner (the normal turns with the position), and inside it."""
+    rng = np.random.default_rng(13)
+    hl = np.array([0.15, 0.15, 0.05])
+    seen = {"outside": 0, "inside": 0, "edge_or_corner": 0}
+    for trial in range(600):
+        # a point just outside or inside a random face, edge or corner region
+        axes = rng.integers(1, 4)
+        sign = rng.choice([-1.0, 1.0], size=3)
+        x = rng.uniform(-1.0, 1.0, size=3) * hl * 0.9
+        for k in rng.choice(3, size=axes, replace=False):
+            x[k] = sign[k] * (hl[k] + rng.uniform(-0.003, 0.004))
+        c = rng.normal(size=3) * 0.01
+        inp = fl(np.concatenate([x + c, rng.normal(size=3) * 0.3, c, hl, [0.002, 0.001, 0.5, 0.0],
+                                 rng.normal(size=3)]))
+        out = call(H.box_rev_check, inp, n_out=13)
+        if out[12] == 0:
+            continue
+        q = np.abs(x) - hl
+        outside = bool(np.any(q > 0))
+        seen["outside" if outside else "inside"] += 1
+        seen["edge_or_corner"] += int(np.sum(q > 0) >= 2)
+        ref = out[6:12]
+        np.testing.assert_allclose(out[:6], ref, rtol=2e-3, atol=2e-3 * max(np.abs(ref).max(), 1e-6))
+    assert min(seen.values()) > 20, seen
