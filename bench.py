@@ -45,9 +45,9 @@ FLOPS_FWD_PER_VS = 912.3
 FLOPS_BWD_PER_VS = 3650.0
 # DRAM bytes (read + write) of the backward per rod-frame of the 128-vertex trajopt workload,
 # from ncu captures (cold cache) of a 304-rod x 50-frame case of it, one 50-frame chunk:
-# rev_kernel 1621.56 + 27.45 MB, rec_kernel 25.05 + 1544.64 MB
+# rev_kernel 1621.64 + 27.34 MB, rec_kernel 25.05 + 1544.64 MB
 # (profiles/rec_rev_kernels_trajopt_304x128x50.md)
-BWD_DRAM_BYTES_PER_ROD_FRAME = (1621.555e6 + 27.448832e6 + 25.052928e6 + 1544.644e6) / (304 * 50)
+BWD_DRAM_BYTES_PER_ROD_FRAME = (1621.64096e6 + 27.341568e6 + 25.052928e6 + 1544.644e6) / (304 * 50)
 FP32_LANES_PER_SM = 128     # for the nominal figure printed beside the measured peak
 
 
