@@ -308,3 +308,58 @@ def test_closed_form_box_contact_reverse_matches_dual_numbers(H):
         ref = out[6:12]
         np.testing.assert_allclose(out[:6], ref, rtol=2e-3, atol=2e-3 * max(np.abs(ref).max(), 1e-6))
     assert min(seen.values()) > 20, seen
+
+
+def test_closed_form_pair_reverses_match_the_oracles_autograd(H):
+    """The same closed-form pair reverses against the FP64 oracle's own self-collision sweep and
+    friction (App. A.1), differentiated by autograd: an independent definition of the
+    projection, so a mistake shared by the device's forward and reverse would show here."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(23)
+    r, mu, h = 0.002, 0.3, 2e-4
+    n_cmp = 0
+    for trial in range(400):
+        p0 = rng.normal(size=3) * 0.004
+        d1 = rng.normal(size=3)
+        d1 *= 0.01 / np.linalg.norm(d1)
+        d2 = rng.normal(size=3)
+        d2 *= 0.01 / np.linalg.norm(d2)
+        off = rng.normal(size=3)
+        off *= rng.uniform(0.2, 1.0) * 2 * r / np.linalg.norm(off)
+        q0 = p0 + rng.uniform(-0.2, 1.2) * d1 + off - rng.uniform(0.0, 1.0) * d2
+        P = np.stack([p0, p0 + d1, q0, q0 + d2])
+        V = rng.normal(size=(4, 3)) * 0.05
+        w = rng.uniform(0.5, 2.0, size=4)
+        lx, lv = rng.normal(size=(4, 3)), rng.normal(size=(4, 3))
+        inp = fl(np.concatenate([P.ravel(), V.ravel(), w, [2 * r, mu, h], lx.ravel(), lv.ravel()]))
+        out = call(H.pair_vjp_check, inp, n_out=74)
+        # the oracle: one record of four vertices, the pair (0, 2): segments 0-1 and 2-3, in
+        # FP64 and, for the float32 floor of these products, in float32
+        res = {}
+        for dt in (torch.float64, torch.float32):
+            Pt = torch.tensor(P[None], dtype=dt, requires_grad=True)
+            Vt = torch.tensor(V[None], dtype=dt, requires_grad=True)
+            G = dict(N=4, R=dict(r=torch.tensor([r], dtype=dt), w=torch.tensor(w[None], dtype=dt)))
+            xs, infos = OracleSim.contact_sweep(None, G, Pt, [torch.tensor([[0, 2]])])
+            if not bool(infos[0]["act"][0]):
+                res[dt] = None
+                continue
+            gp = torch.autograd.grad((xs * torch.tensor(lx[None], dtype=dt)).sum(), Pt, retain_graph=True)[0]
+            vs = OracleSim.self_friction(SimpleNamespace(p=SimpleNamespace(mu_self=mu)), G, Vt, infos, h)
+            gP, gV = torch.autograd.grad((vs * torch.tensor(lv[None], dtype=dt)).sum(), [Pt, Vt])
+            res[dt] = (gp[0].double().numpy() - lx, np.concatenate([gP[0].double().numpy().ravel(),
+                                                                     gV[0].double().numpy().ravel() - lv.ravel()]))
+        if res[torch.float64] is None:
+            assert out[72] == 0
+            continue
+        assert out[72] == 1 and out[73] == 1
+        n_cmp += 1
+        (gp, ref), f32 = res[torch.float64], res[torch.float32]
+        # where float32 cannot resolve a product (a segment end close to the clamped closest-point
+        # solve's boundary, the friction's division by h |v_t|), its float32 floor, taken from the
+        # same definitions run in float32, bounds the comparison
+        f0 = 0.0 if f32 is None else np.abs(f32[0].ravel() - gp.ravel()).max()
+        f1 = 0.0 if f32 is None else np.abs(f32[1] - ref).max()
+        np.testing.assert_allclose(out[:12], gp.ravel(), rtol=1e-3, atol=max(1e-3 * np.abs(gp).max(), 4.0 * f0))
+        np.testing.assert_allclose(out[24:48], ref, rtol=1e-3, atol=max(1e-3 * np.abs(ref).max(), 4.0 * f1))
+    assert n_cmp > 100
