@@ -99,7 +99,7 @@ def test_full_size_backward_sampled_rods(full):
     # sensitivity sums the strains |e|/|ebar| - 1 of nearly inextensible edges, ~1e-4, which
     # float32 positions resolve to a few 1e-3 of themselves).  The same definitions run in
     # float32 from the same state miss by 1e-4 to 1e-2 depending on the rod; the bar is the
-    # the benchmark spec's 1e-3 or twice the largest of these float32 errors over the sampled rods.
+    # gradient tolerance 1e-3 or twice the largest of these float32 errors over the sampled rods.
     floor = max(f for _, _, f in mat)
     for b, (rel, cos), f in mat:
         assert rel <= max(1e-3, 2.0 * floor) and cos >= 0.999, (b, "material", rel, cos, f, floor)
