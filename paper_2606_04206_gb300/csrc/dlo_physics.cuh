@@ -470,7 +470,10 @@ DLO_HD bool pair_correction(V3<T> xa0, V3<T> xa1, V3<T> xb0, V3<T> xb1, float wa
 }
 
 // Friction of one pair (App. A.1), as a function of the four positions at the first
-// projection and the four rebuilt velocities; returns whether the pair acts.
+// projection and the four rebuilt velocities; returns whether the pair acts.  This is the
+// definition the closed-form reverse fric_pair_vjp differentiates (and is checked against
+// with dual numbers); the kernels' forward applies the same formula from the first sweep's
+// stored pair data (self_friction).
 template <class T>
 DLO_HD bool fric_pair(const V3<T>* P, const V3<T>* Vv, const float* w, float rsum, float mu, float h, V3<T>* dv) {
     T s, u, d, W;
