@@ -363,3 +363,73 @@ def test_closed_form_pair_reverses_match_the_oracles_autograd(H):
         np.testing.assert_allclose(out[:12], gp.ravel(), rtol=1e-3, atol=max(1e-3 * np.abs(gp).max(), 4.0 * f0))
         np.testing.assert_allclose(out[24:48], ref, rtol=1e-3, atol=max(1e-3 * np.abs(ref).max(), 4.0 * f1))
     assert n_cmp > 100
+
+
+def test_closed_form_rigid_contact_reverses_match_the_oracles_autograd(H):
+    """The closed-form reverses of the soft contact with a box and with a capsule gripper
+    against the FP64 oracle's own rigid-contact response (Sec. 3.2) under autograd: the
+    cotangents of the vertex position and velocity, and for the gripper of its position,
+    linear and angular velocity."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(29)
+    r, eps, mu = 0.002, 0.001, 0.5
+
+    def fake(boxes=(), hl=0.02, rc=0.01):
+        p = SimpleNamespace(eps_soft=eps / r, restitution=0.0, mu_rigid=mu, planes=[], boxes=list(boxes),
+                            grip_half_len=hl, grip_radius=rc)
+        return SimpleNamespace(p=p, dtype=torch.float64, _note=lambda *a: None)
+
+    def group(ngrip):
+        return dict(R=dict(r=torch.tensor([r], dtype=torch.float64), mass=torch.ones(1, 1, dtype=torch.float64)),
+                    kind=torch.zeros(1, 1, dtype=torch.int64), ngrip=torch.tensor([ngrip]))
+
+    n_box = 0
+    hlb = np.array([0.15, 0.15, 0.05])
+    for trial in range(300):
+        x = rng.uniform(-1.0, 1.0, size=3) * hlb * 0.9
+        for k in rng.choice(3, size=rng.integers(1, 4), replace=False):
+            x[k] = rng.choice([-1.0, 1.0]) * (hlb[k] + rng.uniform(-0.003, 0.004))
+        v, lo = rng.normal(size=3) * 0.3, rng.normal(size=3)
+        out = call(H.box_rev_check, fl(np.concatenate([x, v, np.zeros(3), hlb, [r, eps, mu, 0.0], lo])), n_out=13)
+        xt = torch.tensor(x[None, None], requires_grad=True)
+        vt = torch.tensor(v[None, None], requires_grad=True)
+        z = torch.zeros(1, 2, 3, dtype=torch.float64)
+        vo = OracleSim.rigid_contact(fake(boxes=[np.concatenate([np.zeros(3), hlb])]), group(0), xt, vt, z,
+                                     torch.eye(3, dtype=torch.float64).expand(1, 2, 3, 3), z, z)
+        if out[12] == 0:
+            continue
+        n_box += 1
+        gx, gv = torch.autograd.grad((vo * torch.tensor(lo)).sum(), [xt, vt])
+        ref = np.concatenate([gx.numpy().ravel(), gv.numpy().ravel()])
+        np.testing.assert_allclose(out[:6], ref, rtol=1e-3, atol=1e-3 * np.abs(ref).max())
+    assert n_box > 50
+
+    n_cap = 0
+    for trial in range(300):
+        ax = rng.normal(size=3)
+        ax /= np.linalg.norm(ax)
+        # a frame whose third column is the capsule axis
+        e1 = np.cross(ax, [1.0, 0.0, 0.0] if abs(ax[0]) < 0.9 else [0.0, 1.0, 0.0])
+        e1 /= np.linalg.norm(e1)
+        Rg = np.stack([e1, np.cross(ax, e1), ax], 1)
+        x = rng.normal(size=3) * 0.006
+        x[2] = abs(x[2]) + 0.009
+        v, vp, w, lo = rng.normal(size=3) * 0.2, rng.normal(size=3) * 0.05, rng.normal(size=3), rng.normal(size=3)
+        inp = fl(np.concatenate([x, v, np.zeros(3), ax, [0.02, 0.01], vp, w, [r, eps, mu, 0.0], lo]))
+        out = call(H.capsule_rev_check, inp, n_out=37)
+        if out[36] == 0:
+            continue
+        n_cap += 1
+        xt = torch.tensor(x[None, None], requires_grad=True)
+        vt = torch.tensor(v[None, None], requires_grad=True)
+        p0 = torch.zeros(1, 2, 3, dtype=torch.float64, requires_grad=True)
+        vpt = torch.tensor(np.stack([vp, np.zeros(3)])[None], requires_grad=True)
+        wt = torch.tensor(np.stack([w, np.zeros(3)])[None], requires_grad=True)
+        R0 = torch.tensor(np.stack([Rg, np.eye(3)])[None])
+        vo = OracleSim.rigid_contact(fake(), group(1), xt, vt, p0, R0, vpt, wt)
+        gx, gv, gp, gvp, gw = torch.autograd.grad((vo * torch.tensor(lo)).sum(), [xt, vt, p0, vpt, wt])
+        ref = np.concatenate([gx.numpy().ravel(), gv.numpy().ravel(), gp[0, 0].numpy(), gvp[0, 0].numpy(),
+                              gw[0, 0].numpy()])
+        got = np.concatenate([out[0:3], out[3:6], out[6:9], out[12:15], out[15:18]])
+        np.testing.assert_allclose(got, ref, rtol=1e-3, atol=1e-3 * np.abs(ref).max())
+    assert n_cap > 20
