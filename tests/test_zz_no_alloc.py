@@ -85,7 +85,7 @@ def test_noalloc_matches_backward_twice_in_a_row(kind, monkeypatch):
 def test_noalloc_with_more_resident_rods_than_the_static_scratch_holds(monkeypatch):
     """400 rods of 128 vertices, checkpoints every 50 frames: each resident rod needs ~1.1 MB of
     recompute scratch, so the static array holds fewer rods at once (~240) than the backward
-    keeps resident when it allocates (two per SM); the rods then run in fewer, longer-lived
+    keeps resident when it allocates (three per SM); the rods then run in fewer, longer-lived
     slots, with the same gradients."""
     p = inputs.small_case("trajopt", n_rods=400, n=128, frames=50)
     sim = sim_for(p, checkpoint_every=50)
