@@ -2,8 +2,10 @@
 //
 // Shared by the forward kernel and the backward kernel's recomputations.  Per substep
 // (DLO-Lab Sec. 3.1 / 3.2 / App. A.1):
-//   hinge phase   reference frames by time-parallel transport, curvature and twist, bending
-//                 plasticity on the rest curvature, exact energy gradient of each hinge
+//   edge phase    each edge's reference frame by time-parallel transport and its material frame
+//   hinge phase   curvature and twist, bending plasticity on the rest curvature, and the
+//                 hinge's energy gradient back to its two edges' frames
+//   edge phase    each edge's frame reversed once on the sum of its two hinges' seeds
 //   vertex phase  gradient gather + stretching, gravity, damping, symplectic-Euler velocity,
 //                 soft SDF contact (planes, boxes, capsule grippers), displacement predict,
 //                 kinematic vertices, new reference-frame base
